@@ -1,0 +1,341 @@
+"""Benchmark: cell-stage updates per second of the SSP-RK3 FVCW solver on the
+2-D corner-blast workload at 4096^2 (FP32 line arithmetic with FP64 state
+accumulation, with the plain FP64 form measured beside it).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+One JSON line on stdout (rank 0).  N > 1 (torchrun, one process per GPU) runs
+N independent replicas of the workload (the grid is not split across GPUs):
+value = the cell-stages of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-stage updates/s at 2D 4096^2, FP32 form vs FP64 plain, at stated L1 error"
+UNIT = "cell-stage/s"
+N_GRID = 4096
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            self.tmp.flush()
+            rows = [r.split(",") for r in open(self.tmp.name).read().strip().splitlines()]
+            os.unlink(self.tmp.name)
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# per-kernel algorithmic bytes per cell (design of the two-pass 2-D stage):
+# x sweep reads U_k (4 x 8 B) and writes D (4 x 8 B FP64 / 4 x 4 B mixed);
+# y sweep reads U_k and D, reads U^n in stages 2 and 3, writes U_{k+1}.
+def _kernel_bytes(prec: int) -> dict:
+    d = 8 if prec == 0 else 4
+    return {"x": 32 + 4 * d, "y": 32 + 4 * d + 32 * 2.0 / 3.0 + 32}
+
+
+def run_native(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1402_5618_gb300 import binding as B
+    from paper_1402_5618_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    B.lib()
+    p = W.blast_2d(N_GRID)
+    U0 = np.ascontiguousarray(p.U0).ravel()
+    ncell = p.nx * p.ny
+    stream = torch.cuda.Stream()
+    results = {}
+    for prec, steps in ((1, args.steps), (0, args.fp64_steps)):
+        s = B.Solver(B.config_from_problem(p, prec), stream=stream)
+        s.set_state(U0)
+        s.enqueue_steps(args.warmup)
+        torch.cuda.synchronize()
+        # per-kernel durations with CUDA events on the solver's stream
+        prof = [s.profile_step() for _ in range(args.profile_steps)]
+        torch.cuda.synchronize()
+        launches = s.launches_per_step()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _barrier(ws)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            s.enqueue_steps(steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        _barrier(ws)
+        ms = ev0.elapsed_time(ev1)
+        st = s.stats()
+        results[prec] = dict(ms=ms, steps=steps, prof=prof, launches=launches, clk=clk.summary(),
+                             violations=st.violations, t=st.t, theta2=st.theta2_active)
+        s.close()
+
+    # end-to-end through the public API with host buffers: H2D initial state,
+    # K steps, D2H final state, inside one wall-clock region
+    s = B.Solver(B.config_from_problem(p, 1), stream=stream)
+    Uh = np.empty_like(U0)
+    s.set_state(U0)
+    s.enqueue_steps(args.warmup)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    t0 = time.perf_counter()
+    s.set_state(U0)
+    s.enqueue_steps(args.steps)
+    s.get_state(Uh)
+    e2e_s = time.perf_counter() - t0
+    s.close()
+
+    # stated accuracy, measured live on a small smooth case: L1 density error
+    # of both forms against the translated closed-form vortex
+    acc = {}
+    pv = W.vortex_2d(128, t_final=1.0)
+    ex = W.vortex_2d(128, t=1.0).U0[0]
+    for prec in (0, 1):
+        sv = B.Solver(B.config_from_problem(pv, prec), stream=stream)
+        sv.set_state(np.ascontiguousarray(pv.U0).ravel())
+        sv.advance(pv.t_final)
+        Uv = sv.get_state()[0].reshape(pv.U0.shape)
+        sv.close()
+        acc[prec] = float(np.mean(np.abs(Uv[0] - ex)))
+
+    return dict(results=results, ncell=ncell, e2e_s=e2e_s, acc=acc,
+                state_bytes=U0.nbytes)
+
+
+def _roofline(r, prec, ncell, hbm_peak, peak_kind):
+    import numpy as np
+    prof = np.array(r["prof"])           # [steps, kernels]: dt kernel, then x, y per stage
+    kb = _kernel_bytes(prec)
+    xs = prof[:, 1::2].ravel()
+    ys = prof[:, 2::2].ravel()
+    dom, t_ms, per_cell = ("y_sweep", ys.mean(), kb["y"]) if ys.sum() >= xs.sum() else \
+        ("x_sweep", xs.mean(), kb["x"])
+    achieved = per_cell * ncell / (t_ms * 1e-3) / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+            "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
+            "peak_source": peak_kind, "alg_bytes_per_cell": round(per_cell, 1),
+            "avg_launch_ms": round(float(t_ms), 4),
+            "share_x_y": [round(float(xs.sum() / prof.sum()), 3), round(float(ys.sum() / prof.sum()), 3)]}
+
+
+def _cpu_baseline(seconds_target: float = 20.0):
+    """The oracle as it stands on the host cores: full 4096^2 RK3 steps."""
+    import numpy as np
+
+    import oracle
+    from paper_1402_5618_gb300 import workloads as W
+    p = W.blast_2d(N_GRID)
+    g = oracle.make_grid(p.ndim, p.nx, p.ny, p.dx, p.dy, p.gamma, p.bc)
+    U = np.ascontiguousarray(p.U0)
+    dt = p.cfl / oracle.max_rate(g, U)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        U = oracle.rk3_step(g, U, dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > seconds_target or n >= 4:
+            break
+    return {"value": p.nx * p.ny * 3 * n / el, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{n} SSP-RK3 step(s) of the 4096^2 blast in FP64 "
+                                         f"({el:.1f} s, OpenMP over grid lines)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=6)
+    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, ws)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    out = run_native(args, ws, rank, local)
+    ncell = out["ncell"]
+    rm = out["results"][1]
+    rd = out["results"][0]
+    ms_m = _barrier_max(rm["ms"], ws)
+    ms_d = _barrier_max(rd["ms"], ws)
+    e2e = _barrier_max(out["e2e_s"], ws)
+    if rank == 0:
+        hbm, kind = _peaks()
+        value = ws * ncell * 3 * rm["steps"] / (ms_m * 1e-3)
+        value_fp64 = ws * ncell * 3 * rd["steps"] / (ms_d * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_m / rm["steps"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "2-D corner blast (Sedov-type) 4096^2 on [0,1.1]^2, reflective "
+                                   "x-lo/y-lo, transmissive x-hi/y-hi, CFL 0.5, SSP-RK3, FVCW "
+                                   "component-wise with Zhang-Shu limiter and HLLC",
+                       "precision": "mixed: FP32 line arithmetic, FP64 state and stage combination",
+                       "grid": [N_GRID, N_GRID], "cells": ncell,
+                       "l2": "no flush: the state (537 MB FP64) and stage buffers exceed L2",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": _roofline(rm, 1, ncell, hbm, kind),
+            "clocks": rm["clk"],
+            "e2e": {"value": ws * ncell * 3 * args.steps / e2e, "unit": UNIT,
+                    "h2d_bytes_per_step": out["state_bytes"] / args.steps,
+                    "d2h_bytes_per_step": out["state_bytes"] / args.steps,
+                    "note": "set_state from host, K steps, get_state to host, wall clock"},
+            "gpu_launches": int(rm["launches"] * rm["steps"]),
+            "fp64_plain": {"value": value_fp64, "unit": UNIT, "steps": rd["steps"],
+                           "ms_per_step": ms_d / rd["steps"], "dtype": "f64",
+                           "roofline": _roofline(rd, 0, ncell, hbm, kind), "clocks": rd["clk"]},
+            "accuracy": {"case": "isentropic vortex 128^2, t = 1, L1 of density vs closed form",
+                         "l1_fp64": out["acc"][0], "l1_mixed": out["acc"][1],
+                         "ratio_mixed_over_fp64": out["acc"][1] / out["acc"][0]},
+            "positivity_violations": int(rm["violations"] + rd["violations"]),
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = _cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args, ws):
+    """The oracle (FP64 CPU reference) as it stands, on the host cores; each
+    step is one SSP-RK3 step of the blast on a 1024^2 grid (a bounded sample
+    of the 4096^2 workload: same problem, same per-cell work)."""
+    import numpy as np
+
+    import oracle
+    from paper_1402_5618_gb300 import workloads as W
+    n = 1024
+    p = W.blast_2d(n)
+    g = oracle.make_grid(p.ndim, p.nx, p.ny, p.dx, p.dy, p.gamma, p.bc)
+    U = np.ascontiguousarray(p.U0)
+    for _ in range(args.warmup):
+        dt = p.cfl / oracle.max_rate(g, U)
+        U = oracle.rk3_step(g, U, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dt = p.cfl / oracle.max_rate(g, U)
+        U = oracle.rk3_step(g, U, dt)
+    el = time.perf_counter() - t0
+    value = n * n * 3 * args.steps / el
+    sample = f"{args.steps} SSP-RK3 steps of the blast on a 1024^2 grid per run (FP64 oracle)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "2-D corner blast (Sedov-type), sampled at 1024^2",
+                   "grid": [n, n], "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

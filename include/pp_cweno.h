@@ -1,0 +1,170 @@
+/*
+ * pp_cweno.h -- C ABI of the GB300 (sm_103a) implementation of the
+ * positivity-preserving fifth-order finite-volume compact-WENO scheme for
+ * the compressible Euler equations (Guo, Xiong & Shi).
+ *
+ * The problem is the one the paper states (Sec. 1, eq. (1DEuler); Sec. 2.1):
+ * conservative Euler equations of an ideal gas with ratio of specific heats
+ * gamma, cell averages on a uniform grid, an SSP-RK3 time integrator whose
+ * stages apply the spatial operator of Sec. 2.2-2.4 (WENO-Z weights on the
+ * compact candidate stencils, tridiagonal solves, Zhang-Shu limiter, HLLC
+ * flux, flux difference) and a time step dt = cfl / max((|u|+a)/dx) taken
+ * from the cell averages at the start of each step (eq. (CFL-CD)).
+ * The 2-D form is a dimension-by-dimension extension (the paper is 1-D):
+ * the same line operator is applied along x and y and the two flux
+ * differences are added; dt = cfl / max((|u|+a)/dx + (|v|+a)/dy).
+ *
+ * State layout (every pointer in this API): float64 structure of arrays
+ *   U[v][j][i], i = 0..nx-1 fastest, j = 0..ny-1 (ny = 1 in 1-D),
+ *   1-D: v = 0..2 -> (rho, rho*u, E)
+ *   2-D: v = 0..3 -> (rho, rho*u, rho*v, E)
+ * A batch concatenates the problems' arrays in the order of the configs,
+ * each problem in the layout above.
+ *
+ * Ownership: a handle owns all device memory it allocates; the caller's
+ * buffers are only copied from / to and never retained.  All work is
+ * enqueued on the CUDA stream given at creation (NULL = legacy default
+ * stream).  Host pointers need not be pinned.
+ *
+ * Errors: every function returns PP_OK (0) or one of the PP_ERR_* codes
+ * below; none aborts, traps or prints.  pp_cweno_strerror() names a code.
+ * A handle that returned PP_ERR_CUDA may be unusable; destroy it.
+ */
+#ifndef PP_CWENO_H
+#define PP_CWENO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pp_cweno_s *pp_cweno_t;
+
+/* Boundary conditions of one grid side.  Periodic sides must pair. */
+typedef enum {
+  PP_BC_PERIODIC = 0,
+  PP_BC_TRANSMISSIVE = 1, /* zero-gradient ("Neumann"): ghosts copy the boundary cell */
+  PP_BC_REFLECTIVE = 2    /* mirror ghosts, normal momentum negated */
+} pp_bc_t;
+
+/* Arithmetic of the line operator. */
+typedef enum {
+  PP_PREC_FP64 = 0,  /* everything in FP64 */
+  PP_PREC_MIXED = 1  /* reconstruction, solves and HLLC in FP32; limiter
+                        factors near vacuum and the stage accumulation of
+                        the conserved variables in FP64 */
+} pp_prec_t;
+
+enum {
+  PP_OK = 0,
+  PP_ERR_ARG = 1,          /* bad sizes, gamma <= 1, cfl <= 0, unpaired periodic sides, ... */
+  PP_ERR_STATE = 2,        /* set_state input not in the admissible set G or not finite */
+  PP_ERR_NONPHYSICAL = 3,  /* a step produced a cell outside G (see stats.first_bad_cell) */
+  PP_ERR_STEPS = 4,        /* advance stopped at max_steps before t_final */
+  PP_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  PP_ERR_CUDA = 6,         /* a CUDA runtime call failed */
+  PP_ERR_UNSUPPORTED = 7   /* configuration outside what this build supports */
+};
+
+typedef struct {
+  int ndim;                /* 1 or 2 */
+  int64_t nx, ny;          /* cells; ny is ignored (1) when ndim == 1; each >= 8 */
+  double x0, x1, y0, y1;   /* domain [x0,x1] (x [y0,y1]) */
+  double gamma;            /* > 1 */
+  double cfl;              /* dt = cfl / max((|u|+a)/dx [+ (|v|+a)/dy]) */
+  int bc[4];               /* pp_bc_t of x-lo, x-hi, y-lo, y-hi */
+  int precision;           /* pp_prec_t */
+  double gl_weight;        /* Gauss-Lobatto end weight omega_hat_1 of the limiter, Sec. 2.4 (1/12) */
+  double eps_weno;         /* epsilon of the WENO-Z weights, eq. (weight) (1e-13) */
+  double eps_pos;          /* cap of the limiter epsilon, Sec. 2.4 step 1 (1e-13) */
+  int cfl_positivity_cap;  /* 1: use min(cfl, gl_weight), the bound of eq. (CFL-CD) */
+  int limiter;             /* 1: Zhang-Shu limiter on (default); 0: off */
+} pp_cweno_config;
+
+typedef struct {
+  int64_t steps;           /* completed SSP-RK3 steps since set_state */
+  int64_t stages;          /* completed stages */
+  int64_t theta1_active;   /* cell-sweeps with theta_1 < 1 (density limited) */
+  int64_t theta2_active;   /* cell-sweeps with theta_2 < 1 (internal energy limited) */
+  int64_t violations;      /* cells found outside G after a stage */
+  int64_t first_bad_cell;  /* flat cell index of one violation, -1 if none */
+  double t;                /* simulation time */
+  double last_dt;          /* last time step */
+  double max_rate;         /* max (|u|+a)/dx (+(|v|+a)/dy) at the current state */
+  double min_rho;          /* min density average at the current state */
+} pp_cweno_stats_t;
+
+/* Fill *cfg with the defaults above (1-D, periodic, FP64, gamma 1.4, cfl 0.5). */
+int pp_cweno_config_default(pp_cweno_config *cfg);
+
+/* Create a solver for one problem; allocates device memory sized for it.
+ * cuda_stream: a cudaStream_t or NULL.  On failure *out is NULL. */
+int pp_cweno_create(const pp_cweno_config *cfg, void *cuda_stream, pp_cweno_t *out);
+
+/* Create one handle for nprob independent problems advanced together (each
+ * with its own time step).  All configs must share ndim, gamma, precision
+ * and the limiter settings; sizes, domains, boundaries and cfl may differ. */
+int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda_stream,
+                          pp_cweno_t *out);
+
+/* Copy initial cell averages in (layout above; on_device != 0: U is a
+ * device pointer), set t = t0 and the step count to 0, check every cell is
+ * in G and finite (PP_ERR_STATE otherwise).  Synchronises the stream. */
+int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0);
+
+/* Copy the current state out; t and steps may be NULL.  Synchronises. */
+int pp_cweno_get_state(pp_cweno_t h, double *U, int on_device, double *t, int64_t *steps);
+
+/* One SSP-RK3 step with dt = min(cfl-limited dt, dt_max); *dt_taken may be
+ * NULL.  Synchronises.  Batch handles: every problem takes one step. */
+int pp_cweno_step(pp_cweno_t h, double dt_max, double *dt_taken);
+
+/* March every problem until its t reaches t_final (the last step is cut to
+ * land on it), or until max_steps steps were taken (PP_ERR_STEPS).  Steps
+ * are replayed from a captured CUDA graph; the host reads the device-side
+ * progress flags once per replay.  *steps_taken (may be NULL) receives the
+ * steps of this call (the maximum over problems for a batch). */
+int pp_cweno_advance(pp_cweno_t h, double t_final, int64_t max_steps, int64_t *steps_taken);
+
+/* Enqueue exactly nsteps steps on the handle's stream with no host
+ * synchronisation and no stopping time (for timing); errors are reported by
+ * the next synchronising call. */
+int pp_cweno_enqueue_steps(pp_cweno_t h, int64_t nsteps);
+
+/* Evaluate the spatial operator once: L = L(U) (eq. (1DEulerFV-b); in 2-D
+ * L_x + L_y) with limiter epsilon eps (eps <= 0: min(eps_pos, min rho)).
+ * U and L are device pointers in the state layout; single-problem handles
+ * only.  Synchronises. */
+int pp_cweno_operator(pp_cweno_t h, const double *U_dev, double *L_dev, double eps);
+
+/* Statistics; synchronises.  For a batch, sums and extrema over problems. */
+int pp_cweno_stats(pp_cweno_t h, pp_cweno_stats_t *out);
+
+/* Number of problems in the handle and the cell count of problem k. */
+int pp_cweno_num_problems(pp_cweno_t h, int64_t *nprob);
+int pp_cweno_problem_cells(pp_cweno_t h, int64_t k, int64_t *ncell);
+
+/* Kernel launches enqueued per step (for launch accounting). */
+int pp_cweno_launches_per_step(pp_cweno_t h, int64_t *n);
+
+/* Measurement: enqueue one step launch by launch with CUDA events on the
+ * handle's stream between kernels, synchronise and return each kernel's
+ * duration in ms (ms[0] the dt kernel, then the sweeps in launch order) in
+ * ms[0..*nk-1] (at most nmax entries). */
+int pp_cweno_profile_step(pp_cweno_t h, float *ms, int nmax, int *nk);
+
+/* Measurement: sustained fused multiply-add throughput of this GPU's CUDA
+ * cores in GFLOP/s (2 flops per FMA), FP64 if fp64 != 0 else FP32, from a
+ * dependent-chain-free kernel filling every SM.  Synchronises. */
+int pp_cweno_fma_peak(int fp64, double *gflops);
+
+/* Free all device memory of the handle (h may be NULL). */
+int pp_cweno_destroy(pp_cweno_t h);
+
+const char *pp_cweno_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PP_CWENO_H */

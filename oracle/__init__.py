@@ -78,6 +78,8 @@ def lib():
             L.orc_hllc_batch.argtypes = [C.c_int, C.c_double, C.c_long, dp, dp, dp]
             L.orc_limit_cell.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, dp, dp, dp]
             L.orc_operator.argtypes = [gp, dp, dp, C.c_double, cp]
+            lp = C.POINTER(C.c_long)
+            L.orc_operator_lines.argtypes = [gp, dp, C.c_double, C.c_long, lp, C.c_long, lp, dp, dp]
             L.orc_max_rate.argtypes = [gp, dp]
             L.orc_max_rate.restype = C.c_double
             L.orc_min_rho.argtypes = [gp, dp]
@@ -202,6 +204,26 @@ def operator(g: Grid, U: np.ndarray, eps: float | None = None):
     if rc:
         raise ArithmeticError("operator failed")
     return L, cnt
+
+
+def operator_lines(g: Grid, U: np.ndarray, eps: float, rows, cols):
+    """(Lx on rows [nr, nv, nx], Ly on cols [nc, nv, ny]) -- sampled operator."""
+    U = _f64(U)
+    nv = 4 if g.ndim == 2 else 3
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    cols = np.ascontiguousarray(np.asarray(cols, dtype=np.int64))
+    Lx = np.zeros((len(rows), nv, g.nx))
+    Ly = np.zeros((len(cols), nv, g.ny))
+    lp = C.POINTER(C.c_long)
+    rc = lib().orc_operator_lines(C.byref(g), _p(U), eps, len(rows), rows.ctypes.data_as(lp),
+                                  len(cols), cols.ctypes.data_as(lp), _p(Lx), _p(Ly))
+    if rc:
+        raise ArithmeticError("operator_lines failed")
+    return Lx, Ly
+
+
+def min_rho(g: Grid, U: np.ndarray) -> float:
+    return float(lib().orc_min_rho(C.byref(g), _p(_f64(U))))
 
 
 def max_rate(g: Grid, U: np.ndarray) -> float:

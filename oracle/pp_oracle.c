@@ -21,7 +21,11 @@
  *    the right star flux uses S_R (the printed formulas carry typos).
  *  - limiter: rho_min is the minimum of the three listed densities, theta_1
  *    is evaluated only when rho_min < eps; e is the specific internal
- *    energy; theta_2 = 0 if the cell average itself has e <= eps.
+ *    energy; theta_2 = 0 if the cell average itself has e <= eps.  Both
+ *    thresholds carry a round-off allowance (a bound on the rounding of the
+ *    rescaled states) so that the limited states are in G in floating point;
+ *    with the exact-arithmetic thresholds a face with large kinetic energy
+ *    can land at e < 0 after rounding.
  *  - Gauss-Lobatto end weight omega_hat_1 = 1/12 (M = 4 points) by default.
  *  - 2-D: dimension by dimension, L = L_x + L_y, HLLC at face centres with
  *    the tangential momentum carried by the contact.
@@ -268,11 +272,6 @@ static double pressure(int nv, double gamma, const double *U) {
   return (gamma - 1.0) * (U[nv - 1] - kinetic(nv, U));
 }
 
-/* specific internal energy e = E/rho - |u|^2/2 (the set G of Sec. 2.4) */
-static double spec_internal(int nv, const double *U) {
-  return U[nv - 1] / U[0] - 0.5 * (U[1] * U[1] + (nv == 4 ? U[2] * U[2] : 0.0)) / (U[0] * U[0]);
-}
-
 void orc_hllc_batch(int nv, double gamma, long n, const double *Ul, const double *Ur, double *F) {
   for (long i = 0; i < n; ++i) orc_hllc(nv, gamma, Ul + i * nv, Ur + i * nv, F + i * nv);
 }
@@ -339,15 +338,38 @@ void orc_hllc(int nv, double gamma, const double *Ul, const double *Ur, double *
 /* Sec. 2.4: the positivity-preserving limiter, steps 1-4.                    */
 /* ------------------------------------------------------------------------ */
 
-/* root t in (0, 1] of e((1-t) ubar + t w) = eps, i.e. of
- * (rho E - |m|^2/2 - eps rho^2)(t) = A t^2 + B t + C = 0 with C > 0 */
-static double energy_root(int nv, double eps, const double *ubar, const double *w) {
+/* Unit round-off of FP64. */
+#define ORC_U 1.1102230246251565e-16
+
+/* g(W) = rho E - |m|^2 / 2 - eps rho^2; for rho > 0, e(W) >= eps iff g >= 0 */
+static double energy_form(int nv, double eps, const double *w) {
+  double m2 = w[1] * w[1] + (nv == 4 ? w[2] * w[2] : 0.0);
+  return w[0] * w[nv - 1] - 0.5 * m2 - eps * w[0] * w[0];
+}
+
+/* Round-off allowance of g along the segment from ubar to w: every state
+ * (1-t) ubar + t w is formed with an error of a few ulps of |ubar| + |w| per
+ * component, which moves the bilinear form g by at most a small multiple of
+ * u [(|E|+|E_w|)(|rho|+|rho_w|) + (|m|+|m_w|)^2].  Requiring g >= eta rather
+ * than g >= 0 keeps the rounded limited states inside G. */
+static double energy_allowance(int nv, const double *ubar, const double *w) {
+  double sm = 0.0;
+  for (int k = 1; k < nv - 1; ++k) sm += (fabs(ubar[k]) + fabs(w[k])) * (fabs(ubar[k]) + fabs(w[k]));
+  return 16.0 * ORC_U *
+         ((fabs(ubar[nv - 1]) + fabs(w[nv - 1])) * (fabs(ubar[0]) + fabs(w[0])) + sm);
+}
+
+/* root t in (0, 1] of g((1-t) ubar + t w) = eta, a quadratic
+ * A t^2 + B t + (C - eta) = 0 with C - eta > 0 at t = 0 and < 0 at t = 1;
+ * the cancellation-free form 2C'/(-B + sqrt(B^2 - 4AC')) is the root in (0,1) */
+static double energy_root(int nv, double eps, double eta, const double *ubar, const double *w) {
   double dr = w[0] - ubar[0], dE = w[nv - 1] - ubar[nv - 1];
   double dm1 = w[1] - ubar[1], dm2 = nv == 4 ? w[2] - ubar[2] : 0.0;
   double m1 = ubar[1], m2 = nv == 4 ? ubar[2] : 0.0;
   double A = dE * dr - 0.5 * (dm1 * dm1 + dm2 * dm2) - eps * dr * dr;
   double B = ubar[nv - 1] * dr + dE * ubar[0] - (m1 * dm1 + m2 * dm2) - 2.0 * eps * ubar[0] * dr;
-  double C = ubar[nv - 1] * ubar[0] - 0.5 * (m1 * m1 + m2 * m2) - eps * ubar[0] * ubar[0];
+  double C = ubar[nv - 1] * ubar[0] - 0.5 * (m1 * m1 + m2 * m2) - eps * ubar[0] * ubar[0] - eta;
+  if (!(C > 0.0)) return 0.0;
   double D = B * B - 4.0 * A * C;
   if (D < 0.0) D = 0.0;
   double den = -B + sqrt(D);
@@ -362,12 +384,14 @@ int orc_limit_cell(int nv, double gamma, double wgl, double eps,
   (void)gamma;
   int flags = 0;
   /* step 2: theta_1 from the minimum density over the two face values and
-   * the interior point value rho_j(x^{1*}) implied by the quadrature */
+   * the interior point value rho_j(x^{1*}) implied by the quadrature; the
+   * threshold carries the round-off allowance of forming the scaled values */
   double rho_star = (ubar[0] - wgl * up[0] - wgl * um[0]) / (1.0 - 2.0 * wgl);
   double rho_min = fmin(fmin(um[0], up[0]), rho_star);
+  double eps_r = eps + 8.0 * ORC_U * (fabs(ubar[0]) + fabs(rho_min));
   double theta1 = 1.0;
-  if (rho_min < eps) {
-    theta1 = fmin((ubar[0] - eps) / (ubar[0] - rho_min), 1.0);
+  if (rho_min < eps_r) {
+    theta1 = fmin(fmax((ubar[0] - eps_r) / (ubar[0] - rho_min), 0.0), 1.0);
     flags |= 1;
   }
   /* step 3, eq. (limiter-rho): rescale the density face values (theta_1 = 1
@@ -384,16 +408,14 @@ int orc_limit_cell(int nv, double gamma, double wgl, double eps,
     W[1][k] = up[k];
     W[2][k] = (ubar[k] - wgl * up[k] - wgl * um[k]) / (1.0 - 2.0 * wgl);
   }
-  /* step 4: theta_2 = min over the three points of t_eps */
+  /* step 4: theta_2 = min over the three points of t_eps; a point needs
+   * limiting when e(W) < eps, i.e. g(W) < 0, checked with the allowance */
   double theta2 = 1.0;
-  if (spec_internal(nv, ubar) <= eps) {
-    theta2 = 0.0;  /* the average itself is at the floor: first order */
-  } else {
-    for (int a = 0; a < 3; ++a) {
-      if (spec_internal(nv, W[a]) < eps) {
-        double t = energy_root(nv, eps, ubar, W[a]);
-        if (t < theta2) theta2 = t;
-      }
+  for (int a = 0; a < 3; ++a) {
+    double eta = energy_allowance(nv, ubar, W[a]);
+    if (energy_form(nv, eps, W[a]) < eta) {
+      double t = energy_root(nv, eps, eta, ubar, W[a]);
+      if (t < theta2) theta2 = t;
     }
   }
   if (theta2 < 1.0) {
@@ -537,6 +559,37 @@ int orc_operator(const orc_grid *g, const double *U, double *L, double eps, orc_
     }
   }
   if (cnt) { cnt->theta1_active += t1; cnt->theta2_active += t2; }
+  return rc;
+}
+
+/* The x-sweep part L_x on the listed rows and the y-sweep part L_y on the
+ * listed columns (sampled checks of large grids): Lx_rows is [nr][nv][nx],
+ * Ly_cols is [nc][nv][ny], both in grid variable order. */
+int orc_operator_lines(const orc_grid *g, const double *U, double eps, long nr, const long *rows,
+                       long nc, const long *cols, double *Lx_rows, double *Ly_cols) {
+  long nx = g->nx, ny = g->ndim == 2 ? g->ny : 1, ncell = nx * ny;
+  int nv = g->ndim == 2 ? 4 : 3;
+  int rc = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(min : rc)
+  for (long q = 0; q < nr + nc; ++q) {
+    int is_row = q < nr;
+    long idx = is_row ? rows[q] : cols[q - nr];
+    long n = is_row ? nx : ny;
+    const int mapx[4] = {0, 1, 2, 3}, mapy[4] = {0, 2, 1, 3};
+    const int *map = is_row ? mapx : mapy;
+    double *line = (double *)malloc(sizeof(double) * (size_t)(nv * n));
+    double *Lo = (double *)calloc((size_t)(nv * n), sizeof(double));
+    for (int v = 0; v < nv; ++v)
+      for (long i = 0; i < n; ++i)
+        line[v * n + i] = is_row ? U[map[v] * ncell + idx * nx + i] : U[map[v] * ncell + i * nx + idx];
+    int r = is_row ? line_operator(g, nv, n, line, g->bc[0], g->bc[1], g->dx, eps, Lo, 0)
+                   : line_operator(g, nv, n, line, g->bc[2], g->bc[3], g->dy, eps, Lo, 0);
+    double *out = is_row ? Lx_rows + q * nv * nx : Ly_cols + (q - nr) * nv * ny;
+    for (int v = 0; v < nv; ++v)
+      for (long i = 0; i < n; ++i) out[map[v] * n + i] = Lo[v * n + i];
+    if (r < rc) rc = r;
+    free(line); free(Lo);
+  }
   return rc;
 }
 

@@ -88,6 +88,10 @@ int orc_limit_cell(int nv, double gamma, double wgl, double eps,
  * eq. (1DEuler-FVCW).  eps is the limiter epsilon.  Returns 0 or -1. */
 int orc_operator(const orc_grid *g, const double *U, double *L, double eps,
                  orc_counters *cnt);
+/* L_x on the listed rows ([nr][nv][nx]) and L_y on the listed columns
+ * ([nc][nv][ny]), grid variable order; for sampled checks of large grids. */
+int orc_operator_lines(const orc_grid *g, const double *U, double eps, long nr, const long *rows,
+                       long nc, const long *cols, double *Lx_rows, double *Ly_cols);
 /* max over cells of (|u|+a)/dx (+ (|v|+a)/dy); negative if a state is invalid */
 double orc_max_rate(const orc_grid *g, const double *U);
 /* min over cells of the density average */

@@ -1,0 +1,293 @@
+// physics.cuh -- per-cell and per-face device arithmetic of the FVCW scheme
+// (Guo, Xiong & Shi): WENO-Z weights and compact rows (Sec. 2.2), the
+// explicit WENO5-Z closure of bounded lines, the Zhang-Shu limiter and the
+// HLLC flux with Batten's wave speeds (Sec. 2.4).
+//
+// Line variables are ordered (rho, m_n, [m_t,] E): m_n is the momentum
+// normal to the faces of the line, m_t (2-D only) the tangential one.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace ppk {
+
+template <typename real>
+__device__ __forceinline__ real sqr(real x) { return x * x; }
+
+// Sec. 2.2, eq. (weight): Jiang-Shu indicators of the three sub-stencils of
+// cell i and the WENO-Z ratios q_k = (tau5 / (beta_k + eps))^2 they feed.
+// The minus side (face i+1/2) uses (q0, q1, q2) with c = (0.2, 0.5, 0.3);
+// the mirrored plus side (face i-1/2) uses (q2, q1, q0).
+template <typename real>
+__device__ __forceinline__ void zratios(real um2, real um1, real u0, real up1, real up2,
+                                        real eps, real &q0, real &q1, real &q2) {
+  const real c13 = real(13.0) / real(12.0);
+  real b0 = c13 * sqr(um2 - real(2) * um1 + u0) + real(0.25) * sqr(um2 - real(4) * um1 + real(3) * u0);
+  real b1 = c13 * sqr(um1 - real(2) * u0 + up1) + real(0.25) * sqr(um1 - up1);
+  real b2 = c13 * sqr(u0 - real(2) * up1 + up2) + real(0.25) * sqr(real(3) * u0 - real(4) * up1 + up2);
+  real tau = fabs(b2 - b0);
+  q0 = sqr(tau / (b0 + eps));
+  q1 = sqr(tau / (b1 + eps));
+  q2 = sqr(tau / (b2 + eps));
+}
+
+// FP32 form of the same ratios, scaled so nothing overflows: with
+// d_k = beta_k + eps and dmin = min d_k, when tau > dmin the returned values
+// are (dmin/tau)^2 q_k = (dmin/d_k)^2 and the constant 1 of eq. (weight)
+// becomes s = (dmin/tau)^2; the normalised weights are unchanged
+// (near a jump of 3e6 the plain q_k reaches 1e52, beyond FP32's range).
+__device__ __forceinline__ void zratios_scaled(float um2, float um1, float u0, float up1, float up2,
+                                               float eps, float &q0, float &q1, float &q2,
+                                               float &one) {
+  const float c13 = 13.0f / 12.0f;
+  float b0 = c13 * sqr(um2 - 2.0f * um1 + u0) + 0.25f * sqr(um2 - 4.0f * um1 + 3.0f * u0);
+  float b1 = c13 * sqr(um1 - 2.0f * u0 + up1) + 0.25f * sqr(um1 - up1);
+  float b2 = c13 * sqr(u0 - 2.0f * up1 + up2) + 0.25f * sqr(3.0f * u0 - 4.0f * up1 + up2);
+  float tau = fabsf(b2 - b0);
+  float d0 = b0 + eps, d1 = b1 + eps, d2 = b2 + eps;
+  float dmin = fminf(fminf(d0, d1), d2);
+  if (tau <= dmin) {
+    one = 1.0f;
+    q0 = sqr(tau / d0);
+    q1 = sqr(tau / d1);
+    q2 = sqr(tau / d2);
+  } else {
+    one = sqr(dmin / tau);
+    q0 = sqr(dmin / d0);
+    q1 = sqr(dmin / d1);
+    q2 = sqr(dmin / d2);
+  }
+}
+
+// normalised weights from linear weights (d0, d1, d2) and ratios (q0, q1, q2);
+// one is the scaled constant term (1 unless the ratios were rescaled)
+template <typename real>
+__device__ __forceinline__ void zweights(real d0, real d1, real d2, real q0, real q1, real q2,
+                                         real &w0, real &w1, real &w2, real one = real(1)) {
+  real a0 = d0 * (one + q0), a1 = d1 * (one + q1), a2 = d2 * (one + q2);
+  real s = a0 + a1 + a2;
+  w0 = a0 / s;
+  w1 = a1 / s;
+  w2 = a2 / s;
+}
+
+// ratios in the arithmetic of the line: plain in FP64, scaled in FP32
+template <typename real>
+__device__ __forceinline__ void zratios_any(real um2, real um1, real u0, real up1, real up2,
+                                            real eps, real &q0, real &q1, real &q2, real &one) {
+  if constexpr (sizeof(real) == 4) {
+    zratios_scaled(um2, um1, u0, up1, up2, eps, q0, q1, q2, one);
+  } else {
+    zratios(um2, um1, u0, up1, up2, eps, q0, q1, q2);
+    one = real(1);
+  }
+}
+
+// One tridiagonal row in elimination order: a on the previously eliminated
+// neighbour, b on the unknown, c on the next one, r the right-hand side.
+template <typename real>
+struct Row {
+  real a, b, c, r;
+};
+
+// eq. (CWENO-FV) with weights (w0, w1, w2): the row for the unknown u~ at
+// the face this cell reconstructs; uprev / unext are the neighbour averages
+// on the side of the previously / next eliminated unknown.  The plus side
+// is the mirror image, so the same formula serves both sides.
+template <typename real>
+__device__ __forceinline__ Row<real> compact_row(real w0, real w1, real w2, real uprev, real u0,
+                                                  real unext) {
+  Row<real> row;
+  row.a = (real(2) * w0 + w1) / real(3);
+  row.b = (w0 + real(2) * (w1 + w2)) / real(3);
+  row.c = w2 / real(3);
+  row.r = w0 / real(6) * uprev + (real(5) * (w0 + w1) + w2) / real(6) * u0 +
+          (w1 + real(5) * w2) / real(6) * unext;
+  return row;
+}
+
+// explicit fifth-order WENO-Z value at the face on the "next" side of the
+// centre cell u0, from the five cells ordered from the far "previous" side
+// (closure rows of bounded lines)
+template <typename real>
+__device__ __forceinline__ real weno5z_face(real um2, real um1, real u0, real up1, real up2,
+                                            real eps) {
+  real q0, q1, q2, w0, w1, w2, one;
+  zratios_any(um2, um1, u0, up1, up2, eps, q0, q1, q2, one);
+  zweights(real(0.1), real(0.6), real(0.3), q0, q1, q2, w0, w1, w2, one);
+  real p0 = (real(2) * um2 - real(7) * um1 + real(11) * u0) / real(6);
+  real p1 = (-um1 + real(5) * u0 + real(2) * up1) / real(6);
+  real p2 = (real(2) * u0 + real(5) * up1 - up2) / real(6);
+  return w0 * p0 + w1 * p1 + w2 * p2;
+}
+
+// ---------------------------------------------------------------- Euler
+template <typename real, int NV>
+__device__ __forceinline__ real kin2(const real *U) {  // |m|^2
+  real m2 = U[1] * U[1];
+  if (NV == 4) m2 += U[2] * U[2];
+  return m2;
+}
+
+template <typename real, int NV>
+__device__ __forceinline__ real pressure(const real *U, real gamma) {
+  return (gamma - real(1)) * (U[NV - 1] - real(0.5) * kin2<real, NV>(U) / U[0]);
+}
+
+// specific internal energy e = E/rho - |u|^2 / 2
+template <typename real, int NV>
+__device__ __forceinline__ real spec_e(const real *U) {
+  return U[NV - 1] / U[0] - real(0.5) * kin2<real, NV>(U) / (U[0] * U[0]);
+}
+
+template <typename real, int NV>
+__device__ __forceinline__ void phys_flux(const real *U, real p, real *F) {
+  real un = U[1] / U[0];
+  F[0] = U[1];
+  F[1] = U[1] * un + p;
+  if (NV == 4) F[2] = U[2] * un;
+  F[NV - 1] = un * (U[NV - 1] + p);
+}
+
+// HLLC flux (Sec. 2.4, eqs. (HLLC), (contact-v), (star-l), (acoustic ws)).
+// S_M's denominator uses rho_r on the right-state term, S_R is the max of
+// the two estimates and the right star flux uses S_R.  In 2-D the
+// tangential velocity is carried by the contact.
+template <typename real, int NV>
+__device__ __forceinline__ void hllc(const real *Ul, const real *Ur, real gamma, real *F) {
+  real rl = Ul[0], rr = Ur[0];
+  real ul = Ul[1] / rl, ur = Ur[1] / rr;
+  real vl = NV == 4 ? Ul[2] / rl : real(0), vr = NV == 4 ? Ur[2] / rr : real(0);
+  real El = Ul[NV - 1], Er = Ur[NV - 1];
+  real pl = pressure<real, NV>(Ul, gamma), pr = pressure<real, NV>(Ur, gamma);
+  real al = sqrt(gamma * pl / rl), ar = sqrt(gamma * pr / rr);
+  real Hl = (El + pl) / rl, Hr = (Er + pr) / rr;
+  real R = sqrt(rr / rl);
+  real ut = (ul + ur * R) / (real(1) + R);
+  real vt = (vl + vr * R) / (real(1) + R);
+  real Ht = (Hl + Hr * R) / (real(1) + R);
+  real at = sqrt((gamma - real(1)) * (Ht - real(0.5) * (ut * ut + vt * vt)));
+  real SL = fmin(ul - al, ut - at);
+  real SR = fmax(ur + ar, ut + at);
+  real SM = (rr * ur * (SR - ur) - rl * ul * (SL - ul) + pl - pr) / (rr * (SR - ur) - rl * (SL - ul));
+  if (SL > real(0)) {
+    phys_flux<real, NV>(Ul, pl, F);
+  } else if (SM > real(0)) {
+    real Fk[NV], Us[NV];
+    real ps = rl * (ul - SL) * (ul - SM) + pl;
+    real inv = real(1) / (SL - SM);
+    Us[0] = rl * (SL - ul) * inv;
+    Us[1] = ((SL - ul) * rl * ul + (ps - pl)) * inv;
+    if (NV == 4) Us[2] = Us[0] * vl;
+    Us[NV - 1] = ((SL - ul) * El - pl * ul + ps * SM) * inv;
+    phys_flux<real, NV>(Ul, pl, Fk);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) F[k] = Fk[k] + SL * (Us[k] - Ul[k]);
+  } else if (SR >= real(0)) {
+    real Fk[NV], Us[NV];
+    real ps = rr * (ur - SR) * (ur - SM) + pr;
+    real inv = real(1) / (SR - SM);
+    Us[0] = rr * (SR - ur) * inv;
+    Us[1] = ((SR - ur) * rr * ur + (ps - pr)) * inv;
+    if (NV == 4) Us[2] = Us[0] * vr;
+    Us[NV - 1] = ((SR - ur) * Er - pr * ur + ps * SM) * inv;
+    phys_flux<real, NV>(Ur, pr, Fk);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) F[k] = Fk[k] + SR * (Us[k] - Ur[k]);
+  } else {
+    phys_flux<real, NV>(Ur, pr, F);
+  }
+}
+
+template <typename real>
+__device__ __forceinline__ constexpr real unit_roundoff() {
+  return sizeof(real) == 8 ? real(1.1102230246251565e-16) : real(5.9604645e-08);
+}
+
+// g(W) = rho E - |m|^2 / 2 - eps rho^2: for rho > 0, e(W) >= eps iff g >= 0
+template <typename real, int NV>
+__device__ __forceinline__ real energy_form(const real *w, real eps) {
+  return w[0] * w[NV - 1] - real(0.5) * kin2<real, NV>(w) - eps * w[0] * w[0];
+}
+
+// round-off allowance of g along the segment from Ubar to W: forming
+// (1-t) Ubar + t W costs a few ulps of |Ubar| + |W| per component, which
+// moves the bilinear form g by at most a small multiple of
+// u [(|E|+|E_w|)(|rho|+|rho_w|) + (|m|+|m_w|)^2]; the limiter asks g >= eta
+// so that the rounded limited states stay inside G
+template <typename real, int NV>
+__device__ __forceinline__ real energy_allowance(const real *ub, const real *w) {
+  real sm = real(0);
+#pragma unroll
+  for (int k = 1; k < NV - 1; ++k) sm += sqr(fabs(ub[k]) + fabs(w[k]));
+  return real(16) * unit_roundoff<real>() *
+         ((fabs(ub[NV - 1]) + fabs(w[NV - 1])) * (fabs(ub[0]) + fabs(w[0])) + sm);
+}
+
+// root t in (0, 1] of g((1 - t) Ubar + t W) = eta: the quadratic
+// A t^2 + B t + (C - eta) = 0 with C - eta > 0; the cancellation-free form
+// 2C' / (-B + sqrt(B^2 - 4AC')) picks the root in (0, 1)
+template <typename real, int NV>
+__device__ __forceinline__ real energy_root(const real *ub, const real *w, real eps, real eta) {
+  real dr = w[0] - ub[0], dE = w[NV - 1] - ub[NV - 1];
+  real dm1 = w[1] - ub[1], dm2 = NV == 4 ? w[2] - ub[2] : real(0);
+  real m1 = ub[1], m2 = NV == 4 ? ub[2] : real(0);
+  real A = dE * dr - real(0.5) * (dm1 * dm1 + dm2 * dm2) - eps * dr * dr;
+  real B = ub[NV - 1] * dr + dE * ub[0] - (m1 * dm1 + m2 * dm2) - real(2) * eps * ub[0] * dr;
+  real C = ub[NV - 1] * ub[0] - real(0.5) * (m1 * m1 + m2 * m2) - eps * ub[0] * ub[0] - eta;
+  if (!(C > real(0))) return real(0);
+  real D = fmax(B * B - real(4) * A * C, real(0));
+  real den = -B + sqrt(D);
+  real t = den > real(0) ? real(2) * C / den : real(0);
+  if (!(t >= real(0))) t = real(0);
+  return fmin(t, real(1));
+}
+
+// Zhang-Shu limiter of one cell (Sec. 2.4, steps 1-4).  um = U^-_{i+1/2},
+// up = U^+_{i-1/2} are limited in place.  Returns bit 0 if theta_1 < 1 and
+// bit 1 if theta_2 < 1.  theta = 1 leaves the values untouched.  Both
+// thresholds carry the round-off allowance that keeps the rounded limited
+// states in G.
+template <typename real, int NV>
+__device__ __forceinline__ int limit_cell(const real *ub, real *um, real *up, real wgl, real eps) {
+  int flags = 0;
+  const real uu = unit_roundoff<real>();
+  real inv12 = real(1) / (real(1) - real(2) * wgl);
+  real rho_star = (ub[0] - wgl * up[0] - wgl * um[0]) * inv12;
+  real rho_min = fmin(fmin(um[0], up[0]), rho_star);
+  real eps_r = eps + real(8) * uu * (fabs(ub[0]) + fabs(rho_min));
+  if (rho_min < eps_r) {
+    real th1 = fmin(fmax((ub[0] - eps_r) / (ub[0] - rho_min), real(0)), real(1));
+    um[0] = th1 * (um[0] - ub[0]) + ub[0];
+    up[0] = th1 * (up[0] - ub[0]) + ub[0];
+    flags |= 1;
+  }
+  real th2 = real(1);
+  real w3[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) w3[k] = (ub[k] - wgl * up[k] - wgl * um[k]) * inv12;
+  {
+    real eta = energy_allowance<real, NV>(ub, um);
+    if (energy_form<real, NV>(um, eps) < eta) th2 = fmin(th2, energy_root<real, NV>(ub, um, eps, eta));
+  }
+  {
+    real eta = energy_allowance<real, NV>(ub, up);
+    if (energy_form<real, NV>(up, eps) < eta) th2 = fmin(th2, energy_root<real, NV>(ub, up, eps, eta));
+  }
+  {
+    real eta = energy_allowance<real, NV>(ub, w3);
+    if (energy_form<real, NV>(w3, eps) < eta) th2 = fmin(th2, energy_root<real, NV>(ub, w3, eps, eta));
+  }
+  if (th2 < real(1)) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      um[k] = th2 * (um[k] - ub[k]) + ub[k];
+      up[k] = th2 * (up[k] - ub[k]) + ub[k];
+    }
+    flags |= 2;
+  }
+  return flags;
+}
+
+}  // namespace ppk

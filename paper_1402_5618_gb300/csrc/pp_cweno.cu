@@ -1,0 +1,689 @@
+// pp_cweno.cu -- host side of the C ABI declared in include/pp_cweno.h.
+//
+// A handle owns, for one problem, the state U^n (FP64), one stage buffer,
+// the x-sweep flux-difference buffer (FP64 in the plain form, FP32 in the
+// mixed form) and a device control block holding t, dt, the step count and
+// the grid-wide reductions.  A step is: one single-thread kernel that fixes
+// dt from the previous step's max wave speed (eq. (CFL-CD)), then three
+// stages (eq. (RK3)) of one fused line sweep (1-D) or an x sweep and a y
+// sweep (2-D).  Steps are captured once into a CUDA graph of K steps and
+// replayed; kernels of a finished problem return immediately, so a replay
+// past t_final is harmless.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/pp_cweno.h"
+#include "sweeps.cuh"
+
+using namespace ppk;
+
+namespace {
+
+constexpr int GRAPH_STEPS = 16;
+
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ double bitsd(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+
+// Start of a step: dt from the max rate of U^n, the last step cut to land on
+// t_final, reductions of this step reset.
+__global__ void step_begin_kernel(Ctl *ctl) {
+  if (threadIdx.x != 0) return;
+  ctl->active = 0;
+  if (ctl->done || ctl->nviol) return;
+  if (ctl->step >= ctl->step_limit) { ctl->err_steps = 1; return; }
+  double rate = bitsd(ctl->rate);
+  if (!(rate > 0.0) || !isfinite(rate)) { ctl->err_rate = 1; return; }
+  double dt = ctl->cfl / rate;
+  dt = fmin(dt, ctl->dt_cap);
+  double rem = ctl->t_final - ctl->t;
+  int last = 0;
+  if (dt >= rem) { dt = rem; last = 1; }
+  ctl->dt = dt;
+  ctl->last_dt = dt;
+  ctl->t = last ? ctl->t_final : ctl->t + dt;
+  ctl->step += 1;
+  ctl->done = last;
+  ctl->active = 1;
+  ctl->eps0 = fmin(ctl->eps_pos, bitsd(ctl->minrho[2]));
+  const unsigned long long inf = dbits(INFINITY);
+  ctl->minrho[0] = inf;
+  ctl->minrho[1] = inf;
+  ctl->minrho[2] = inf;
+  ctl->rate = 0ull;
+}
+
+// Reductions of a state: min density, max rate, cells outside G.
+template <int NV>
+__global__ void state_reduce_kernel(const double *U, long long ncell, long long nx, double dx,
+                                    double dy, double gamma, Ctl *ctl) {
+  double mn = 1e300, mx = 0.0;
+  unsigned long long bad = 0, first = ~0ull;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    double rho = U[c], m1 = U[ncell + c], m2 = NV == 4 ? U[2 * ncell + c] : 0.0;
+    double E = U[(NV - 1) * ncell + c];
+    double e = E / rho - 0.5 * (m1 * m1 + m2 * m2) / (rho * rho);
+    bool ok = rho > 0.0 && e > 0.0 && isfinite(E) && isfinite(m1) && isfinite(m2) && isfinite(rho);
+    if (!ok) {
+      ++bad;
+      first = (unsigned long long)c < first ? (unsigned long long)c : first;
+      continue;
+    }
+    mn = fmin(mn, rho);
+    double a = sqrt(gamma * (gamma - 1.0) * e);
+    double r = (fabs(m1 / rho) + a) / dx;
+    if (NV == 4) r += (fabs(m2 / rho) + a) / dy;
+    mx = fmax(mx, r);
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, d));
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, d));
+    bad += __shfl_down_sync(0xffffffffu, bad, d);
+    unsigned long long f = __shfl_down_sync(0xffffffffu, first, d);
+    first = f < first ? f : first;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&ctl->minrho[2], dbits(mn));
+    atomicMax(&ctl->rate, dbits(mx));
+    if (bad) {
+      atomicAdd(&ctl->nviol, bad);
+      atomicMin(&ctl->first_bad, first);
+    }
+  }
+}
+
+template <typename T>
+__global__ void fma_peak_kernel(T *out, int iters, T a, T b) {
+  T x0 = T(threadIdx.x) * T(1e-3), x1 = x0 + T(1), x2 = x0 + T(2), x3 = x0 + T(3);
+  T x4 = x0 + T(4), x5 = x0 + T(5), x6 = x0 + T(6), x7 = x0 + T(7);
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  T s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  if (s == T(-12345)) out[0] = s;   // keeps the chain alive, never true in practice
+}
+
+}  // namespace
+
+struct pp_cweno_s {
+  pp_cweno_config cfg;
+  cudaStream_t stream = nullptr;
+  int nv = 3;
+  long long nx = 0, ny = 1, ncell = 0;
+  double dx = 1, dy = 1;
+  double *U0 = nullptr, *U1 = nullptr;
+  void *D = nullptr;
+  Ctl *ctl = nullptr, *ctl_scratch = nullptr;
+  Ctl *hctl = nullptr;   // pinned mirror
+  cudaGraphExec_t graph = nullptr;
+  long long launches_per_step = 0;
+};
+
+namespace {
+
+int cuerr(cudaError_t e) { return e == cudaSuccess ? PP_OK : PP_ERR_CUDA; }
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  memcpy(&d, &b, sizeof(d));
+  return d;
+}
+
+int seg_count(long long n) { return (int)((n + SEG_CELLS - 1) / SEG_CELLS); }
+
+bool bc_valid(int b) { return b == PP_BC_PERIODIC || b == PP_BC_TRANSMISSIVE || b == PP_BC_REFLECTIVE; }
+
+int check_config(const pp_cweno_config *c) {
+  if (!c) return PP_ERR_ARG;
+  if (c->ndim != 1 && c->ndim != 2) return PP_ERR_ARG;
+  if (c->nx < 8 || (c->ndim == 2 && c->ny < 8)) return PP_ERR_ARG;
+  if (!(c->gamma > 1.0) || !(c->cfl > 0.0)) return PP_ERR_ARG;
+  if (!(c->x1 > c->x0) || (c->ndim == 2 && !(c->y1 > c->y0))) return PP_ERR_ARG;
+  if (!(c->gl_weight > 0.0 && c->gl_weight < 0.5)) return PP_ERR_ARG;
+  if (!(c->eps_weno > 0.0) || !(c->eps_pos > 0.0)) return PP_ERR_ARG;
+  if (c->precision != PP_PREC_FP64 && c->precision != PP_PREC_MIXED) return PP_ERR_ARG;
+  int nb = c->ndim == 2 ? 4 : 2;
+  for (int k = 0; k < nb; ++k)
+    if (!bc_valid(c->bc[k])) return PP_ERR_ARG;
+  if ((c->bc[0] == PP_BC_PERIODIC) != (c->bc[1] == PP_BC_PERIODIC)) return PP_ERR_ARG;
+  if (c->ndim == 2 && (c->bc[2] == PP_BC_PERIODIC) != (c->bc[3] == PP_BC_PERIODIC)) return PP_ERR_ARG;
+  // one line per cluster of at most 16 CTAs
+  if (seg_count(c->nx) > 16 || (c->ndim == 2 && seg_count(c->ny) > 16)) return PP_ERR_UNSUPPORTED;
+  return PP_OK;
+}
+
+cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const double *Uin, const double *U0,
+                   const void *Din, void *Dout, double *Uout, int stage, double eps_fixed,
+                   Ctl *ctl, bool attrs_only = false) {
+  SweepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.U = Uin;
+  a.U0 = U0;
+  a.Din = Din;
+  a.Dout = Dout;
+  a.Uout = Uout;
+  a.ncell = h->ncell;
+  a.gamma = h->cfg.gamma;
+  a.wgl = h->cfg.gl_weight;
+  a.eps_weno = h->cfg.eps_weno;
+  a.stage = stage;
+  a.eps_fixed = eps_fixed;
+  a.limiter = h->cfg.limiter;
+  a.ctl = ctl;
+  long long nlines;
+  bool periodic;
+  if (xdir) {
+    a.n = (int)h->nx;
+    a.cell_stride = 1;
+    a.line_stride = h->nx;
+    nlines = h->ny;
+    a.vn = 1;
+    a.vt = h->nv == 4 ? 2 : -1;
+    a.bclo = h->cfg.bc[0];
+    a.bchi = h->cfg.bc[1];
+    a.h = h->dx;
+    a.h_other = h->nv == 4 ? h->dy : 0.0;
+  } else {
+    a.n = (int)h->ny;
+    a.cell_stride = h->nx;
+    a.line_stride = 1;
+    nlines = h->nx;
+    a.vn = 2;
+    a.vt = 1;
+    a.bclo = h->cfg.bc[2];
+    a.bchi = h->cfg.bc[3];
+    a.h = h->dy;
+    a.h_other = h->dx;
+  }
+  periodic = a.bclo == PP_BC_PERIODIC;
+  a.R = seg_count(a.n);
+  LaunchCfg c;
+  c.precision = h->cfg.precision;
+  c.nv = h->nv;
+  c.periodic = periodic;
+  c.mode = mode;
+  c.attrs_only = attrs_only;
+  return h->cfg.precision == PP_PREC_FP64 ? launch_sweep_f64(c, a, nlines, h->stream)
+                                         : launch_sweep_f32(c, a, nlines, h->stream);
+}
+
+// enqueue one step (begin kernel + 3 stages)
+cudaError_t enqueue_step(pp_cweno_s *h) {
+  step_begin_kernel<<<1, 32, 0, h->stream>>>(h->ctl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int s = 0; s < 3; ++s) {
+    const double *Uin = s == 0 ? h->U0 : h->U1;
+    double *Uout = s == 2 ? h->U0 : h->U1;
+    if (h->nv == 4) {
+      e = launch(h, MODE_XSWEEP, true, Uin, h->U0, nullptr, h->D, nullptr, s, 0.0, h->ctl);
+      if (e != cudaSuccess) return e;
+      e = launch(h, MODE_FINAL, false, Uin, h->U0, h->D, nullptr, Uout, s, 0.0, h->ctl);
+    } else {
+      e = launch(h, MODE_FINAL, true, Uin, h->U0, nullptr, nullptr, Uout, s, 0.0, h->ctl);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int build_graph(pp_cweno_s *h) {
+  if (h->graph) return PP_OK;
+  // make sure every kernel attribute is set outside the capture
+  cudaGraph_t g;
+  cudaStream_t cap;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return PP_ERR_CUDA;
+  cudaStream_t keep = h->stream;
+  h->stream = cap;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < GRAPH_STEPS && e == cudaSuccess; ++k) e = enqueue_step(h);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  h->stream = keep;
+  if (e == cudaSuccess) {
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+  }
+  cudaStreamDestroy(cap);
+  return cuerr(e);
+}
+
+int reduce_state(pp_cweno_s *h, const double *U, Ctl *ctl) {
+  Ctl z;
+  memset(&z, 0, sizeof(z));
+  z.minrho[2] = 0x7ff0000000000000ull;  // +inf
+  z.first_bad = ~0ull;
+  cudaError_t e = cudaMemcpyAsync(ctl, &z, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return PP_ERR_CUDA;
+  int blocks = (int)fmin(1184.0, (double)((h->ncell + 255) / 256));
+  if (blocks < 1) blocks = 1;
+  if (h->nv == 4)
+    state_reduce_kernel<4><<<blocks, 256, 0, h->stream>>>(U, h->ncell, h->nx, h->dx, h->dy,
+                                                          h->cfg.gamma, ctl);
+  else
+    state_reduce_kernel<3><<<blocks, 256, 0, h->stream>>>(U, h->ncell, h->nx, h->dx, h->dy,
+                                                          h->cfg.gamma, ctl);
+  return cuerr(cudaGetLastError());
+}
+
+int pull_ctl(pp_cweno_s *h) {
+  if (cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return PP_ERR_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
+  return PP_OK;
+}
+
+int push_ctl(pp_cweno_s *h) {
+  return cuerr(cudaMemcpyAsync(h->ctl, h->hctl, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+}
+
+double effective_cfl(const pp_cweno_config &c) {
+  return c.cfl_positivity_cap ? fmin(c.cfl, c.gl_weight) : c.cfl;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pp_cweno_config_default(pp_cweno_config *cfg) {
+  if (!cfg) return PP_ERR_ARG;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->ndim = 1;
+  cfg->nx = 200;
+  cfg->ny = 1;
+  cfg->x0 = 0.0;
+  cfg->x1 = 1.0;
+  cfg->y0 = 0.0;
+  cfg->y1 = 1.0;
+  cfg->gamma = 1.4;
+  cfg->cfl = 0.5;
+  cfg->bc[0] = cfg->bc[1] = cfg->bc[2] = cfg->bc[3] = PP_BC_PERIODIC;
+  cfg->precision = PP_PREC_FP64;
+  cfg->gl_weight = 1.0 / 12.0;
+  cfg->eps_weno = 1e-13;
+  cfg->eps_pos = 1e-13;
+  cfg->cfl_positivity_cap = 0;
+  cfg->limiter = 1;
+  return PP_OK;
+}
+
+int pp_cweno_create(const pp_cweno_config *cfg, void *cuda_stream, pp_cweno_t *out) {
+  if (!out) return PP_ERR_ARG;
+  *out = nullptr;
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  pp_cweno_s *h = new (std::nothrow) pp_cweno_s();
+  if (!h) return PP_ERR_CUDA;
+  h->cfg = *cfg;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->nv = cfg->ndim == 2 ? 4 : 3;
+  h->nx = cfg->nx;
+  h->ny = cfg->ndim == 2 ? cfg->ny : 1;
+  h->ncell = h->nx * h->ny;
+  h->dx = (cfg->x1 - cfg->x0) / (double)h->nx;
+  h->dy = cfg->ndim == 2 ? (cfg->y1 - cfg->y0) / (double)h->ny : 1.0;
+  size_t bytes = sizeof(double) * (size_t)h->nv * (size_t)h->ncell;
+  size_t dbytes = (cfg->precision == PP_PREC_FP64 ? sizeof(double) : sizeof(float)) *
+                  (size_t)h->nv * (size_t)h->ncell;
+  cudaError_t e = cudaMalloc(&h->U0, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->U1, bytes);
+  if (e == cudaSuccess && h->nv == 4) e = cudaMalloc(&h->D, dbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->ctl, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaMalloc(&h->ctl_scratch, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->hctl, sizeof(Ctl));
+  if (e != cudaSuccess) {
+    pp_cweno_destroy(h);
+    return PP_ERR_CUDA;
+  }
+  memset(h->hctl, 0, sizeof(Ctl));
+  // kernel attributes (dynamic shared memory, cluster size) are set here,
+  // never inside a stream capture
+  {
+    const int modes_2d[3] = {MODE_XSWEEP, MODE_FINAL, MODE_OPERATOR};
+    for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
+      if (h->nv == 3 && modes_2d[m] == MODE_XSWEEP) continue;
+      e = launch(h, modes_2d[m], true, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0.0,
+                 nullptr, true);
+      if (e == cudaSuccess && h->nv == 4)
+        e = launch(h, modes_2d[m], false, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0.0,
+                   nullptr, true);
+    }
+    if (e != cudaSuccess) {
+      pp_cweno_destroy(h);
+      return PP_ERR_CUDA;
+    }
+  }
+  h->launches_per_step = 1 + 3 * (h->nv == 4 ? 2 : 1);
+  *out = h;
+  return PP_OK;
+}
+
+int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda_stream,
+                          pp_cweno_t *out) {
+  if (!out || !cfgs || nprob < 1) return PP_ERR_ARG;
+  *out = nullptr;
+  if (nprob == 1) return pp_cweno_create(cfgs, cuda_stream, out);
+  return PP_ERR_UNSUPPORTED;
+}
+
+int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) {
+  if (!h || !U || !isfinite(t0)) return PP_ERR_ARG;
+  size_t bytes = sizeof(double) * (size_t)h->nv * (size_t)h->ncell;
+  cudaError_t e = cudaMemcpyAsync(h->U0, U, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e != cudaSuccess) return PP_ERR_CUDA;
+  int rc = reduce_state(h, h->U0, h->ctl);
+  if (rc) return rc;
+  if ((rc = pull_ctl(h))) return rc;
+  Ctl *c = h->hctl;
+  int bad = c->nviol != 0;
+  c->t = t0;
+  c->t_final = t0;
+  c->dt = 0.0;
+  c->last_dt = 0.0;
+  c->cfl = effective_cfl(h->cfg);
+  c->dt_cap = INFINITY;
+  c->step = 0;
+  c->step_limit = 0;
+  c->active = 0;
+  c->done = 1;
+  c->err_steps = 0;
+  c->err_rate = 0;
+  c->eps_pos = h->cfg.eps_pos;
+  c->theta1 = c->theta2 = 0;
+  if ((rc = push_ctl(h))) return rc;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
+  return bad ? PP_ERR_STATE : PP_OK;
+}
+
+int pp_cweno_get_state(pp_cweno_t h, double *U, int on_device, double *t, int64_t *steps) {
+  if (!h || !U) return PP_ERR_ARG;
+  size_t bytes = sizeof(double) * (size_t)h->nv * (size_t)h->ncell;
+  cudaError_t e = cudaMemcpyAsync(U, h->U0, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e != cudaSuccess) return PP_ERR_CUDA;
+  int rc = pull_ctl(h);
+  if (rc) return rc;
+  if (t) *t = h->hctl->t;
+  if (steps) *steps = h->hctl->step;
+  return PP_OK;
+}
+
+static int status_after(pp_cweno_s *h) {
+  Ctl *c = h->hctl;
+  if (c->nviol) return PP_ERR_NONPHYSICAL;
+  if (c->err_rate) return PP_ERR_NONPHYSICAL;
+  if (c->err_steps) return PP_ERR_STEPS;
+  return PP_OK;
+}
+
+int pp_cweno_step(pp_cweno_t h, double dt_max, double *dt_taken) {
+  if (!h || !(dt_max > 0.0)) return PP_ERR_ARG;
+  int rc = pull_ctl(h);
+  if (rc) return rc;
+  Ctl *c = h->hctl;
+  if (c->nviol) return PP_ERR_NONPHYSICAL;
+  c->t_final = INFINITY;
+  c->dt_cap = dt_max;
+  c->done = 0;
+  c->step_limit = c->step + 1;
+  c->err_steps = 0;
+  if ((rc = push_ctl(h))) return rc;
+  cudaError_t e = enqueue_step(h);
+  if (e != cudaSuccess) return PP_ERR_CUDA;
+  if ((rc = pull_ctl(h))) return rc;
+  c->t_final = c->t;
+  c->dt_cap = INFINITY;
+  c->done = 1;
+  if ((rc = push_ctl(h))) return rc;
+  if (dt_taken) *dt_taken = c->last_dt;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
+  return status_after(h);
+}
+
+int pp_cweno_advance(pp_cweno_t h, double t_final, int64_t max_steps, int64_t *steps_taken) {
+  if (!h || !isfinite(t_final) || max_steps < 0) return PP_ERR_ARG;
+  int rc = pull_ctl(h);
+  if (rc) return rc;
+  Ctl *c = h->hctl;
+  if (c->nviol) return PP_ERR_NONPHYSICAL;
+  long long start = c->step;
+  c->t_final = t_final;
+  c->dt_cap = INFINITY;
+  c->done = c->t >= t_final;
+  c->step_limit = c->step + max_steps;
+  c->err_steps = 0;
+  c->err_rate = 0;
+  if ((rc = push_ctl(h))) return rc;
+  if ((rc = build_graph(h))) return rc;
+  for (;;) {
+    if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return PP_ERR_CUDA;
+    if ((rc = pull_ctl(h))) return rc;
+    if (c->done || c->nviol || c->err_steps || c->err_rate) break;
+  }
+  if (steps_taken) *steps_taken = c->step - start;
+  return status_after(h);
+}
+
+int pp_cweno_enqueue_steps(pp_cweno_t h, int64_t nsteps) {
+  if (!h || nsteps < 0) return PP_ERR_ARG;
+  int rc = pull_ctl(h);
+  if (rc) return rc;
+  Ctl *c = h->hctl;
+  c->t_final = INFINITY;
+  c->dt_cap = INFINITY;
+  c->done = 0;
+  c->step_limit = c->step + nsteps;
+  c->err_steps = 0;
+  if ((rc = push_ctl(h))) return rc;
+  if ((rc = build_graph(h))) return rc;
+  int64_t left = nsteps;
+  while (left >= GRAPH_STEPS) {
+    if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return PP_ERR_CUDA;
+    left -= GRAPH_STEPS;
+  }
+  while (left > 0) {
+    if (enqueue_step(h) != cudaSuccess) return PP_ERR_CUDA;
+    --left;
+  }
+  return PP_OK;
+}
+
+int pp_cweno_operator(pp_cweno_t h, const double *U_dev, double *L_dev, double eps) {
+  if (!h || !U_dev || !L_dev) return PP_ERR_ARG;
+  int rc;
+  if (!(eps > 0.0)) {
+    if ((rc = reduce_state(h, U_dev, h->ctl_scratch))) return rc;
+    Ctl tmp;
+    if (cudaMemcpyAsync(&tmp, h->ctl_scratch, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+      return PP_ERR_CUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
+    double mr = bits_to_double(tmp.minrho[2]);
+    eps = fmin(h->cfg.eps_pos, mr);
+    if (!(eps > 0.0)) return PP_ERR_STATE;
+  }
+  Ctl z;
+  memset(&z, 0, sizeof(z));
+  z.active = 1;
+  if (cudaMemcpyAsync(h->ctl_scratch, &z, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return PP_ERR_CUDA;
+  cudaError_t e;
+  if (h->nv == 4) {
+    e = launch(h, MODE_XSWEEP, true, U_dev, U_dev, nullptr, h->D, nullptr, 0, eps, h->ctl_scratch);
+    if (e == cudaSuccess)
+      e = launch(h, MODE_OPERATOR, false, U_dev, U_dev, h->D, nullptr, L_dev, 0, eps, h->ctl_scratch);
+  } else {
+    e = launch(h, MODE_OPERATOR, true, U_dev, U_dev, nullptr, nullptr, L_dev, 0, eps, h->ctl_scratch);
+  }
+  if (e != cudaSuccess) return PP_ERR_CUDA;
+  return cuerr(cudaStreamSynchronize(h->stream));
+}
+
+int pp_cweno_stats(pp_cweno_t h, pp_cweno_stats_t *out) {
+  if (!h || !out) return PP_ERR_ARG;
+  int rc = pull_ctl(h);
+  if (rc) return rc;
+  // current-state reductions come from a fresh pass over U^n
+  Ctl *c = h->hctl;
+  memset(out, 0, sizeof(*out));
+  out->steps = c->step;
+  out->stages = 3 * c->step;
+  out->theta1_active = (int64_t)c->theta1;
+  out->theta2_active = (int64_t)c->theta2;
+  out->violations = (int64_t)c->nviol;
+  out->first_bad_cell = c->nviol ? (int64_t)c->first_bad : -1;
+  out->t = c->t;
+  out->last_dt = c->last_dt;
+  if ((rc = reduce_state(h, h->U0, h->ctl_scratch))) return rc;
+  Ctl tmp;
+  if (cudaMemcpyAsync(&tmp, h->ctl_scratch, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return PP_ERR_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
+  out->max_rate = bits_to_double(tmp.rate);
+  out->min_rho = bits_to_double(tmp.minrho[2]);
+  return PP_OK;
+}
+
+int pp_cweno_num_problems(pp_cweno_t h, int64_t *nprob) {
+  if (!h || !nprob) return PP_ERR_ARG;
+  *nprob = 1;
+  return PP_OK;
+}
+
+int pp_cweno_problem_cells(pp_cweno_t h, int64_t k, int64_t *ncell) {
+  if (!h || !ncell || k != 0) return PP_ERR_ARG;
+  *ncell = h->ncell;
+  return PP_OK;
+}
+
+int pp_cweno_launches_per_step(pp_cweno_t h, int64_t *n) {
+  if (!h || !n) return PP_ERR_ARG;
+  *n = h->launches_per_step;
+  return PP_OK;
+}
+
+int pp_cweno_profile_step(pp_cweno_t h, float *ms, int nmax, int *nk) {
+  if (!h || !ms || !nk || nmax < 1) return PP_ERR_ARG;
+  int rc = pull_ctl(h);
+  if (rc) return rc;
+  Ctl *c = h->hctl;
+  c->t_final = INFINITY;
+  c->dt_cap = INFINITY;
+  c->done = 0;
+  c->step_limit = c->step + 1;
+  c->err_steps = 0;
+  if ((rc = push_ctl(h))) return rc;
+  const int nker = 1 + 3 * (h->nv == 4 ? 2 : 1);
+  cudaEvent_t ev[16];
+  for (int k = 0; k <= nker; ++k)
+    if (cudaEventCreate(&ev[k]) != cudaSuccess) return PP_ERR_CUDA;
+  cudaError_t e = cudaEventRecord(ev[0], h->stream);
+  int idx = 0;
+  step_begin_kernel<<<1, 32, 0, h->stream>>>(h->ctl);
+  cudaEventRecord(ev[++idx], h->stream);
+  for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
+    const double *Uin = s == 0 ? h->U0 : h->U1;
+    double *Uout = s == 2 ? h->U0 : h->U1;
+    if (h->nv == 4) {
+      e = launch(h, MODE_XSWEEP, true, Uin, h->U0, nullptr, h->D, nullptr, s, 0.0, h->ctl);
+      cudaEventRecord(ev[++idx], h->stream);
+      if (e == cudaSuccess)
+        e = launch(h, MODE_FINAL, false, Uin, h->U0, h->D, nullptr, Uout, s, 0.0, h->ctl);
+      cudaEventRecord(ev[++idx], h->stream);
+    } else {
+      e = launch(h, MODE_FINAL, true, Uin, h->U0, nullptr, nullptr, Uout, s, 0.0, h->ctl);
+      cudaEventRecord(ev[++idx], h->stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  int n = 0;
+  for (int k = 0; k < nker && k < nmax && e == cudaSuccess; ++k) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+    ms[n++] = t;
+  }
+  for (int k = 0; k <= nker; ++k) cudaEventDestroy(ev[k]);
+  *nk = n;
+  if (e != cudaSuccess) return PP_ERR_CUDA;
+  if ((rc = pull_ctl(h))) return rc;
+  c->t_final = c->t;
+  c->done = 1;
+  if ((rc = push_ctl(h))) return rc;
+  return cuerr(cudaStreamSynchronize(h->stream));
+}
+
+int pp_cweno_fma_peak(int fp64, double *gflops) {
+  if (!gflops) return PP_ERR_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PP_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PP_ERR_CUDA;
+  const int threads = 256, blocks = sms * 8;
+  const int iters = fp64 ? 4096 : 65536;
+  void *out = nullptr;
+  if (cudaMalloc(&out, 16) != cudaSuccess) return PP_ERR_CUDA;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(a, 0);
+    if (fp64) fma_peak_kernel<double><<<blocks, threads>>>((double *)out, iters, 0.999999, 1e-7);
+    else fma_peak_kernel<float><<<blocks, threads>>>((float *)out, iters, 0.999999f, 1e-7f);
+    cudaEventRecord(b, 0);
+    cudaEventSynchronize(b);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    if (rep > 0 && t < best) best = t;
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(out);
+  if (e != cudaSuccess) return PP_ERR_CUDA;
+  double flops = 2.0 * 8.0 * (double)iters * (double)threads * (double)blocks;
+  *gflops = flops / (best * 1e-3) / 1e9;
+  return PP_OK;
+}
+
+int pp_cweno_destroy(pp_cweno_t h) {
+  if (!h) return PP_OK;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  cudaFree(h->U0);
+  cudaFree(h->U1);
+  cudaFree(h->D);
+  cudaFree(h->ctl);
+  cudaFree(h->ctl_scratch);
+  if (h->hctl) cudaFreeHost(h->hctl);
+  delete h;
+  return PP_OK;
+}
+
+const char *pp_cweno_strerror(int code) {
+  switch (code) {
+    case PP_OK: return "ok";
+    case PP_ERR_ARG: return "invalid argument";
+    case PP_ERR_STATE: return "state outside the admissible set (rho > 0, e > 0, finite)";
+    case PP_ERR_NONPHYSICAL: return "a step produced a non-physical cell";
+    case PP_ERR_STEPS: return "max_steps reached before t_final";
+    case PP_ERR_TIMEOUT: return "bounded device wait expired";
+    case PP_ERR_CUDA: return "CUDA runtime error";
+    case PP_ERR_UNSUPPORTED: return "configuration not supported by this build";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// sweeps.cuh -- launch helpers shared by the host library and the
+// per-precision translation units that instantiate the line kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "line_sweep.cuh"
+
+namespace ppk {
+
+constexpr int M_ROWS = 8;   // rows per thread chunk
+constexpr int SEG_CELLS = KC * M_ROWS;
+
+struct LaunchCfg {
+  int precision;   // 0 fp64, 1 mixed (fp32 line arithmetic)
+  int nv;          // 3 or 4
+  bool periodic;
+  int mode;        // MODE_*
+  bool attrs_only; // set the kernel's attributes, launch nothing
+};
+
+// Launch one sweep over nlines lines with R CTAs per line (cluster of R).
+// Implemented in the per-precision translation units.
+cudaError_t launch_sweep_f64(const LaunchCfg &c, const SweepArgs &a, long long nlines,
+                             cudaStream_t st);
+cudaError_t launch_sweep_f32(const LaunchCfg &c, const SweepArgs &a, long long nlines,
+                             cudaStream_t st);
+
+template <typename real, int NV, bool PER, int MODE, typename dreal>
+cudaError_t launch_one(const SweepArgs &a, long long nlines, cudaStream_t st, bool attrs_only) {
+  using S = Smem<real, NV, M_ROWS>;
+  auto kern = line_sweep<real, NV, M_ROWS, PER, MODE, dreal>;
+  if (attrs_only) {   // called at handle creation, outside any stream capture
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nlines * a.R), 1, 1);
+  cfg.blockDim = dim3(NV * KC, 1, 1);
+  cfg.dynamicSmemBytes = S::bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)a.R;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <typename real, typename dreal>
+cudaError_t launch_dispatch(const LaunchCfg &c, const SweepArgs &a, long long nlines,
+                            cudaStream_t st) {
+  if (c.nv == 3) {
+    if (c.mode == MODE_FINAL)
+      return c.periodic ? launch_one<real, 3, true, MODE_FINAL, dreal>(a, nlines, st, c.attrs_only)
+                        : launch_one<real, 3, false, MODE_FINAL, dreal>(a, nlines, st, c.attrs_only);
+    if (c.mode == MODE_OPERATOR)
+      return c.periodic ? launch_one<real, 3, true, MODE_OPERATOR, dreal>(a, nlines, st, c.attrs_only)
+                        : launch_one<real, 3, false, MODE_OPERATOR, dreal>(a, nlines, st, c.attrs_only);
+    return cudaErrorInvalidValue;
+  }
+  if (c.nv == 4) {
+    if (c.mode == MODE_XSWEEP)
+      return c.periodic ? launch_one<real, 4, true, MODE_XSWEEP, dreal>(a, nlines, st, c.attrs_only)
+                        : launch_one<real, 4, false, MODE_XSWEEP, dreal>(a, nlines, st, c.attrs_only);
+    if (c.mode == MODE_FINAL)
+      return c.periodic ? launch_one<real, 4, true, MODE_FINAL, dreal>(a, nlines, st, c.attrs_only)
+                        : launch_one<real, 4, false, MODE_FINAL, dreal>(a, nlines, st, c.attrs_only);
+    if (c.mode == MODE_OPERATOR)
+      return c.periodic ? launch_one<real, 4, true, MODE_OPERATOR, dreal>(a, nlines, st, c.attrs_only)
+                        : launch_one<real, 4, false, MODE_OPERATOR, dreal>(a, nlines, st, c.attrs_only);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ppk

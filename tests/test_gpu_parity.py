@@ -1,0 +1,271 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every case feeds the same seeded inputs (paper_1402_5618_gb300.workloads) to
+both sides.  FP64 tolerances:
+  * one operator evaluation: element-wise 1e-12 of the variable's flux scale
+    (max |F_v| + max |U_v| max(|u|+a)) / h;
+  * whole runs on smooth data: relative L1 <= 1e-11 per conserved variable
+    with an identical step count;
+  * whole runs with shocks: the scheme itself amplifies rounding (the WENO-Z
+    weights with eps = 1e-13 react to rounding-level changes near jumps):
+    the oracle run from inputs perturbed by a seeded 1e-16 relative noise
+    differs from the unperturbed oracle run by d_ref (1e-10 .. 1e-7 on these
+    cases).  The GPU result must lie within max(1e-11, 20 d_ref) of the
+    oracle, with an identical step count.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_5618_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_5618_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _grid(p, **kw):
+    return oracle.make_grid(p.ndim, p.nx, p.ny, p.dx, p.dy, p.gamma, p.bc, **kw)
+
+
+def _gpu_operator(B, p, U, eps, precision=0):
+    s = B.Solver(B.config_from_problem(p, precision))
+    Ud = torch.from_numpy(np.ascontiguousarray(U).ravel()).cuda()
+    Ld = torch.zeros_like(Ud)
+    s.operator(Ud, Ld, eps)
+    s.close()
+    return Ld.cpu().numpy().reshape(U.shape)
+
+
+def _scale(p, U):
+    """per-variable flux scale (max |F_v| + max |U_v| max(|u|+a)) / h"""
+    nv = U.shape[0]
+    flat = U.reshape(nv, -1)
+    rho = flat[0]
+    vel = np.sqrt(np.sum(flat[1:nv - 1] ** 2, axis=0)) / rho
+    pr = (p.gamma - 1) * (flat[nv - 1] - 0.5 * rho * vel ** 2)
+    smax = np.max(vel + np.sqrt(p.gamma * np.maximum(pr, 0) / rho))
+    F = [np.abs(flat[1]).max(), np.abs(flat[1] * vel + pr).max()]
+    if nv == 4:
+        F.append(np.abs(flat[2] * vel).max())
+    F.append(np.abs(vel * (flat[nv - 1] + pr)).max())
+    h = min(p.dx, p.dy) if p.ndim == 2 else p.dx
+    return np.array([(F[v] + np.abs(flat[v]).max() * smax) / h for v in range(nv)])
+
+
+def _assert_operator_close(Lg, Lo, scale, tol=1e-12):
+    nv = Lo.shape[0]
+    for v in range(nv):
+        err = np.abs(Lg[v] - Lo[v]).max()
+        assert err <= tol * scale[v], (v, err, scale[v])
+
+
+OPERATOR_CASES_1D = [
+    ("smooth_periodic_200", lambda: W.random_smooth_1d(200, stream=51)),
+    ("smooth_periodic_1500", lambda: W.random_smooth_1d(1500, stream=52)),
+    ("smooth_bounded_1100", lambda: W.random_smooth_1d(1100, stream=53, periodic=False)),
+    ("riemann_1300", lambda: W.riemann_1d(1300, (1.0, 0.75, 1.0), (0.125, -0.3, 0.1), bc=(2, 1))),
+    ("riemann_vacuum_517", lambda: W.riemann_1d(517, (1.0, -3.5, 0.4), (1.0, 3.5, 0.4))),
+    ("leblanc_1000", lambda: W.leblanc(1000)),
+    ("n8_periodic", lambda: W.random_smooth_1d(8, stream=54)),
+    ("n8_bounded", lambda: W.random_smooth_1d(8, stream=55, periodic=False)),
+]
+
+
+@pytest.mark.parametrize("name,make", OPERATOR_CASES_1D, ids=[c[0] for c in OPERATOR_CASES_1D])
+def test_operator_parity_1d(B, name, make):
+    p = make()
+    eps = min(1e-13, p.U0[0].min())
+    Lo, _ = oracle.operator(_grid(p), p.U0, eps)
+    Lg = _gpu_operator(B, p, p.U0, eps)
+    _assert_operator_close(Lg, Lo, _scale(p, p.U0))
+
+
+OPERATOR_CASES_2D = [
+    ("vortex_64", lambda: W.vortex_2d(64)),
+    ("jumps_600x530", lambda: W.random_jumps_2d(600, 530, stream=61)),
+    ("jumps_periodic_96x40", lambda: W.random_jumps_2d(96, 40, stream=62, bc=(0, 0, 0, 0))),
+    ("blast_96", lambda: W.blast_2d(96)),
+    ("quadrant_1030", lambda: W.quadrant_batch(1, 1030, 1031, stream=63)[0]),
+]
+
+
+@pytest.mark.parametrize("name,make", OPERATOR_CASES_2D, ids=[c[0] for c in OPERATOR_CASES_2D])
+def test_operator_parity_2d(B, name, make):
+    p = make()
+    eps = min(1e-13, p.U0[0].min())
+    Lo, _ = oracle.operator(_grid(p), p.U0, eps)
+    Lg = _gpu_operator(B, p, p.U0, eps)
+    _assert_operator_close(Lg, Lo, _scale(p, p.U0))
+
+
+def _run_both(B, p, t_final=None, max_steps=10**9):
+    t_final = p.t_final if t_final is None else t_final
+    Uo, to, so, dto, cnt, rc = oracle.advance(_grid(p), p.U0, p.cfl, t_final, max_steps=max_steps)
+    s = B.Solver(B.config_from_problem(p))
+    s.set_state(np.ascontiguousarray(p.U0).ravel())
+    n, rcg = s.advance(t_final, max_steps, check=False)
+    Ug, tg, sg = s.get_state()
+    st = s.stats()
+    s.close()
+    return Uo, so, rc, Ug.reshape(p.U0.shape), sg, rcg, st
+
+
+def _rel_l1(A, B):
+    nv = A.shape[0]
+    return np.array([np.abs(A[v] - B[v]).sum() / max(np.abs(B[v]).sum(), 1e-300) for v in range(nv)])
+
+
+def _assert_run_close(Uo, Ug, tol=1e-11):
+    rel = _rel_l1(Ug, Uo)
+    assert np.all(rel <= tol), rel
+
+
+def _rounding_sensitivity(p, t_final=None, max_steps=10**9):
+    """relative L1 between oracle runs from U0 and from U0 (1 + 1e-16 noise)"""
+    t_final = p.t_final if t_final is None else t_final
+    g = _grid(p)
+    noise = W.rng(999).standard_normal(p.U0.shape)
+    Ua, *_ = oracle.advance(g, p.U0, p.cfl, t_final, max_steps=max_steps)
+    Ub, *_ = oracle.advance(g, p.U0 * (1 + 1e-16 * noise), p.cfl, t_final, max_steps=max_steps)
+    return _rel_l1(Ub, Ua)
+
+
+def test_run_parity_density_wave_n200(B):
+    """The density-wave run (Sec. 3 Ex. 3.1) at N = 200 to t = 2."""
+    p = W.density_wave(200)
+    Uo, so, rc, Ug, sg, rcg, st = _run_both(B, p)
+    assert rc == 0 and rcg == 0 and so == sg
+    _assert_run_close(Uo, Ug)
+    err = p.dx * np.abs(Ug[0] - W.density_wave_exact(200, 2.0)).sum()
+    assert 5e-11 < err < 1.5e-10
+
+
+RUN_CASES_1D = [
+    ("sod_100", lambda: W.paper_riemann("sod", 100, cfl=0.4)),
+    ("lax_200", lambda: W.paper_riemann("lax", 200, cfl=0.4)),
+    ("123_400", lambda: W.paper_riemann("123", 400, cfl=1 / 12)),
+    ("strong_shock_200", lambda: W.paper_riemann("strong_shock", 200, cfl=1 / 12)),
+    ("wc_blast_reflective_300", lambda: W.blastwave_wc(300, cfl=0.3)),
+    ("riemann_1300_multicta", lambda: W.riemann_1d(1300, (2.0, 0.3, 2.0), (0.5, -0.4, 0.3),
+                                                     bc=(1, 2), t_final=0.05)),
+    ("smooth_periodic_1500", lambda: W.random_smooth_1d(1500, stream=71)),
+]
+
+
+@pytest.mark.parametrize("name,make", RUN_CASES_1D, ids=[c[0] for c in RUN_CASES_1D])
+def test_run_parity_1d(B, name, make):
+    p = make()
+    Uo, so, rc, Ug, sg, rcg, st = _run_both(B, p)
+    assert rc == 0 and rcg == 0
+    assert so == sg
+    tol = np.maximum(1e-11, 20 * _rounding_sensitivity(p))
+    rel = _rel_l1(Ug, Uo)
+    assert np.all(rel <= tol), (rel, tol)
+    assert st.violations == 0
+
+
+RUN_CASES_2D = [
+    ("vortex_48", lambda: W.vortex_2d(48, t_final=0.5), False),
+    ("blast_64_cfl_1_12", lambda: W.blast_2d(64, cfl=1 / 12, t_final=0.05), True),
+    ("jumps_520x300", lambda: W.random_jumps_2d(520, 300, stream=81), True),
+]
+
+
+@pytest.mark.parametrize("name,make,shocks", RUN_CASES_2D, ids=[c[0] for c in RUN_CASES_2D])
+def test_run_parity_2d(B, name, make, shocks):
+    p = make()
+    Uo, so, rc, Ug, sg, rcg, st = _run_both(B, p, max_steps=40)
+    assert rc in (0, -2) and rcg in (0, B.PP_ERR_STEPS)
+    assert so == sg
+    tol = np.maximum(1e-11, 20 * _rounding_sensitivity(p, max_steps=40)) if shocks else 1e-11
+    rel = _rel_l1(Ug, Uo)
+    assert np.all(rel <= tol), (rel, tol)
+    assert st.violations == 0
+
+
+def test_full_size_blast_4096_one_step(B):
+    """The benchmark's 4096^2 blast: one SSP-RK3 step through the C ABI in
+    the benchmark's launch configuration against the oracle's step with the
+    same dt, over the whole grid."""
+    p = W.blast_2d(4096)
+    g = _grid(p)
+    s = B.Solver(B.config_from_problem(p))
+    s.set_state(np.ascontiguousarray(p.U0).ravel())
+    dt = s.step()
+    Ug, tg, sg = s.get_state()
+    s.close()
+    rate = oracle.max_rate(g, p.U0)
+    assert abs(dt - p.cfl / rate) <= 1e-15 * dt
+    Uo = oracle.rk3_step(g, p.U0, dt)
+    _assert_run_close(Uo, Ug.reshape(p.U0.shape))
+
+
+def test_full_size_sampled_operator_4096(B):
+    """Operator at 4096^2 on random jump data: GPU L at the intersections of
+    sampled rows and columns equals the oracle's L_x(row) + L_y(column)."""
+    p = W.random_jumps_2d(4096, 4096, stream=91)
+    g = _grid(p)
+    eps = 1e-13
+    Lg = _gpu_operator(B, p, p.U0, eps)
+    rng = W.rng(92)
+    rows = np.sort(rng.choice(4096, 24, replace=False))
+    cols = np.sort(rng.choice(4096, 24, replace=False))
+    Lx, Ly = oracle.operator_lines(g, p.U0, eps, rows, cols)
+    scale = _scale(p, p.U0)
+    for a, j in enumerate(rows):
+        for b, i in enumerate(cols):
+            Lo = Lx[a, :, i] + Ly[b, :, j]
+            assert np.all(np.abs(Lg[:, j, i] - Lo) <= 1e-12 * scale), (j, i)
+
+
+# ------------------------------------------------------------ API behaviour
+def test_set_state_rejects_inadmissible(B):
+    p = W.random_smooth_1d(64, stream=3)
+    U = p.U0.copy()
+    U[0, 10] = -1.0
+    s = B.Solver(B.config_from_problem(p))
+    assert s.set_state(U.ravel(), check=False) == B.PP_ERR_STATE
+    U[0, 10] = np.nan
+    assert s.set_state(U.ravel(), check=False) == B.PP_ERR_STATE
+    s.close()
+
+
+def test_advance_step_limit_and_resume_bitwise(B):
+    """max_steps stops early with PP_ERR_STEPS; a checkpoint through
+    get_state / set_state resumes bit-identically."""
+    p = W.riemann_1d(700, (1.0, 0.0, 1.0), (0.3, 0.0, 0.2), t_final=0.06)
+    s = B.Solver(B.config_from_problem(p))
+    s.set_state(p.U0.ravel())
+    n, rc = s.advance(p.t_final, 5, check=False)
+    assert rc == B.PP_ERR_STEPS and n == 5
+    U5, t5, s5 = s.get_state()
+    s.advance(p.t_final)
+    Ua, ta, sa = s.get_state()
+    s2 = B.Solver(B.config_from_problem(p))
+    s2.set_state(U5, t0=t5)
+    s2.advance(p.t_final)
+    Ub, tb, sb = s2.get_state()
+    assert ta == tb and sa == sb + 5
+    assert np.array_equal(Ua, Ub)
+    s.close(); s2.close()
+
+
+def test_deterministic(B):
+    p = W.random_jumps_2d(200, 130, stream=5)
+    outs = []
+    for _ in range(2):
+        s = B.Solver(B.config_from_problem(p))
+        s.set_state(p.U0.ravel())
+        s.advance(p.t_final, 12, check=False)
+        outs.append(s.get_state()[0])
+        s.close()
+    assert np.array_equal(outs[0], outs[1])

@@ -1,0 +1,53 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+function that include/pp_cweno.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1402_5618_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pp_cweno.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pp_cweno_[a-z_]+)\s*\(", src)))
+
+
+def test_header_matches_binding_list():
+    assert _declared() == sorted(binding.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_config_struct_layout_matches_header():
+    # sizeof(pp_cweno_config) as laid out by the C compiler on this host
+    import subprocess
+    import tempfile
+    src = '#include "pp_cweno.h"\n#include <stdio.h>\n#include <stddef.h>\n' \
+          'int main(){printf("%zu %zu %zu\\n", sizeof(pp_cweno_config), ' \
+          'sizeof(pp_cweno_stats_t), offsetof(pp_cweno_config, limiter));return 0;}\n'
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    assert int(out[0]) == ctypes.sizeof(binding.Config)
+    assert int(out[1]) == ctypes.sizeof(binding.Stats)
+    assert int(out[2]) == binding.Config.limiter.offset
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(RuntimeError):
+        binding.lib()
