@@ -5,18 +5,20 @@
 // memory and runs, in order:
 //   load     cell averages of the segment plus a two-cell halo (ghost cells
 //            from the boundary condition at the line ends);
+//   weights  WENO-Z weights of every cell for both sides (Sec. 2.2, eq.
+//            (weight)), kept in shared memory for the two passes below;
 //   solve    for each conserved variable the minus and plus compact-WENO
-//            systems (Sec. 2.2, eqs. (weight), (CWENO-FV)) by Thomas
-//            elimination in the stable order (minus left to right, plus
-//            right to left), parallelised exactly: every thread owns a chunk
-//            of M rows, the forward elimination of a chunk is a projective
-//            map of the state (c', d') carried in from the previous rows
-//            ((P, Q, D) with c' = P/Q, d' = D/Q evolves linearly), the maps
-//            are composed by warp-shuffle scans, across warps in shared
-//            memory and across the cluster's CTAs through distributed shared
-//            memory; the back substitution is an affine map per chunk,
-//            scanned the same way.  Periodic lines add the second right-hand
-//            side of the Sherman-Morrison correction to the same sweep.
+//            systems (eq. (CWENO-FV)) by Thomas elimination in the stable
+//            order (minus left to right, plus right to left), parallelised
+//            exactly: every thread owns a chunk of M rows, the forward
+//            elimination of a chunk is a projective map of the state (c', d')
+//            carried in from the previous rows ((P, Q, D) with c' = P/Q,
+//            d' = D/Q evolves linearly), the maps are composed by
+//            warp-shuffle scans, across warps in shared memory and across the
+//            cluster's CTAs through distributed shared memory; the back
+//            substitution is an affine map per chunk, scanned the same way.
+//            Periodic lines add the second right-hand side of the
+//            Sherman-Morrison correction to the same sweep.
 //   limit    Zhang-Shu limiter per cell (Sec. 2.4);
 //   flux     HLLC at every face of the segment (the two segment-end faces
 //            read the neighbour CTA's limited face value);
@@ -24,12 +26,19 @@
 //            output D = L_x, or the SSP-RK3 stage combination (eq. (RK3))
 //            with L = D + L_y (2-D) / L (1-D), plus the grid-wide reductions
 //            that fix the next stage's limiter epsilon and the next dt.
+//
+// real = double: the plain form (FP64 state and arithmetic).
+// real = float: the mixed form -- FP32 line arithmetic, the state stored as
+// FP32 hi + lo pairs combined with compensated (double-float) arithmetic,
+// FP64 only for the limiter factors of cells that need limiting and for the
+// Sherman-Morrison scalars.
 #pragma once
 
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
 #include "physics.cuh"
 
 namespace cg = cooperative_groups;
@@ -57,11 +66,16 @@ struct Ctl {
 enum { MODE_XSWEEP = 0, MODE_FINAL = 1, MODE_OPERATOR = 2 };
 
 struct SweepArgs {
-  const double *U;    // stage input (grid variables), [nv][ncell]
+  // plain form: FP64 planes [nv][ncell]
+  const double *U;    // stage input
   const double *U0;   // U^n
-  const void *Din;    // flux difference of the other direction (FINAL / OPERATOR, 2-D)
-  void *Dout;         // x-sweep output
-  double *Uout;       // FINAL: stage output; OPERATOR: L
+  double *Uout;       // FINAL: stage output
+  // mixed form: FP32 hi / lo planes of the same states
+  const float *Uh, *Ul, *U0h, *U0l;
+  float *Uoh, *Uol;
+  const void *Din;    // flux difference of the other direction (2-D), real
+  void *Dout;         // x-sweep output, real
+  double *Lout;       // OPERATOR: L (FP64 planes)
   long long ncell;    // cells per variable plane
   int n;              // cells per line
   int R;              // CTAs per line (cluster size)
@@ -186,14 +200,13 @@ __device__ __forceinline__ Fwd<real> fwd_shfl(const Fwd<real> &f, int d) {
   return o;
 }
 
-// backward (substitution) map of a run: x_first = A + B x_after, z alike
+// back-substitution map of a run: x_first = A + B x_after (z alike, same B)
 template <typename real>
 struct Bwd {
   real A, B, Az;
 };
 
-// Y is the run eliminated first in back substitution order... the composite
-// of "this run" (X, nearer) followed by the run after it (Y):
+// the run X followed (in back-substitution order) by the run Y:
 // x_first(X) = X.A + X.B (Y.A + Y.B x_after(Y))
 template <typename real>
 __device__ __forceinline__ Bwd<real> bwd_compose(const Bwd<real> &X, const Bwd<real> &Y) {
@@ -213,42 +226,45 @@ struct Exch {
   Bwd<real> warp_bwd[NV][2][WPV];
   real warp_xn[NV][2][WPV][2];   // x, z after each warp
   Bwd<real> seg_bwd[NV][2];
-  real sm[NV][2][6];             // y_f, z_f, y_l, z_l, ratio a0/b0 (periodic)
-  double red_min[32];
-  double red_max[32];
-  unsigned int red_cnt[4];
+  double sm[NV][2][6];           // y_f, z_f, y_l, z_l, -a0/b0 (periodic)
 };
 
 template <typename real, int NV, int M>
 struct Smem {
   static constexpr int SEG = KC * M;
-  static constexpr size_t u_off = 0;                                   // real Us[NV][SEG+4]
-  static constexpr size_t fm_off = u_off + sizeof(real) * NV * (SEG + 4);
-  static constexpr size_t fp_off = fm_off + sizeof(real) * NV * SEG;   // real Fm, Fp[NV][SEG]
-  static constexpr size_t fl_off = fp_off + sizeof(real) * NV * SEG;   // real Fl[NV][SEG+1]
+  static constexpr size_t u_off = 0;                                    // real Us[NV][SEG+4]
+  static constexpr size_t w_off = u_off + sizeof(real) * NV * (SEG + 4); // real Wt[NV][4][SEG]
+  static constexpr size_t fm_off = w_off + sizeof(real) * NV * 4 * SEG;
+  static constexpr size_t fp_off = fm_off + sizeof(real) * NV * SEG;    // real Fm, Fp[NV][SEG]
+  static constexpr size_t fl_off = fp_off + sizeof(real) * NV * SEG;    // real Fl[NV][SEG+2]
   static constexpr size_t rm_off = fl_off + sizeof(real) * NV * (SEG + 2);  // remote stencils
   static constexpr size_t ex_off = (rm_off + sizeof(real) * NV * 2 * 6 + 15) / 16 * 16;
   static constexpr size_t bytes = ex_off + sizeof(Exch<real, NV>);
 };
-
-__device__ __forceinline__ double ull_as_double(unsigned long long b) { return __longlong_as_double((long long)b); }
-__device__ __forceinline__ unsigned long long double_as_ull(double x) {
-  return (unsigned long long)__double_as_longlong(x);
-}
 
 // line-variable k -> grid variable
 __device__ __forceinline__ int gvar(int k, int nv, int vn, int vt) {
   return k == 0 ? 0 : (k == nv - 1 ? nv - 1 : (k == 1 ? vn : vt));
 }
 
+__device__ __forceinline__ unsigned long long double_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ double bits_double(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+
 // ---------------------------------------------------------------- kernel
-template <typename real, int NV, int M, bool PER, int MODE, typename dreal>
+template <typename real, int NV, int M, bool PER, int MODE>
 __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
+  constexpr bool MIXED = sizeof(real) == 4;
   using S = Smem<real, NV, M>;
   constexpr int SEG = S::SEG;
   constexpr int T = NV * KC;
+  constexpr int UW = SEG + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real *Us = reinterpret_cast<real *>(smem_raw + S::u_off);
+  real *Wt = reinterpret_cast<real *>(smem_raw + S::w_off);
   real *Fm = reinterpret_cast<real *>(smem_raw + S::fm_off);
   real *Fp = reinterpret_cast<real *>(smem_raw + S::fp_off);
   real *Fl = reinterpret_cast<real *>(smem_raw + S::fl_off);
@@ -278,16 +294,16 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
   real eps_pos;
   if (args.eps_fixed > 0.0) eps_pos = real(args.eps_fixed);
   else if (args.stage == 0) eps_pos = real(ctl->eps0);
-  else eps_pos = real(fmin(ctl->eps_pos, ull_as_double(ctl->minrho[args.stage - 1])));
+  else eps_pos = real(fmin(ctl->eps_pos, bits_double(ctl->minrho[args.stage - 1])));
 
   const long long lbase = line * args.line_stride;
   const long long cs = args.cell_stride;
 
   // ---------------------------------------------------------------- load
-  auto cell_val = [&](int kv, int i) -> double {
-    // value of line variable kv at line cell i (any i; ghosts by BC)
+  auto cell_val = [&](int kv, int i) -> real {
+    // line variable kv at line cell i (any i; ghosts by the boundary condition)
     int g = gvar(kv, NV, args.vn, args.vt);
-    double sign = 1.0;
+    bool neg = false;
     if (i < 0 || i >= n) {
       if (PER) {
         i = (i % n + n) % n;
@@ -297,17 +313,21 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
           i = i < 0 ? 0 : n - 1;
         } else {  // reflective mirror
           i = i < 0 ? -i - 1 : 2 * n - 1 - i;
-          if (kv == 1) sign = -1.0;
+          neg = kv == 1;
         }
       }
     }
-    return sign * args.U[g * args.ncell + lbase + (long long)i * cs];
+    long long a = g * args.ncell + lbase + (long long)i * cs;
+    real x;
+    if constexpr (MIXED) x = args.Uh[a];
+    else x = args.U[a];
+    return neg ? -x : x;
   };
 
-  for (int idx = tid; idx < NV * (SEG + 4); idx += T) {
-    int kv = idx / (SEG + 4), j = idx % (SEG + 4);
+  for (int idx = tid; idx < NV * UW; idx += T) {
+    int kv = idx / UW, j = idx % UW;
     int i = lo - 2 + j;
-    Us[kv * (SEG + 4) + j] = (i < hi + 2) ? real(cell_val(kv, i)) : real(0);
+    Us[kv * UW + j] = (i < hi + 2) ? cell_val(kv, i) : real(0);
   }
   if (PER) {
     // stencils of the two "position 0" cells (minus: cell 0, plus: cell n-1)
@@ -315,74 +335,88 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
     for (int idx = tid; idx < NV * 2 * 5; idx += T) {
       int kv = idx / 10, s = (idx / 5) % 2, j = idx % 5;
       int c0 = s == 0 ? 0 : n - 1;
-      Rm[(kv * 2 + s) * 6 + j] = real(cell_val(kv, c0 - 2 + j));
+      Rm[(kv * 2 + s) * 6 + j] = cell_val(kv, c0 - 2 + j);
     }
   }
   __syncthreads();
 
   // ---------------------------------------------------------------- rows
-  const real *u = Us + v * (SEG + 4) + 2;   // u[i - lo], valid i - lo in [-2, hi-lo+2)
-  const int s0 = lo + k * M;                 // first cell of this thread's chunk
+  const real *u = Us + v * UW + 2;            // u[i - lo], valid i - lo in [-2, hi-lo+2)
+  real *wt = Wt + v * 4 * SEG;                // wt[q*SEG + c]: w0-, w2-, w0+, w2+
+  const int s0 = lo + k * M;                  // first cell of this thread's chunk
   const int len = max(0, min(M, hi - s0));
   const bool bounded = !PER;
 
-  // rows of cell i (line index) for both sides, in each side's elimination
-  // order: minus couples (i-1 prev, i+1 next), plus (i+1 prev, i-1 next)
-  auto rows_of = [&](int i, Row<real> &rm, Row<real> &rp, real &um_, real &up_) {
+  // weights of cell i for both sides (stored), or the closure values
+  auto weights_of = [&](int i) {
     const real *x = u + (i - lo);
-    real q0, q1, q2, w0, w1, w2, one;
-    um_ = real(0);
-    up_ = real(0);
+    real *o = wt + (i - lo);
     if (bounded && (i == 0 || i == n - 1)) {
-      rm.a = real(0); rm.b = real(1); rm.c = real(0);
-      rp.a = real(0); rp.b = real(1); rp.c = real(0);
-      rm.r = weno5z_face(x[-2], x[-1], x[0], x[1], x[2], eps_w);
-      rp.r = weno5z_face(x[2], x[1], x[0], x[-1], x[-2], eps_w);
+      o[0] = weno5z_face(x[-2], x[-1], x[0], x[1], x[2], eps_w);
+      o[2 * SEG] = weno5z_face(x[2], x[1], x[0], x[-1], x[-2], eps_w);
       return;
     }
+    real q0, q1, q2, one, w0, w1, w2;
     zratios_any(x[-2], x[-1], x[0], x[1], x[2], eps_w, q0, q1, q2, one);
     zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
-    rm = compact_row(w0, w1, w2, x[-1], x[0], x[1]);
+    o[0] = w0;
+    o[SEG] = w2;
     zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, w0, w1, w2, one);
-    rp = compact_row(w0, w1, w2, x[1], x[0], x[-1]);
-    if (PER) {
-      // Sherman-Morrison: T = A - u v^T with g = -b at position 0 (minus:
-      // cell 0, plus: cell n-1) and the corner couplings removed
-      if (i == 0) {          // minus position 0; plus position n-1
-        um_ = -rm.b;
-        rm.b = rm.b + rm.b;
-        rm.a = real(0);
-        const real *y = Rm + (v * 2 + 1) * 6 + 2;   // stencil of cell n-1
-        real r0, r1, r2, a0, a1, a2, o1;
-        zratios_any(y[-2], y[-1], y[0], y[1], y[2], eps_w, r0, r1, r2, o1);
-        zweights(real(0.2), real(0.5), real(0.3), r2, r1, r0, a0, a1, a2, o1);
-        real pa = (real(2) * a0 + a1) / real(3), pb = (a0 + real(2) * (a1 + a2)) / real(3);
-        up_ = rp.c;
-        rp.b = rp.b + rp.c * pa / pb;
-        rp.c = real(0);
-      }
-      if (i == n - 1) {      // plus position 0; minus position n-1
-        up_ = -rp.b;
-        rp.b = rp.b + rp.b;
-        rp.a = real(0);
-        const real *y = Rm + (v * 2 + 0) * 6 + 2;   // stencil of cell 0
-        real r0, r1, r2, a0, a1, a2, o1;
-        zratios_any(y[-2], y[-1], y[0], y[1], y[2], eps_w, r0, r1, r2, o1);
-        zweights(real(0.2), real(0.5), real(0.3), r0, r1, r2, a0, a1, a2, o1);
-        real pa = (real(2) * a0 + a1) / real(3), pb = (a0 + real(2) * (a1 + a2)) / real(3);
-        um_ = rm.c;
-        rm.b = rm.b + rm.c * pa / pb;
-        rm.c = real(0);
-      }
-    }
+    o[2 * SEG] = w0;
+    o[3 * SEG] = w2;
   };
 
-  // ------------------------------------------- chunk forward maps (F1)
+  // a, b of the unmodified position-0 row of side 0 (cell 0) or 1 (cell n-1),
+  // needed by the Sherman-Morrison row at the far end of a periodic system
+  auto far_row = [&](int side, real &a0, real &b0) {
+    const real *y = Rm + (v * 2 + side) * 6 + 2;
+    real q0, q1, q2, one, w0, w1, w2;
+    zratios_any(y[-2], y[-1], y[0], y[1], y[2], eps_w, q0, q1, q2, one);
+    if (side == 0) zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
+    else zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, w0, w1, w2, one);
+    Row<real> r = compact_row02(w0, w2, real(0), real(0), real(0));
+    a0 = r.a;
+    b0 = r.b;
+  };
+
+  // row of cell i, side 0 (minus: prev = i-1) or 1 (plus: prev = i+1), from
+  // the stored weights; zr = the Sherman-Morrison right-hand side entry
+  auto row_of = [&](int i, int side, real &zr) -> Row<real> {
+    const real *x = u + (i - lo);
+    const real *o = wt + (i - lo) + 2 * side * SEG;
+    Row<real> r;
+    zr = real(0);
+    if (bounded && (i == 0 || i == n - 1)) {
+      r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
+      return r;
+    }
+    if (side == 0) r = compact_row02(o[0], o[SEG], x[-1], x[0], x[1]);
+    else r = compact_row02(o[0], o[SEG], x[1], x[0], x[-1]);
+    if (PER) {
+      const int first = side == 0 ? 0 : n - 1, last = side == 0 ? n - 1 : 0;
+      if (i == first) {          // T = A - u v^T with g = -b at position 0
+        zr = -r.b;
+        r.b = r.b + r.b;
+        r.a = real(0);
+      } else if (i == last) {    // corner removed, b reduced by c a0 / g
+        real a0, b0;
+        far_row(side, a0, b0);
+        zr = r.c;
+        r.b = r.b + r.c * a0 / b0;
+        r.c = real(0);
+      }
+    }
+    return r;
+  };
+
+  // ------------------------------------------- weights + chunk maps (F1)
   Fwd<real> fm = fwd_identity<real>(), fp = fwd_identity<real>();
+  for (int j = 0; j < len; ++j) weights_of(s0 + j);
+  // each thread reads back only the weights it wrote (no barrier needed)
   for (int j = 0; j < len; ++j) {
-    Row<real> rm, rp;
     real zm, zp;
-    rows_of(s0 + j, rm, rp, zm, zp);
+    Row<real> rm = row_of(s0 + j, 0, zm);
+    Row<real> rp = row_of(s0 + j, 1, zp);
     fwd_push_left<real, PER>(fm, rm, zm);
     fwd_push_right<real, PER>(fp, rp, zp);
   }
@@ -455,21 +489,18 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
   // A = sum_j (prod_{l<j} -c'_l) d'_j, B = prod_l -c'_l.
   // minus: position j <-> cell s0 + j; plus: position j <-> cell s0+len-1-j.
   real cmv[M], dmv[M], zmv[M], cpv[M], dpv[M], zpv[M];
-  real pa[M], pb[M], pc[M], pr[M], pu[M];   // plus rows of the chunk, by cell
   Bwd<real> bm, bp;
   {
     real pim = real(1), A = real(0), Az = real(0);
 #pragma unroll
     for (int j = 0; j < M; ++j) {
       if (j < len) {
-        Row<real> rm, rp;
-        real zm, zp;
-        rows_of(s0 + j, rm, rp, zm, zp);
-        pa[j] = rp.a; pb[j] = rp.b; pc[j] = rp.c; pr[j] = rp.r; pu[j] = zp;
+        real zr;
+        Row<real> rm = row_of(s0 + j, 0, zr);
         real ip = real(1) / (rm.b - rm.a * cpm);
         cpm = rm.c * ip;
         dpm = (rm.r - rm.a * dpm) * ip;
-        if (PER) zpm = (zm - rm.a * zpm) * ip;
+        if (PER) zpm = (zr - rm.a * zpm) * ip;
         cmv[j] = cpm;
         dmv[j] = dpm;
         zmv[j] = PER ? zpm : real(0);
@@ -483,14 +514,14 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
   {
     real pip = real(1), A = real(0), Az = real(0);
 #pragma unroll
-    for (int jj = 0; jj < M; ++jj) {
-      int j = M - 1 - jj;          // cells from the right end of the chunk
-      if (j < len) {
-        int pos = len - 1 - j;     // plus position inside the chunk
-        real ip = real(1) / (pb[j] - pa[j] * cpp);
-        cpp = pc[j] * ip;
-        dpp = (pr[j] - pa[j] * dpp) * ip;
-        if (PER) zpp = (pu[j] - pa[j] * zpp) * ip;
+    for (int pos = 0; pos < M; ++pos) {
+      if (pos < len) {
+        real zr;
+        Row<real> rp = row_of(s0 + len - 1 - pos, 1, zr);
+        real ip = real(1) / (rp.b - rp.a * cpp);
+        cpp = rp.c * ip;
+        dpp = (rp.r - rp.a * dpp) * ip;
+        if (PER) zpp = (zr - rp.a * zpp) * ip;
         cpv[pos] = cpp;
         dpv[pos] = dpp;
         zpv[pos] = PER ? zpp : real(0);
@@ -531,7 +562,8 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
     int vv = tid >> 1, sd = tid & 1;
     Bwd<real> sg;
     sg.A = real(0); sg.B = real(1); sg.Az = real(0);
-    // minus: segment first cell = warp 0 o warp 1 o ...; plus: last warp first
+    // minus: first cell of the segment = warp 0 o warp 1 o ...; plus: the
+    // last warp's map is applied first
     for (int ww = WPV - 1; ww >= 0; --ww) {
       int wi = sd == 0 ? ww : WPV - 1 - ww;
       sg = bwd_compose(ex.warp_bwd[vv][sd][wi], sg);
@@ -597,40 +629,33 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
     real z = bp_ex.Az + bp_ex.B * zn;
 #pragma unroll
     for (int jj = 0; jj < M; ++jj) {
-      int pos = M - 1 - jj;     // plus positions from the chunk's last (left-most cell)
+      int pos = M - 1 - jj;     // plus positions from the chunk's left-most cell
       if (pos < len) {
         x = dpv[pos] - cpv[pos] * x;
         if (PER) z = zpv[pos] - cpv[pos] * z;
-        int cell = s0 + len - 1 - pos;
-        Fp[v * SEG + (cell - lo)] = x;
+        Fp[v * SEG + (s0 + len - 1 - pos - lo)] = x;
         zpo[pos] = z;
       }
     }
   }
 
   if (PER) {
-    // Sherman-Morrison correction: x = y - (v.y)/(1 + v.z) z with
-    // v = e_first + (corner_first / g) e_last, corner_first / g = -a0/b0
-    if (k == 0 && lo == 0) {       // cell 0: minus first, plus last
-      // ratio -a0/b0 of the minus position-0 row from the unmodified weights
-      const real *x = u;
-      real q0, q1, q2, w0, w1, w2, one;
-      zratios_any(x[-2], x[-1], x[0], x[1], x[2], eps_w, q0, q1, q2, one);
-      zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
-      Row<real> rm = compact_row(w0, w1, w2, x[-1], x[0], x[1]);
-      ex.sm[v][0][4] = -rm.a / rm.b;
+    // Sherman-Morrison correction x = y - (v.y)/(1 + v.z) z, with
+    // v = e_first + (corner_first / g) e_last and corner_first / g = -a0/b0
+    // of the unmodified position-0 row; the scalars in FP64
+    if (len > 0 && s0 == 0) {              // cell 0: minus first, plus last
+      real a0, b0;
+      far_row(0, a0, b0);
+      ex.sm[v][0][4] = -(double)a0 / (double)b0;
       ex.sm[v][0][0] = Fm[v * SEG + 0];
       ex.sm[v][0][1] = zmo[0];
       ex.sm[v][1][2] = Fp[v * SEG + 0];
       ex.sm[v][1][3] = zpo[len - 1];
     }
-    if (len > 0 && s0 + len == n) {  // cell n-1: plus first, minus last
-      const real *x = u + (n - 1 - lo);
-      real q0, q1, q2, w0, w1, w2, one;
-      zratios_any(x[-2], x[-1], x[0], x[1], x[2], eps_w, q0, q1, q2, one);
-      zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, w0, w1, w2, one);
-      Row<real> rp = compact_row(w0, w1, w2, x[1], x[0], x[-1]);
-      ex.sm[v][1][4] = -rp.a / rp.b;
+    if (len > 0 && s0 + len == n) {        // cell n-1: plus first, minus last
+      real a0, b0;
+      far_row(1, a0, b0);
+      ex.sm[v][1][4] = -(double)a0 / (double)b0;
       ex.sm[v][1][0] = Fp[v * SEG + (n - 1 - lo)];
       ex.sm[v][1][1] = zpo[0];
       ex.sm[v][0][2] = Fm[v * SEG + (n - 1 - lo)];
@@ -640,22 +665,16 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
     {
       Exch<real, NV> *r0 = cluster.map_shared_rank(&ex, 0);
       Exch<real, NV> *rl = cluster.map_shared_rank(&ex, R - 1);
-      // minus: first = cell 0 (rank 0), last = cell n-1 (rank R-1)
-      real ratio = r0->sm[v][0][4];
-      real yf = r0->sm[v][0][0], zf = r0->sm[v][0][1];
-      real yl = rl->sm[v][0][2], zl = rl->sm[v][0][3];
-      real facm = (yf + ratio * yl) / (real(1) + zf + ratio * zl);
-      // plus: first = cell n-1 (rank R-1), last = cell 0 (rank 0)
-      real ratiop = rl->sm[v][1][4];
-      real ypf = rl->sm[v][1][0], zpf = rl->sm[v][1][1];
-      real ypl = r0->sm[v][1][2], zpl = r0->sm[v][1][3];
-      real facp = (ypf + ratiop * ypl) / (real(1) + zpf + ratiop * zpl);
+      double facm = (r0->sm[v][0][0] + r0->sm[v][0][4] * rl->sm[v][0][2]) /
+                    (1.0 + r0->sm[v][0][1] + r0->sm[v][0][4] * rl->sm[v][0][3]);
+      double facp = (rl->sm[v][1][0] + rl->sm[v][1][4] * r0->sm[v][1][2]) /
+                    (1.0 + rl->sm[v][1][1] + rl->sm[v][1][4] * r0->sm[v][1][3]);
+      real fm_ = real(facm), fp_ = real(facp);
 #pragma unroll
       for (int j = 0; j < M; ++j) {
         if (j < len) {
-          Fm[v * SEG + (s0 + j - lo)] -= facm * zmo[j];
-          int pos = len - 1 - j;
-          Fp[v * SEG + (s0 + j - lo)] -= facp * zpo[pos];
+          Fm[v * SEG + (s0 + j - lo)] -= fm_ * zmo[j];
+          Fp[v * SEG + (s0 + j - lo)] -= fp_ * zpo[len - 1 - j];
         }
       }
     }
@@ -669,11 +688,13 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
       real ub[NV], a[NV], b[NV];
 #pragma unroll
       for (int kv = 0; kv < NV; ++kv) {
-        ub[kv] = Us[kv * (SEG + 4) + c + 2];
+        ub[kv] = Us[kv * UW + c + 2];
         a[kv] = Fm[kv * SEG + c];
         b[kv] = Fp[kv * SEG + c];
       }
-      int f = limit_cell<real, NV>(ub, a, b, wgl, eps_pos);
+      int f;
+      if constexpr (MIXED) f = limit_cell_mixed<NV>(ub, a, b, wgl, eps_pos);
+      else f = limit_cell<real, NV>(ub, a, b, wgl, eps_pos, unit_roundoff<real>());
       if (f) {
 #pragma unroll
         for (int kv = 0; kv < NV; ++kv) {
@@ -690,39 +711,35 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
   // ---------------------------------------------------------------- flux
   for (int f = lo + tid; f <= hi; f += T) {
     real Ul[NV], Ur[NV], F[NV];
-    const real *srcL;
-    const real *srcR;
-    int il, ir;
-    bool bl = false, br = false;
+    const real *srcL = nullptr;
+    const real *srcR = nullptr;
+    int il = 0, ir = 0;
     // left state: U^- of cell f-1
     if (f == 0) {
-      if (PER) {
-        srcL = cluster.map_shared_rank(Fm, R - 1); il = (n - 1) - (R - 1) * SEG;
-      } else { srcL = nullptr; il = 0; bl = true; }
+      if (PER) { srcL = cluster.map_shared_rank(Fm, R - 1); il = (n - 1) - (R - 1) * SEG; }
     } else if (f - 1 < lo) {
       srcL = cluster.map_shared_rank(Fm, rank - 1); il = f - 1 - (rank - 1) * SEG;
     } else { srcL = Fm; il = f - 1 - lo; }
     // right state: U^+ of cell f
     if (f == n) {
       if (PER) { srcR = cluster.map_shared_rank(Fp, 0); ir = 0; }
-      else { srcR = nullptr; ir = 0; br = true; }
     } else if (f >= hi) {
       srcR = cluster.map_shared_rank(Fp, rank + 1); ir = f - (rank + 1) * SEG;
     } else { srcR = Fp; ir = f - lo; }
-    if (!bl) {
+    if (srcL) {
 #pragma unroll
       for (int kv = 0; kv < NV; ++kv) Ul[kv] = srcL[kv * SEG + il];
     }
-    if (!br) {
+    if (srcR) {
 #pragma unroll
       for (int kv = 0; kv < NV; ++kv) Ur[kv] = srcR[kv * SEG + ir];
     }
-    if (bl) {  // boundary face 0: exterior = BC(interior)
+    if (!srcL) {  // boundary face 0: exterior = BC(interior)
 #pragma unroll
       for (int kv = 0; kv < NV; ++kv) Ul[kv] = Ur[kv];
       if (args.bclo == 2) Ul[1] = -Ul[1];
     }
-    if (br) {
+    if (!srcR) {
 #pragma unroll
       for (int kv = 0; kv < NV; ++kv) Ur[kv] = Ul[kv];
       if (args.bchi == 2) Ur[1] = -Ur[1];
@@ -731,68 +748,114 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
 #pragma unroll
     for (int kv = 0; kv < NV; ++kv) Fl[kv * (SEG + 2) + (f - lo)] = F[kv];
   }
-  cluster.sync();   // neighbours' face values no longer needed after this
+  cluster.sync();   // neighbours' face values are no longer read after this
 
   // ---------------------------------------------------------------- update
   double mymin = 1.0e300, mymax = 0.0;
   unsigned int nbad = 0;
   unsigned long long firstbad = ~0ull;
-  const double h = args.h;
+  const real ih = real(1.0 / args.h);
   const double dt = (MODE == MODE_FINAL) ? ctl->dt : 0.0;
+  const real *Din = reinterpret_cast<const real *>(args.Din);
   for (int c = tid; c < hi - lo; c += T) {
     int i = lo + c;
     long long addr = lbase + (long long)i * cs;
-    double Lv[NV];
+    real Lv[NV];
 #pragma unroll
-    for (int kv = 0; kv < NV; ++kv)
-      Lv[kv] = -(double(Fl[kv * (SEG + 2) + c + 1]) - double(Fl[kv * (SEG + 2) + c])) / h;
+    for (int kv = 0; kv < NV; ++kv) {
+      Lv[kv] = (Fl[kv * (SEG + 2) + c] - Fl[kv * (SEG + 2) + c + 1]) * ih;
+      if (MODE != MODE_XSWEEP && Din) Lv[kv] += Din[gvar(kv, NV, args.vn, args.vt) * args.ncell + addr];
+    }
     if (MODE == MODE_XSWEEP) {
-      dreal *D = reinterpret_cast<dreal *>(args.Dout);
+      real *D = reinterpret_cast<real *>(args.Dout);
 #pragma unroll
-      for (int kv = 0; kv < NV; ++kv) D[gvar(kv, NV, args.vn, args.vt) * args.ncell + addr] = dreal(Lv[kv]);
-    } else {
+      for (int kv = 0; kv < NV; ++kv) D[gvar(kv, NV, args.vn, args.vt) * args.ncell + addr] = Lv[kv];
+    } else if (MODE == MODE_OPERATOR) {
+#pragma unroll
+      for (int kv = 0; kv < NV; ++kv) args.Lout[gvar(kv, NV, args.vn, args.vt) * args.ncell + addr] = double(Lv[kv]);
+    } else if constexpr (!MIXED) {
       double Ut[NV];
 #pragma unroll
       for (int kv = 0; kv < NV; ++kv) {
         int g = gvar(kv, NV, args.vn, args.vt);
         double L = Lv[kv];
-        if (args.Din) L = double(reinterpret_cast<const dreal *>(args.Din)[g * args.ncell + addr]) + L;
-        if (MODE == MODE_OPERATOR) {
-          args.Uout[g * args.ncell + addr] = L;
-        } else {
-          double uk = args.U[g * args.ncell + addr];
-          double un;
-          if (args.stage == 0) un = uk + dt * L;
-          else if (args.stage == 1) un = 0.75 * args.U0[g * args.ncell + addr] + 0.25 * uk + 0.25 * dt * L;
-          else un = args.U0[g * args.ncell + addr] / 3.0 + 2.0 / 3.0 * uk + 2.0 / 3.0 * dt * L;
-          args.Uout[g * args.ncell + addr] = un;
-          Ut[g] = un;
-        }
+        double uk = args.U[g * args.ncell + addr];
+        double un;
+        if (args.stage == 0) un = uk + dt * L;
+        else if (args.stage == 1) un = 0.75 * args.U0[g * args.ncell + addr] + 0.25 * uk + 0.25 * dt * L;
+        else un = args.U0[g * args.ncell + addr] / 3.0 + 2.0 / 3.0 * uk + 2.0 / 3.0 * dt * L;
+        args.Uout[g * args.ncell + addr] = un;
+        Ut[g] = un;
       }
-      if (MODE == MODE_FINAL) {
-        double rho = Ut[0];
-        double mx = Ut[1], my = NV == 4 ? Ut[2] : 0.0, E = Ut[NV - 1];
-        double e = E / rho - 0.5 * (mx * mx + my * my) / (rho * rho);
-        bool ok = (rho > 0.0) && (e > 0.0) && isfinite(E) && isfinite(mx) && isfinite(my);
-        if (!ok) {
-          ++nbad;
-          unsigned long long flat = (unsigned long long)addr;
-          firstbad = flat < firstbad ? flat : firstbad;
+      double rho = Ut[0];
+      double mx = Ut[1], my = NV == 4 ? Ut[2] : 0.0, E = Ut[NV - 1];
+      double e = E / rho - 0.5 * (mx * mx + my * my) / (rho * rho);
+      bool ok = (rho > 0.0) && (e > 0.0) && isfinite(E) && isfinite(mx) && isfinite(my);
+      if (!ok) {
+        ++nbad;
+        firstbad = min(firstbad, (unsigned long long)addr);
+      } else {
+        mymin = fmin(mymin, rho);
+        double a = sqrt(args.gamma * (args.gamma - 1.0) * e);
+        double rate;
+        if (NV == 4) {
+          double hx = args.vn == 1 ? args.h : args.h_other;
+          double hy = args.vn == 1 ? args.h_other : args.h;
+          rate = (fabs(mx / rho) + a) / hx + (fabs(my / rho) + a) / hy;
         } else {
-          mymin = fmin(mymin, rho);
-          double a = sqrt(args.gamma * (args.gamma - 1.0) * e);
-          double rate;
-          if (NV == 4) {
-            // grid directions: x uses the line's other spacing on a y-sweep
-            double ux = fabs(mx / rho), uy = fabs(my / rho);
-            double hx = args.vn == 1 ? args.h : args.h_other;
-            double hy = args.vn == 1 ? args.h_other : args.h;
-            rate = (ux + a) / hx + (uy + a) / hy;
-          } else {
-            rate = (fabs(mx / rho) + a) / h;
-          }
-          mymax = fmax(mymax, rate);
+          rate = (fabs(mx / rho) + a) / args.h;
         }
+        mymax = fmax(mymax, rate);
+      }
+    } else {
+      // mixed form: compensated stage combination on hi + lo pairs
+      const dfl dtd = {float(dt), float(dt - double(float(dt)))};
+      const dfl third = {0.333333343f, -9.93410776e-09f};
+      const dfl two3 = {0.666666687f, -1.98682155e-08f};
+      float Th[NV], Tl[NV];
+#pragma unroll
+      for (int kv = 0; kv < NV; ++kv) {
+        int g = gvar(kv, NV, args.vn, args.vt);
+        long long a = g * args.ncell + addr;
+        dfl uk = {args.Uh[a], args.Ul[a]};
+        dfl s = df_add(uk, df_mul_f(dtd, Lv[kv]));          // U_k + dt L
+        dfl un;
+        if (args.stage == 0) {
+          un = s;
+        } else {
+          dfl u0 = {args.U0h[a], args.U0l[a]};
+          if (args.stage == 1) un = df_add(df_mul_f(u0, 0.75f), df_mul_f(s, 0.25f));
+          else un = df_add(df_mul(u0, third), df_mul(s, two3));
+        }
+        args.Uoh[a] = un.hi;
+        args.Uol[a] = un.lo;
+        Th[g] = un.hi;
+        Tl[g] = un.lo;
+      }
+      float rho = Th[0];
+      float mx = Th[1], my = NV == 4 ? Th[2] : 0.0f, E = Th[NV - 1];
+      // g = rho E - |m|^2/2 with the compensated parts (its sign decides G)
+      dfl rE = df_mul({Th[0], Tl[0]}, {Th[NV - 1], Tl[NV - 1]});
+      dfl m2 = df_mul({Th[1], Tl[1]}, {Th[1], Tl[1]});
+      if (NV == 4) m2 = df_add(m2, df_mul({Th[2], Tl[2]}, {Th[2], Tl[2]}));
+      dfl gq = df_add(rE, {-0.5f * m2.hi, -0.5f * m2.lo});
+      bool ok = (rho > 0.0f) && (gq.hi > 0.0f) && isfinite(E) && isfinite(mx) && isfinite(my);
+      if (!ok) {
+        ++nbad;
+        firstbad = min(firstbad, (unsigned long long)addr);
+      } else {
+        mymin = fmin(mymin, (double)rho);
+        float e = gq.hi / (rho * rho);
+        float a = sqrtf(float(args.gamma * (args.gamma - 1.0)) * e);
+        float rate;
+        if (NV == 4) {
+          float hx = float(args.vn == 1 ? args.h : args.h_other);
+          float hy = float(args.vn == 1 ? args.h_other : args.h);
+          rate = (fabsf(mx / rho) + a) / hx + (fabsf(my / rho) + a) / hy;
+        } else {
+          rate = (fabsf(mx / rho) + a) / float(args.h);
+        }
+        mymax = fmax(mymax, (double)rate);
       }
     }
   }
@@ -810,8 +873,8 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
       firstbad = fb < firstbad ? fb : firstbad;
     }
     if (lane == 0) {
-      atomicMin(&ctl->minrho[args.stage], double_as_ull(mymin));
-      if (args.stage == 2) atomicMax(&ctl->rate, double_as_ull(mymax));
+      atomicMin(&ctl->minrho[args.stage], double_bits(mymin));
+      if (args.stage == 2) atomicMax(&ctl->rate, double_bits(mymax));
       if (nbad) {
         atomicAdd(&ctl->nviol, (unsigned long long)nbad);
         atomicMin(&ctl->first_bad, firstbad);

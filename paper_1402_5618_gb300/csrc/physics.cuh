@@ -27,9 +27,11 @@ __device__ __forceinline__ void zratios(real um2, real um1, real u0, real up1, r
   real b1 = c13 * sqr(um1 - real(2) * u0 + up1) + real(0.25) * sqr(um1 - up1);
   real b2 = c13 * sqr(u0 - real(2) * up1 + up2) + real(0.25) * sqr(real(3) * u0 - real(4) * up1 + up2);
   real tau = fabs(b2 - b0);
-  q0 = sqr(tau / (b0 + eps));
-  q1 = sqr(tau / (b1 + eps));
-  q2 = sqr(tau / (b2 + eps));
+  real d0 = b0 + eps, d1 = b1 + eps, d2 = b2 + eps;
+  real ti = tau / (d0 * d1 * d2);   // one division for the three ratios
+  q0 = sqr(ti * d1 * d2);
+  q1 = sqr(ti * d0 * d2);
+  q2 = sqr(ti * d0 * d1);
 }
 
 // FP32 form of the same ratios, scaled so nothing overflows: with
@@ -66,10 +68,10 @@ template <typename real>
 __device__ __forceinline__ void zweights(real d0, real d1, real d2, real q0, real q1, real q2,
                                          real &w0, real &w1, real &w2, real one = real(1)) {
   real a0 = d0 * (one + q0), a1 = d1 * (one + q1), a2 = d2 * (one + q2);
-  real s = a0 + a1 + a2;
-  w0 = a0 / s;
-  w1 = a1 / s;
-  w2 = a2 / s;
+  real is = real(1) / (a0 + a1 + a2);
+  w0 = a0 * is;
+  w1 = a1 * is;
+  w2 = a2 * is;
 }
 
 // ratios in the arithmetic of the line: plain in FP64, scaled in FP32
@@ -98,12 +100,27 @@ struct Row {
 template <typename real>
 __device__ __forceinline__ Row<real> compact_row(real w0, real w1, real w2, real uprev, real u0,
                                                   real unext) {
+  const real third = real(1.0 / 3.0), sixth = real(1.0 / 6.0);
   Row<real> row;
-  row.a = (real(2) * w0 + w1) / real(3);
-  row.b = (w0 + real(2) * (w1 + w2)) / real(3);
-  row.c = w2 / real(3);
-  row.r = w0 / real(6) * uprev + (real(5) * (w0 + w1) + w2) / real(6) * u0 +
-          (w1 + real(5) * w2) / real(6) * unext;
+  row.a = (real(2) * w0 + w1) * third;
+  row.b = (w0 + real(2) * (w1 + w2)) * third;
+  row.c = w2 * third;
+  row.r = (w0 * uprev + (real(5) * (w0 + w1) + w2) * u0 + (w1 + real(5) * w2) * unext) * sixth;
+  return row;
+}
+
+// the same row from (w0, w2) alone, using w0 + w1 + w2 = 1:
+// a = (1 + w0 - w2)/3, b = (2 - w0)/3, c = w2/3,
+// r = (w0 uprev + (5 - 4 w2) u0 + (1 - w0 + 4 w2) unext) / 6
+template <typename real>
+__device__ __forceinline__ Row<real> compact_row02(real w0, real w2, real uprev, real u0,
+                                                    real unext) {
+  const real third = real(1.0 / 3.0), sixth = real(1.0 / 6.0);
+  Row<real> row;
+  row.a = (real(1) + w0 - w2) * third;
+  row.b = (real(2) - w0) * third;
+  row.c = w2 * third;
+  row.r = (w0 * uprev + (real(5) - real(4) * w2) * u0 + (real(1) - w0 + real(4) * w2) * unext) * sixth;
   return row;
 }
 
@@ -116,10 +133,11 @@ __device__ __forceinline__ real weno5z_face(real um2, real um1, real u0, real up
   real q0, q1, q2, w0, w1, w2, one;
   zratios_any(um2, um1, u0, up1, up2, eps, q0, q1, q2, one);
   zweights(real(0.1), real(0.6), real(0.3), q0, q1, q2, w0, w1, w2, one);
-  real p0 = (real(2) * um2 - real(7) * um1 + real(11) * u0) / real(6);
-  real p1 = (-um1 + real(5) * u0 + real(2) * up1) / real(6);
-  real p2 = (real(2) * u0 + real(5) * up1 - up2) / real(6);
-  return w0 * p0 + w1 * p1 + w2 * p2;
+  const real sixth = real(1.0 / 6.0);
+  real p0 = real(2) * um2 - real(7) * um1 + real(11) * u0;
+  real p1 = -um1 + real(5) * u0 + real(2) * up1;
+  real p2 = real(2) * u0 + real(5) * up1 - up2;
+  return (w0 * p0 + w1 * p1 + w2 * p2) * sixth;
 }
 
 // ---------------------------------------------------------------- Euler
@@ -161,6 +179,10 @@ __device__ __forceinline__ void hllc(const real *Ul, const real *Ur, real gamma,
   real vl = NV == 4 ? Ul[2] / rl : real(0), vr = NV == 4 ? Ur[2] / rr : real(0);
   real El = Ul[NV - 1], Er = Ur[NV - 1];
   real pl = pressure<real, NV>(Ul, gamma), pr = pressure<real, NV>(Ur, gamma);
+  if constexpr (sizeof(real) == 4) {   // FP32 form: never a NaN sound speed from rounding
+    pl = fmaxf(pl, 0.0f);
+    pr = fmaxf(pr, 0.0f);
+  }
   real al = sqrt(gamma * pl / rl), ar = sqrt(gamma * pr / rr);
   real Hl = (El + pl) / rl, Hr = (Er + pr) / rr;
   real R = sqrt(rr / rl);
@@ -217,11 +239,11 @@ __device__ __forceinline__ real energy_form(const real *w, real eps) {
 // u [(|E|+|E_w|)(|rho|+|rho_w|) + (|m|+|m_w|)^2]; the limiter asks g >= eta
 // so that the rounded limited states stay inside G
 template <typename real, int NV>
-__device__ __forceinline__ real energy_allowance(const real *ub, const real *w) {
+__device__ __forceinline__ real energy_allowance(const real *ub, const real *w, real uu) {
   real sm = real(0);
 #pragma unroll
   for (int k = 1; k < NV - 1; ++k) sm += sqr(fabs(ub[k]) + fabs(w[k]));
-  return real(16) * unit_roundoff<real>() *
+  return real(16) * uu *
          ((fabs(ub[NV - 1]) + fabs(w[NV - 1])) * (fabs(ub[0]) + fabs(w[0])) + sm);
 }
 
@@ -249,10 +271,12 @@ __device__ __forceinline__ real energy_root(const real *ub, const real *w, real 
 // bit 1 if theta_2 < 1.  theta = 1 leaves the values untouched.  Both
 // thresholds carry the round-off allowance that keeps the rounded limited
 // states in G.
+// uu is the unit round-off of the arithmetic in which the limited faces are
+// stored and used (FP64 for the plain form, FP32 for the mixed form)
 template <typename real, int NV>
-__device__ __forceinline__ int limit_cell(const real *ub, real *um, real *up, real wgl, real eps) {
+__device__ __forceinline__ int limit_cell(const real *ub, real *um, real *up, real wgl, real eps,
+                                          real uu) {
   int flags = 0;
-  const real uu = unit_roundoff<real>();
   real inv12 = real(1) / (real(1) - real(2) * wgl);
   real rho_star = (ub[0] - wgl * up[0] - wgl * um[0]) * inv12;
   real rho_min = fmin(fmin(um[0], up[0]), rho_star);
@@ -268,15 +292,15 @@ __device__ __forceinline__ int limit_cell(const real *ub, real *um, real *up, re
 #pragma unroll
   for (int k = 0; k < NV; ++k) w3[k] = (ub[k] - wgl * up[k] - wgl * um[k]) * inv12;
   {
-    real eta = energy_allowance<real, NV>(ub, um);
+    real eta = energy_allowance<real, NV>(ub, um, uu);
     if (energy_form<real, NV>(um, eps) < eta) th2 = fmin(th2, energy_root<real, NV>(ub, um, eps, eta));
   }
   {
-    real eta = energy_allowance<real, NV>(ub, up);
+    real eta = energy_allowance<real, NV>(ub, up, uu);
     if (energy_form<real, NV>(up, eps) < eta) th2 = fmin(th2, energy_root<real, NV>(ub, up, eps, eta));
   }
   {
-    real eta = energy_allowance<real, NV>(ub, w3);
+    real eta = energy_allowance<real, NV>(ub, w3, uu);
     if (energy_form<real, NV>(w3, eps) < eta) th2 = fmin(th2, energy_root<real, NV>(ub, w3, eps, eta));
   }
   if (th2 < real(1)) {
@@ -288,6 +312,45 @@ __device__ __forceinline__ int limit_cell(const real *ub, real *um, real *up, re
     flags |= 2;
   }
   return flags;
+}
+
+// Mixed form: an FP32 test of the limiter's conditions with doubled
+// allowances; only cells that may need limiting compute the scaling factors
+// theta_1, theta_2 in FP64 (with the FP32 allowance, since the limited faces
+// are stored in FP32).  Returns the limiter flags.
+template <int NV>
+__device__ __forceinline__ int limit_cell_mixed(const float *ub, float *um, float *up, float wgl,
+                                                float eps) {
+  const float uf = 5.9604645e-08f;
+  float inv12 = 1.0f / (1.0f - 2.0f * wgl);
+  float rho_star = (ub[0] - wgl * up[0] - wgl * um[0]) * inv12;
+  float rho_min = fminf(fminf(um[0], up[0]), rho_star);
+  bool need = rho_min < 2.0f * (eps + 8.0f * uf * (fabsf(ub[0]) + fabsf(rho_min)));
+  if (!need) {
+    float w3[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) w3[k] = (ub[k] - wgl * up[k] - wgl * um[k]) * inv12;
+    need = energy_form<float, NV>(um, eps) < 2.0f * energy_allowance<float, NV>(ub, um, uf) ||
+           energy_form<float, NV>(up, eps) < 2.0f * energy_allowance<float, NV>(ub, up, uf) ||
+           energy_form<float, NV>(w3, eps) < 2.0f * energy_allowance<float, NV>(ub, w3, uf);
+  }
+  if (!need) return 0;
+  double b[NV], m[NV], p[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    b[k] = ub[k];
+    m[k] = um[k];
+    p[k] = up[k];
+  }
+  int f = limit_cell<double, NV>(b, m, p, (double)wgl, (double)eps, (double)uf);
+  if (f) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      um[k] = (float)m[k];
+      up[k] = (float)p[k];
+    }
+  }
+  return f;
 }
 
 }  // namespace ppk

@@ -61,16 +61,21 @@ __global__ void step_begin_kernel(Ctl *ctl) {
   ctl->rate = 0ull;
 }
 
-// Reductions of a state: min density, max rate, cells outside G.
+// Reductions of a state: min density, max rate, cells outside G.  The
+// state is FP64 planes (lo == nullptr) or FP32 hi / lo plane pairs.
 template <int NV>
-__global__ void state_reduce_kernel(const double *U, long long ncell, long long nx, double dx,
-                                    double dy, double gamma, Ctl *ctl) {
+__global__ void state_reduce_kernel(const void *Uv, const float *lo, long long ncell, long long nx,
+                                    double dx, double dy, double gamma, Ctl *ctl) {
   double mn = 1e300, mx = 0.0;
   unsigned long long bad = 0, first = ~0ull;
+  auto at = [&](long long i) -> double {
+    if (lo) return (double)reinterpret_cast<const float *>(Uv)[i] + (double)lo[i];
+    return reinterpret_cast<const double *>(Uv)[i];
+  };
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
-    double rho = U[c], m1 = U[ncell + c], m2 = NV == 4 ? U[2 * ncell + c] : 0.0;
-    double E = U[(NV - 1) * ncell + c];
+    double rho = at(c), m1 = at(ncell + c), m2 = NV == 4 ? at(2 * ncell + c) : 0.0;
+    double E = at((NV - 1) * ncell + c);
     double e = E / rho - 0.5 * (m1 * m1 + m2 * m2) / (rho * rho);
     bool ok = rho > 0.0 && e > 0.0 && isfinite(E) && isfinite(m1) && isfinite(m2) && isfinite(rho);
     if (!ok) {
@@ -101,6 +106,23 @@ __global__ void state_reduce_kernel(const double *U, long long ncell, long long 
   }
 }
 
+// FP64 planes <-> FP32 hi / lo plane pairs (mixed form state)
+__global__ void split_kernel(const double *in, float *hi, float *lo, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double x = in[i];
+    float h = (float)x;
+    hi[i] = h;
+    lo[i] = (float)(x - (double)h);
+  }
+}
+
+__global__ void join_kernel(const float *hi, const float *lo, double *out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)hi[i] + (double)lo[i];
+}
+
 template <typename T>
 __global__ void fma_peak_kernel(T *out, int iters, T a, T b) {
   T x0 = T(threadIdx.x) * T(1e-3), x1 = x0 + T(1), x2 = x0 + T(2), x3 = x0 + T(3);
@@ -121,7 +143,7 @@ struct pp_cweno_s {
   int nv = 3;
   long long nx = 0, ny = 1, ncell = 0;
   double dx = 1, dy = 1;
-  double *U0 = nullptr, *U1 = nullptr;
+  void *U0 = nullptr, *U1 = nullptr;   // FP64 planes, or FP32 hi/lo plane pairs (mixed)
   void *D = nullptr;
   Ctl *ctl = nullptr, *ctl_scratch = nullptr;
   Ctl *hctl = nullptr;   // pinned mirror
@@ -132,6 +154,20 @@ struct pp_cweno_s {
 namespace {
 
 int cuerr(cudaError_t e) { return e == cudaSuccess ? PP_OK : PP_ERR_CUDA; }
+
+bool is_mixed(const pp_cweno_s *h) { return h->cfg.precision == PP_PREC_MIXED; }
+
+// a state buffer holds nv FP64 planes, or (mixed form) nv FP32 hi planes
+// followed by nv FP32 lo planes in the same bytes
+float *hi_of(void *p) { return reinterpret_cast<float *>(p); }
+float *lo_of(const pp_cweno_s *h, void *p) {
+  return reinterpret_cast<float *>(p) + (size_t)h->nv * (size_t)h->ncell;
+}
+
+int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
 
 double bits_to_double(unsigned long long b) {
   double d;
@@ -162,16 +198,28 @@ int check_config(const pp_cweno_config *c) {
   return PP_OK;
 }
 
-cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const double *Uin, const double *U0,
-                   const void *Din, void *Dout, double *Uout, int stage, double eps_fixed,
-                   Ctl *ctl, bool attrs_only = false) {
+// Uin, U0, Uout are state buffers (FP64 planes or FP32 hi/lo pairs);
+// Lout (OPERATOR mode) is FP64 planes
+cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const void *Uin, const void *U0,
+                   const void *Din, void *Dout, void *Uout, int stage, double eps_fixed,
+                   Ctl *ctl, bool attrs_only = false, double *Lout = nullptr) {
   SweepArgs a;
   memset(&a, 0, sizeof(a));
-  a.U = Uin;
-  a.U0 = U0;
+  if (is_mixed(h)) {
+    a.Uh = hi_of(const_cast<void *>(Uin));
+    a.Ul = Uin ? lo_of(h, const_cast<void *>(Uin)) : nullptr;
+    a.U0h = hi_of(const_cast<void *>(U0));
+    a.U0l = U0 ? lo_of(h, const_cast<void *>(U0)) : nullptr;
+    a.Uoh = hi_of(Uout);
+    a.Uol = Uout ? lo_of(h, Uout) : nullptr;
+  } else {
+    a.U = reinterpret_cast<const double *>(Uin);
+    a.U0 = reinterpret_cast<const double *>(U0);
+    a.Uout = reinterpret_cast<double *>(Uout);
+  }
   a.Din = Din;
   a.Dout = Dout;
-  a.Uout = Uout;
+  a.Lout = Lout;
   a.ncell = h->ncell;
   a.gamma = h->cfg.gamma;
   a.wgl = h->cfg.gl_weight;
@@ -223,8 +271,8 @@ cudaError_t enqueue_step(pp_cweno_s *h) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int s = 0; s < 3; ++s) {
-    const double *Uin = s == 0 ? h->U0 : h->U1;
-    double *Uout = s == 2 ? h->U0 : h->U1;
+    const void *Uin = s == 0 ? h->U0 : h->U1;
+    void *Uout = s == 2 ? h->U0 : h->U1;
     if (h->nv == 4) {
       e = launch(h, MODE_XSWEEP, true, Uin, h->U0, nullptr, h->D, nullptr, s, 0.0, h->ctl);
       if (e != cudaSuccess) return e;
@@ -260,7 +308,7 @@ int build_graph(pp_cweno_s *h) {
   return cuerr(e);
 }
 
-int reduce_state(pp_cweno_s *h, const double *U, Ctl *ctl) {
+int reduce_state(pp_cweno_s *h, const void *U, Ctl *ctl, bool split_planes) {
   Ctl z;
   memset(&z, 0, sizeof(z));
   z.minrho[2] = 0x7ff0000000000000ull;  // +inf
@@ -269,11 +317,12 @@ int reduce_state(pp_cweno_s *h, const double *U, Ctl *ctl) {
   if (e != cudaSuccess) return PP_ERR_CUDA;
   int blocks = (int)fmin(1184.0, (double)((h->ncell + 255) / 256));
   if (blocks < 1) blocks = 1;
+  const float *lo = split_planes ? lo_of(h, const_cast<void *>(U)) : nullptr;
   if (h->nv == 4)
-    state_reduce_kernel<4><<<blocks, 256, 0, h->stream>>>(U, h->ncell, h->nx, h->dx, h->dy,
+    state_reduce_kernel<4><<<blocks, 256, 0, h->stream>>>(U, lo, h->ncell, h->nx, h->dx, h->dy,
                                                           h->cfg.gamma, ctl);
   else
-    state_reduce_kernel<3><<<blocks, 256, 0, h->stream>>>(U, h->ncell, h->nx, h->dx, h->dy,
+    state_reduce_kernel<3><<<blocks, 256, 0, h->stream>>>(U, lo, h->ncell, h->nx, h->dx, h->dy,
                                                           h->cfg.gamma, ctl);
   return cuerr(cudaGetLastError());
 }
@@ -381,11 +430,23 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
 int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) {
   if (!h || !U || !isfinite(t0)) return PP_ERR_ARG;
   size_t bytes = sizeof(double) * (size_t)h->nv * (size_t)h->ncell;
-  cudaError_t e = cudaMemcpyAsync(h->U0, U, bytes,
-                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                  h->stream);
+  long long nval = (long long)h->nv * h->ncell;
+  cudaError_t e;
+  if (is_mixed(h)) {
+    const double *src = U;
+    if (!on_device) {   // stage through the (idle) stage buffer
+      e = cudaMemcpyAsync(h->U1, U, bytes, cudaMemcpyHostToDevice, h->stream);
+      if (e != cudaSuccess) return PP_ERR_CUDA;
+      src = reinterpret_cast<const double *>(h->U1);
+    }
+    split_kernel<<<grid_for(nval), 256, 0, h->stream>>>(src, hi_of(h->U0), lo_of(h, h->U0), nval);
+    e = cudaGetLastError();
+  } else {
+    e = cudaMemcpyAsync(h->U0, U, bytes,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+  }
   if (e != cudaSuccess) return PP_ERR_CUDA;
-  int rc = reduce_state(h, h->U0, h->ctl);
+  int rc = reduce_state(h, h->U0, h->ctl, is_mixed(h));
   if (rc) return rc;
   if ((rc = pull_ctl(h))) return rc;
   Ctl *c = h->hctl;
@@ -412,9 +473,18 @@ int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) 
 int pp_cweno_get_state(pp_cweno_t h, double *U, int on_device, double *t, int64_t *steps) {
   if (!h || !U) return PP_ERR_ARG;
   size_t bytes = sizeof(double) * (size_t)h->nv * (size_t)h->ncell;
-  cudaError_t e = cudaMemcpyAsync(U, h->U0, bytes,
-                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                  h->stream);
+  long long nval = (long long)h->nv * h->ncell;
+  cudaError_t e;
+  if (is_mixed(h)) {
+    double *dst = on_device ? U : reinterpret_cast<double *>(h->U1);
+    join_kernel<<<grid_for(nval), 256, 0, h->stream>>>(hi_of(h->U0), lo_of(h, h->U0), dst, nval);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && !on_device)
+      e = cudaMemcpyAsync(U, h->U1, bytes, cudaMemcpyDeviceToHost, h->stream);
+  } else {
+    e = cudaMemcpyAsync(U, h->U0, bytes,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  }
   if (e != cudaSuccess) return PP_ERR_CUDA;
   int rc = pull_ctl(h);
   if (rc) return rc;
@@ -506,8 +576,15 @@ int pp_cweno_enqueue_steps(pp_cweno_t h, int64_t nsteps) {
 int pp_cweno_operator(pp_cweno_t h, const double *U_dev, double *L_dev, double eps) {
   if (!h || !U_dev || !L_dev) return PP_ERR_ARG;
   int rc;
+  const void *Uin = U_dev;
+  if (is_mixed(h)) {   // the line kernels read FP32 hi / lo planes
+    long long nval = (long long)h->nv * h->ncell;
+    split_kernel<<<grid_for(nval), 256, 0, h->stream>>>(U_dev, hi_of(h->U1), lo_of(h, h->U1), nval);
+    if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
+    Uin = h->U1;
+  }
   if (!(eps > 0.0)) {
-    if ((rc = reduce_state(h, U_dev, h->ctl_scratch))) return rc;
+    if ((rc = reduce_state(h, U_dev, h->ctl_scratch, false))) return rc;
     Ctl tmp;
     if (cudaMemcpyAsync(&tmp, h->ctl_scratch, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
       return PP_ERR_CUDA;
@@ -523,11 +600,13 @@ int pp_cweno_operator(pp_cweno_t h, const double *U_dev, double *L_dev, double e
     return PP_ERR_CUDA;
   cudaError_t e;
   if (h->nv == 4) {
-    e = launch(h, MODE_XSWEEP, true, U_dev, U_dev, nullptr, h->D, nullptr, 0, eps, h->ctl_scratch);
+    e = launch(h, MODE_XSWEEP, true, Uin, Uin, nullptr, h->D, nullptr, 0, eps, h->ctl_scratch);
     if (e == cudaSuccess)
-      e = launch(h, MODE_OPERATOR, false, U_dev, U_dev, h->D, nullptr, L_dev, 0, eps, h->ctl_scratch);
+      e = launch(h, MODE_OPERATOR, false, Uin, Uin, h->D, nullptr, nullptr, 0, eps, h->ctl_scratch,
+                 false, L_dev);
   } else {
-    e = launch(h, MODE_OPERATOR, true, U_dev, U_dev, nullptr, nullptr, L_dev, 0, eps, h->ctl_scratch);
+    e = launch(h, MODE_OPERATOR, true, Uin, Uin, nullptr, nullptr, nullptr, 0, eps, h->ctl_scratch,
+               false, L_dev);
   }
   if (e != cudaSuccess) return PP_ERR_CUDA;
   return cuerr(cudaStreamSynchronize(h->stream));
@@ -548,7 +627,7 @@ int pp_cweno_stats(pp_cweno_t h, pp_cweno_stats_t *out) {
   out->first_bad_cell = c->nviol ? (int64_t)c->first_bad : -1;
   out->t = c->t;
   out->last_dt = c->last_dt;
-  if ((rc = reduce_state(h, h->U0, h->ctl_scratch))) return rc;
+  if ((rc = reduce_state(h, h->U0, h->ctl_scratch, is_mixed(h)))) return rc;
   Ctl tmp;
   if (cudaMemcpyAsync(&tmp, h->ctl_scratch, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     return PP_ERR_CUDA;
@@ -596,8 +675,8 @@ int pp_cweno_profile_step(pp_cweno_t h, float *ms, int nmax, int *nk) {
   step_begin_kernel<<<1, 32, 0, h->stream>>>(h->ctl);
   cudaEventRecord(ev[++idx], h->stream);
   for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
-    const double *Uin = s == 0 ? h->U0 : h->U1;
-    double *Uout = s == 2 ? h->U0 : h->U1;
+    const void *Uin = s == 0 ? h->U0 : h->U1;
+    void *Uout = s == 2 ? h->U0 : h->U1;
     if (h->nv == 4) {
       e = launch(h, MODE_XSWEEP, true, Uin, h->U0, nullptr, h->D, nullptr, s, 0.0, h->ctl);
       cudaEventRecord(ev[++idx], h->stream);

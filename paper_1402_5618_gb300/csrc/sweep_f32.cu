@@ -5,6 +5,6 @@
 namespace ppk {
 cudaError_t launch_sweep_f32(const LaunchCfg &c, const SweepArgs &a, long long nlines,
                              cudaStream_t st) {
-  return launch_dispatch<float, float>(c, a, nlines, st);
+  return launch_dispatch<float>(c, a, nlines, st);
 }
 }  // namespace ppk

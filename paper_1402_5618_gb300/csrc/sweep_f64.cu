@@ -4,6 +4,6 @@
 namespace ppk {
 cudaError_t launch_sweep_f64(const LaunchCfg &c, const SweepArgs &a, long long nlines,
                              cudaStream_t st) {
-  return launch_dispatch<double, double>(c, a, nlines, st);
+  return launch_dispatch<double>(c, a, nlines, st);
 }
 }  // namespace ppk

@@ -26,10 +26,10 @@ cudaError_t launch_sweep_f64(const LaunchCfg &c, const SweepArgs &a, long long n
 cudaError_t launch_sweep_f32(const LaunchCfg &c, const SweepArgs &a, long long nlines,
                              cudaStream_t st);
 
-template <typename real, int NV, bool PER, int MODE, typename dreal>
+template <typename real, int NV, bool PER, int MODE>
 cudaError_t launch_one(const SweepArgs &a, long long nlines, cudaStream_t st, bool attrs_only) {
   using S = Smem<real, NV, M_ROWS>;
-  auto kern = line_sweep<real, NV, M_ROWS, PER, MODE, dreal>;
+  auto kern = line_sweep<real, NV, M_ROWS, PER, MODE>;
   if (attrs_only) {   // called at handle creation, outside any stream capture
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::bytes);
@@ -51,28 +51,28 @@ cudaError_t launch_one(const SweepArgs &a, long long nlines, cudaStream_t st, bo
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <typename real, typename dreal>
+template <typename real>
 cudaError_t launch_dispatch(const LaunchCfg &c, const SweepArgs &a, long long nlines,
                             cudaStream_t st) {
   if (c.nv == 3) {
     if (c.mode == MODE_FINAL)
-      return c.periodic ? launch_one<real, 3, true, MODE_FINAL, dreal>(a, nlines, st, c.attrs_only)
-                        : launch_one<real, 3, false, MODE_FINAL, dreal>(a, nlines, st, c.attrs_only);
+      return c.periodic ? launch_one<real, 3, true, MODE_FINAL>(a, nlines, st, c.attrs_only)
+                        : launch_one<real, 3, false, MODE_FINAL>(a, nlines, st, c.attrs_only);
     if (c.mode == MODE_OPERATOR)
-      return c.periodic ? launch_one<real, 3, true, MODE_OPERATOR, dreal>(a, nlines, st, c.attrs_only)
-                        : launch_one<real, 3, false, MODE_OPERATOR, dreal>(a, nlines, st, c.attrs_only);
+      return c.periodic ? launch_one<real, 3, true, MODE_OPERATOR>(a, nlines, st, c.attrs_only)
+                        : launch_one<real, 3, false, MODE_OPERATOR>(a, nlines, st, c.attrs_only);
     return cudaErrorInvalidValue;
   }
   if (c.nv == 4) {
     if (c.mode == MODE_XSWEEP)
-      return c.periodic ? launch_one<real, 4, true, MODE_XSWEEP, dreal>(a, nlines, st, c.attrs_only)
-                        : launch_one<real, 4, false, MODE_XSWEEP, dreal>(a, nlines, st, c.attrs_only);
+      return c.periodic ? launch_one<real, 4, true, MODE_XSWEEP>(a, nlines, st, c.attrs_only)
+                        : launch_one<real, 4, false, MODE_XSWEEP>(a, nlines, st, c.attrs_only);
     if (c.mode == MODE_FINAL)
-      return c.periodic ? launch_one<real, 4, true, MODE_FINAL, dreal>(a, nlines, st, c.attrs_only)
-                        : launch_one<real, 4, false, MODE_FINAL, dreal>(a, nlines, st, c.attrs_only);
+      return c.periodic ? launch_one<real, 4, true, MODE_FINAL>(a, nlines, st, c.attrs_only)
+                        : launch_one<real, 4, false, MODE_FINAL>(a, nlines, st, c.attrs_only);
     if (c.mode == MODE_OPERATOR)
-      return c.periodic ? launch_one<real, 4, true, MODE_OPERATOR, dreal>(a, nlines, st, c.attrs_only)
-                        : launch_one<real, 4, false, MODE_OPERATOR, dreal>(a, nlines, st, c.attrs_only);
+      return c.periodic ? launch_one<real, 4, true, MODE_OPERATOR>(a, nlines, st, c.attrs_only)
+                        : launch_one<real, 4, false, MODE_OPERATOR>(a, nlines, st, c.attrs_only);
   }
   return cudaErrorInvalidValue;
 }

@@ -1,0 +1,110 @@
+"""The mixed form (FP32 line arithmetic, compensated FP32 hi+lo state, FP64
+limiter factors) against the FP64 oracle and the exact solution.
+
+Its results cannot match the oracle to FP64 rounding; the checks are the
+ones its purpose sets: the operator agrees with the oracle to FP32 accuracy
+on the flux scale, smooth data keep an L1 error against the closed form
+within 2x of the FP64 path's, and positivity-critical data run without a
+single cell leaving the admissible set."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_5618_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_5618_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _grid(p):
+    return oracle.make_grid(p.ndim, p.nx, p.ny, p.dx, p.dy, p.gamma, p.bc)
+
+
+def _flux_scale(p, U):
+    nv = U.shape[0]
+    flat = U.reshape(nv, -1)
+    rho = flat[0]
+    vel = np.sqrt(np.sum(flat[1:nv - 1] ** 2, axis=0)) / rho
+    pr = (p.gamma - 1) * (flat[nv - 1] - 0.5 * rho * vel ** 2)
+    smax = np.max(vel + np.sqrt(p.gamma * np.maximum(pr, 0) / rho))
+    mom = np.abs(rho * vel * vel + pr).max()
+    F = [np.abs(rho * vel).max(), mom] + ([mom] if nv == 4 else [])
+    F.append(np.abs(vel * (flat[nv - 1] + pr)).max())
+    h = min(p.dx, p.dy) if p.ndim == 2 else p.dx
+    return np.array([(F[v] + np.abs(flat[v]).max() * smax) / h for v in range(nv)])
+
+
+@pytest.mark.parametrize("name,make,tol", [
+    ("vortex_64", lambda: W.vortex_2d(64), 2e-6),
+    ("smooth_1d_1500", lambda: W.random_smooth_1d(1500, stream=52), 2e-6),
+    ("jumps_600x530", lambda: W.random_jumps_2d(600, 530, stream=61), 1e-4),
+    ("riemann_1300", lambda: W.riemann_1d(1300, (1.0, 0.75, 1.0), (0.125, -0.3, 0.1), bc=(2, 1)), 1e-4),
+])
+def test_mixed_operator_close_to_oracle(B, name, make, tol):
+    p = make()
+    eps = min(1e-13, p.U0[0].min())
+    Lo, _ = oracle.operator(_grid(p), p.U0, eps)
+    s = B.Solver(B.config_from_problem(p, B.PREC_MIXED))
+    Ud = torch.from_numpy(np.ascontiguousarray(p.U0).ravel()).cuda()
+    Ld = torch.zeros_like(Ud)
+    s.operator(Ud, Ld, eps)
+    s.close()
+    Lg = Ld.cpu().numpy().reshape(p.U0.shape)
+    scale = _flux_scale(p, p.U0)
+    for v in range(p.U0.shape[0]):
+        assert np.abs(Lg[v] - Lo[v]).max() <= tol * scale[v], (v, np.abs(Lg[v] - Lo[v]).max() / scale[v])
+
+
+def _run(B, p, prec, t_final=None, max_steps=10**9):
+    s = B.Solver(B.config_from_problem(p, prec))
+    s.set_state(np.ascontiguousarray(p.U0).ravel())
+    n, rc = s.advance(p.t_final if t_final is None else t_final, max_steps, check=False)
+    U, t, steps = s.get_state()
+    st = s.stats()
+    s.close()
+    return U.reshape(p.U0.shape), steps, rc, st
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_mixed_vortex_error_within_2x_fp64(B, n):
+    """Smooth data: L1 density error against the translated closed-form
+    vortex within 2x of the FP64 path's."""
+    p = W.vortex_2d(n, t_final=1.0)
+    ex = W.vortex_2d(n, t=1.0).U0
+    U64, s64, rc64, _ = _run(B, p, B.PREC_FP64)
+    U32, s32, rc32, st = _run(B, p, B.PREC_MIXED)
+    assert rc64 == 0 and rc32 == 0 and st.violations == 0
+    e64 = np.mean(np.abs(U64[0] - ex[0]))
+    e32 = np.mean(np.abs(U32[0] - ex[0]))
+    assert e32 <= 2.0 * e64, (e32, e64)
+
+
+def test_mixed_blast_positivity_and_agreement(B):
+    """Corner blast at the positivity CFL: no cell leaves G in the mixed
+    form, and the mixed and FP64 states stay close in relative L1."""
+    p = W.blast_2d(256, cfl=1 / 12, t_final=1e-3)
+    U64, s64, rc64, st64 = _run(B, p, B.PREC_FP64, max_steps=150)
+    U32, s32, rc32, st32 = _run(B, p, B.PREC_MIXED, max_steps=150)
+    assert st64.violations == 0 and st32.violations == 0
+    assert rc32 in (0, B.PP_ERR_STEPS)
+    rel = np.abs(U32[0] - U64[0]).sum() / np.abs(U64[0]).sum()
+    assert rel < 1e-3, rel
+
+
+def test_mixed_1d_riemann_positivity(B):
+    """Near-vacuum double rarefaction (Sec. 3) in the mixed form."""
+    p = W.paper_riemann("123", 400, cfl=1 / 24)
+    U, steps, rc, st = _run(B, p, B.PREC_MIXED)
+    assert rc == 0 and st.violations == 0
+    rho = U[0]
+    e = U[2] / rho - 0.5 * (U[1] / rho) ** 2
+    assert np.all(rho > 0) and np.all(e > 0)

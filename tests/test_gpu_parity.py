@@ -53,9 +53,8 @@ def _scale(p, U):
     vel = np.sqrt(np.sum(flat[1:nv - 1] ** 2, axis=0)) / rho
     pr = (p.gamma - 1) * (flat[nv - 1] - 0.5 * rho * vel ** 2)
     smax = np.max(vel + np.sqrt(p.gamma * np.maximum(pr, 0) / rho))
-    F = [np.abs(flat[1]).max(), np.abs(flat[1] * vel + pr).max()]
-    if nv == 4:
-        F.append(np.abs(flat[2] * vel).max())
+    mom = np.abs(rho * vel * vel + pr).max()      # both momentum components carry p
+    F = [np.abs(rho * vel).max(), mom] + ([mom] if nv == 4 else [])
     F.append(np.abs(vel * (flat[nv - 1] + pr)).max())
     h = min(p.dx, p.dy) if p.ndim == 2 else p.dx
     return np.array([(F[v] + np.abs(flat[v]).max() * smax) / h for v in range(nv)])
