@@ -65,6 +65,20 @@ struct Ctl {
 
 enum { MODE_XSWEEP = 0, MODE_FINAL = 1, MODE_OPERATOR = 2 };
 
+// one problem of a batch: its block of the concatenated state (values
+// [off, off + nv*ncell), variable planes of ncell cells) and grid
+struct ProbDesc {
+  long long off, ncell;
+  int nx, ny;
+  double dx, dy;
+  int bc[4];
+};
+
+// one line of a batched launch: problem index and line index inside it
+struct LineRef {
+  int prob, line;
+};
+
 struct SweepArgs {
   // plain form: FP64 planes [nv][ncell]
   const double *U;    // stage input
@@ -88,7 +102,41 @@ struct SweepArgs {
   double eps_fixed;   // > 0: fixed limiter epsilon, no control-block checks (operator evaluation)
   int limiter;
   Ctl *ctl;
+  // batched launch: line table and problem descriptors (nullptr: one problem)
+  const LineRef *lines;
+  const ProbDesc *probs;
+  int xdir;           // batched launch: 1 x lines, 0 y lines
+  long long nvals;    // batched mixed form: values per hi block (lo block follows)
 };
+
+// resolve the line a cluster works on: for a batched launch, take the
+// problem's grid, boundaries, control block and its slice of every buffer
+template <int NV>
+__device__ __forceinline__ void bind_line(SweepArgs &a, long long &line) {
+  if (!a.lines) return;
+  LineRef lr = a.lines[line];
+  const ProbDesc pd = a.probs[lr.prob];
+  line = lr.line;
+  a.ctl = a.ctl + lr.prob;
+  a.ncell = pd.ncell;
+  if (a.xdir) {
+    a.n = pd.nx; a.cell_stride = 1; a.line_stride = pd.nx;
+    a.bclo = pd.bc[0]; a.bchi = pd.bc[1];
+    a.h = pd.dx; a.h_other = NV == 4 ? pd.dy : 0.0;
+  } else {
+    a.n = pd.ny; a.cell_stride = pd.nx; a.line_stride = 1;
+    a.bclo = pd.bc[2]; a.bchi = pd.bc[3];
+    a.h = pd.dy; a.h_other = pd.dx;
+  }
+  const long long o = pd.off;
+  if (a.U) a.U += o;
+  if (a.U0) a.U0 += o;
+  if (a.Uout) a.Uout += o;
+  if (a.Uh) { a.Uh += o; a.Ul = a.Uh + a.nvals; }
+  if (a.U0h) { a.U0h += o; a.U0l = a.U0h + a.nvals; }
+  if (a.Uoh) { a.Uoh += o; a.Uol = a.Uoh + a.nvals; }
+  if (a.Lout) a.Lout += o;
+}
 
 // ---------------------------------------------------------------- maps
 // Forward elimination map of a run of rows acting on the projective state
@@ -256,7 +304,7 @@ __device__ __forceinline__ double bits_double(unsigned long long b) {
 
 // ---------------------------------------------------------------- kernel
 template <typename real, int NV, int M, bool PER, int MODE>
-__global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
+__global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args_in) {
   constexpr bool MIXED = sizeof(real) == 4;
   using S = Smem<real, NV, M>;
   constexpr int SEG = S::SEG;
@@ -272,9 +320,16 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args) {
   Exch<real, NV> &ex = *reinterpret_cast<Exch<real, NV> *>(smem_raw + S::ex_off);
 
   cg::cluster_group cluster = cg::this_cluster();
+  SweepArgs args = args_in;
   const int R = args.R;
   const int rank = (int)cluster.block_rank();
-  const long long line = blockIdx.x / R;
+  long long line = blockIdx.x / R;
+  bind_line<NV>(args, line);
+  if (args.lines) {   // D buffers follow the state layout of the batch
+    const long long o = args.probs[args_in.lines[blockIdx.x / R].prob].off;
+    if (args.Din) args.Din = reinterpret_cast<const real *>(args.Din) + o;
+    if (args.Dout) args.Dout = reinterpret_cast<real *>(args.Dout) + o;
+  }
   const int n = args.n;
   const int lo = rank * SEG;
   const int hi = min(lo + SEG, n);

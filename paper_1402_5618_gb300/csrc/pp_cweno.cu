@@ -16,6 +16,8 @@
 #include <string.h>
 
 #include <new>
+#include <algorithm>
+#include <vector>
 
 #include "../../include/pp_cweno.h"
 #include "sweeps.cuh"
@@ -35,8 +37,10 @@ __device__ __forceinline__ double bitsd(unsigned long long b) {
 
 // Start of a step: dt from the max rate of U^n, the last step cut to land on
 // t_final, reductions of this step reset.
-__global__ void step_begin_kernel(Ctl *ctl) {
-  if (threadIdx.x != 0) return;
+__global__ void step_begin_kernel(Ctl *ctls, int nprob) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  Ctl *ctl = ctls + p;
   ctl->active = 0;
   if (ctl->done || ctl->nviol) return;
   if (ctl->step >= ctl->step_limit) { ctl->err_steps = 1; return; }
@@ -106,6 +110,53 @@ __global__ void state_reduce_kernel(const void *Uv, const float *lo, long long n
   }
 }
 
+// Batched form of the same reductions: one block per problem.
+template <int NV>
+__global__ void batch_reduce_kernel(const void *Uv, const float *lo, const ProbDesc *probs,
+                                    double gamma, Ctl *ctls) {
+  const ProbDesc pd = probs[blockIdx.x];
+  Ctl *ctl = ctls + blockIdx.x;
+  double mn = 1e300, mx = 0.0;
+  unsigned long long bad = 0, first = ~0ull;
+  auto at = [&](long long i) -> double {
+    i += pd.off;
+    if (lo) return (double)reinterpret_cast<const float *>(Uv)[i] + (double)lo[i];
+    return reinterpret_cast<const double *>(Uv)[i];
+  };
+  const long long nc = pd.ncell;
+  for (long long c = threadIdx.x; c < nc; c += blockDim.x) {
+    double rho = at(c), m1 = at(nc + c), m2 = NV == 4 ? at(2 * nc + c) : 0.0;
+    double E = at((NV - 1) * nc + c);
+    double e = E / rho - 0.5 * (m1 * m1 + m2 * m2) / (rho * rho);
+    bool ok = rho > 0.0 && e > 0.0 && isfinite(E) && isfinite(m1) && isfinite(m2) && isfinite(rho);
+    if (!ok) {
+      ++bad;
+      first = (unsigned long long)c < first ? (unsigned long long)c : first;
+      continue;
+    }
+    mn = fmin(mn, rho);
+    double a = sqrt(gamma * (gamma - 1.0) * e);
+    double r = (fabs(m1 / rho) + a) / pd.dx;
+    if (NV == 4) r += (fabs(m2 / rho) + a) / pd.dy;
+    mx = fmax(mx, r);
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, d));
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, d));
+    bad += __shfl_down_sync(0xffffffffu, bad, d);
+    unsigned long long f = __shfl_down_sync(0xffffffffu, first, d);
+    first = f < first ? f : first;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&ctl->minrho[2], dbits(mn));
+    atomicMax(&ctl->rate, dbits(mx));
+    if (bad) {
+      atomicAdd(&ctl->nviol, bad);
+      atomicMin(&ctl->first_bad, first);
+    }
+  }
+}
+
 // FP64 planes <-> FP32 hi / lo plane pairs (mixed form state)
 __global__ void split_kernel(const double *in, float *hi, float *lo, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -137,18 +188,34 @@ __global__ void fma_peak_kernel(T *out, int iters, T a, T b) {
 
 }  // namespace
 
+// a batched launch group: lines of equal cluster size and boundary kind
+struct LineGroup {
+  int R;
+  bool periodic;
+  bool xdir;
+  LineRef *lines = nullptr;   // device
+  long long nlines = 0;
+};
+
 struct pp_cweno_s {
-  pp_cweno_config cfg;
+  pp_cweno_config cfg;        // single problem: its config; batch: the shared fields
   cudaStream_t stream = nullptr;
   int nv = 3;
-  long long nx = 0, ny = 1, ncell = 0;
+  long long nx = 0, ny = 1, ncell = 0;   // single problem; batch: ncell = all cells
   double dx = 1, dy = 1;
   void *U0 = nullptr, *U1 = nullptr;   // FP64 planes, or FP32 hi/lo plane pairs (mixed)
   void *D = nullptr;
-  Ctl *ctl = nullptr, *ctl_scratch = nullptr;
-  Ctl *hctl = nullptr;   // pinned mirror
+  Ctl *ctl = nullptr, *ctl_scratch = nullptr;   // [nprob]
+  Ctl *hctl = nullptr;   // pinned mirror [nprob]
   cudaGraphExec_t graph = nullptr;
   long long launches_per_step = 0;
+  // batch
+  bool batch = false;
+  int nprob = 1;
+  std::vector<ProbDesc> probs_h;
+  std::vector<pp_cweno_config> cfgs;
+  ProbDesc *probs = nullptr;   // device
+  std::vector<LineGroup> groups;
 };
 
 namespace {
@@ -157,12 +224,13 @@ int cuerr(cudaError_t e) { return e == cudaSuccess ? PP_OK : PP_ERR_CUDA; }
 
 bool is_mixed(const pp_cweno_s *h) { return h->cfg.precision == PP_PREC_MIXED; }
 
-// a state buffer holds nv FP64 planes, or (mixed form) nv FP32 hi planes
-// followed by nv FP32 lo planes in the same bytes
+// a state buffer holds nv FP64 planes per problem, or (mixed form) the FP32
+// hi values of all problems followed by their FP32 lo values in the same bytes
 float *hi_of(void *p) { return reinterpret_cast<float *>(p); }
 float *lo_of(const pp_cweno_s *h, void *p) {
-  return reinterpret_cast<float *>(p) + (size_t)h->nv * (size_t)h->ncell;
+  return p ? reinterpret_cast<float *>(p) + (size_t)h->nv * (size_t)h->ncell : nullptr;
 }
+long long nvals(const pp_cweno_s *h) { return (long long)h->nv * h->ncell; }
 
 int grid_for(long long n) {
   long long b = (n + 255) / 256;
@@ -198,29 +266,11 @@ int check_config(const pp_cweno_config *c) {
   return PP_OK;
 }
 
-// Uin, U0, Uout are state buffers (FP64 planes or FP32 hi/lo pairs);
-// Lout (OPERATOR mode) is FP64 planes
-cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const void *Uin, const void *U0,
-                   const void *Din, void *Dout, void *Uout, int stage, double eps_fixed,
-                   Ctl *ctl, bool attrs_only = false, double *Lout = nullptr) {
-  SweepArgs a;
-  memset(&a, 0, sizeof(a));
-  if (is_mixed(h)) {
-    a.Uh = hi_of(const_cast<void *>(Uin));
-    a.Ul = Uin ? lo_of(h, const_cast<void *>(Uin)) : nullptr;
-    a.U0h = hi_of(const_cast<void *>(U0));
-    a.U0l = U0 ? lo_of(h, const_cast<void *>(U0)) : nullptr;
-    a.Uoh = hi_of(Uout);
-    a.Uol = Uout ? lo_of(h, Uout) : nullptr;
-  } else {
-    a.U = reinterpret_cast<const double *>(Uin);
-    a.U0 = reinterpret_cast<const double *>(U0);
-    a.Uout = reinterpret_cast<double *>(Uout);
-  }
-  a.Din = Din;
-  a.Dout = Dout;
-  a.Lout = Lout;
-  a.ncell = h->ncell;
+double effective_cfl(const pp_cweno_config &c) {
+  return c.cfl_positivity_cap ? fmin(c.cfl, c.gl_weight) : c.cfl;
+}
+
+void fill_common(const pp_cweno_s *h, SweepArgs &a, int stage, double eps_fixed, Ctl *ctl) {
   a.gamma = h->cfg.gamma;
   a.wgl = h->cfg.gl_weight;
   a.eps_weno = h->cfg.eps_weno;
@@ -228,8 +278,49 @@ cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const void *Uin, co
   a.eps_fixed = eps_fixed;
   a.limiter = h->cfg.limiter;
   a.ctl = ctl;
+}
+
+void fill_state(const pp_cweno_s *h, SweepArgs &a, const void *Uin, const void *U0, void *Uout) {
+  if (is_mixed(h)) {
+    a.Uh = hi_of(const_cast<void *>(Uin));
+    a.Ul = lo_of(h, const_cast<void *>(Uin));
+    a.U0h = hi_of(const_cast<void *>(U0));
+    a.U0l = lo_of(h, const_cast<void *>(U0));
+    a.Uoh = hi_of(Uout);
+    a.Uol = lo_of(h, Uout);
+  } else {
+    a.U = reinterpret_cast<const double *>(Uin);
+    a.U0 = reinterpret_cast<const double *>(U0);
+    a.Uout = reinterpret_cast<double *>(Uout);
+  }
+}
+
+cudaError_t dispatch(const pp_cweno_s *h, int mode, bool periodic, const SweepArgs &a,
+                     long long nlines, bool attrs_only) {
+  LaunchCfg c;
+  c.precision = h->cfg.precision;
+  c.nv = h->nv;
+  c.periodic = periodic;
+  c.mode = mode;
+  c.attrs_only = attrs_only;
+  return h->cfg.precision == PP_PREC_FP64 ? launch_sweep_f64(c, a, nlines, h->stream)
+                                         : launch_sweep_f32(c, a, nlines, h->stream);
+}
+
+// Single-problem launch.  Uin, U0, Uout are state buffers (FP64 planes or
+// FP32 hi/lo pairs); Lout (OPERATOR mode) is FP64 planes.
+cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const void *Uin, const void *U0,
+                   const void *Din, void *Dout, void *Uout, int stage, double eps_fixed,
+                   Ctl *ctl, bool attrs_only = false, double *Lout = nullptr) {
+  SweepArgs a;
+  memset(&a, 0, sizeof(a));
+  fill_state(h, a, Uin, U0, Uout);
+  fill_common(h, a, stage, eps_fixed, ctl);
+  a.Din = Din;
+  a.Dout = Dout;
+  a.Lout = Lout;
+  a.ncell = h->ncell;
   long long nlines;
-  bool periodic;
   if (xdir) {
     a.n = (int)h->nx;
     a.cell_stride = 1;
@@ -253,41 +344,66 @@ cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const void *Uin, co
     a.h = h->dy;
     a.h_other = h->dx;
   }
-  periodic = a.bclo == PP_BC_PERIODIC;
   a.R = seg_count(a.n);
-  LaunchCfg c;
-  c.precision = h->cfg.precision;
-  c.nv = h->nv;
-  c.periodic = periodic;
-  c.mode = mode;
-  c.attrs_only = attrs_only;
-  return h->cfg.precision == PP_PREC_FP64 ? launch_sweep_f64(c, a, nlines, h->stream)
-                                         : launch_sweep_f32(c, a, nlines, h->stream);
+  return dispatch(h, mode, a.bclo == PP_BC_PERIODIC, a, nlines, attrs_only);
 }
 
-// enqueue one step (begin kernel + 3 stages)
+// Batched launch of one line group.
+cudaError_t launch_group(const pp_cweno_s *h, const LineGroup &g, int mode, const void *Uin,
+                         const void *U0, const void *Din, void *Dout, void *Uout, int stage,
+                         bool attrs_only = false) {
+  SweepArgs a;
+  memset(&a, 0, sizeof(a));
+  fill_state(h, a, Uin, U0, Uout);
+  fill_common(h, a, stage, 0.0, h->ctl);
+  a.Din = Din;
+  a.Dout = Dout;
+  a.R = g.R;
+  a.lines = g.lines;
+  a.probs = h->probs;
+  a.xdir = g.xdir ? 1 : 0;
+  a.nvals = nvals(h);
+  a.vn = g.xdir ? 1 : 2;
+  a.vt = h->nv == 4 ? (g.xdir ? 2 : 1) : -1;
+  return dispatch(h, mode, g.periodic, a, g.nlines, attrs_only);
+}
+
+// enqueue one step: the per-problem dt kernel, then 3 stages
 cudaError_t enqueue_step(pp_cweno_s *h) {
-  step_begin_kernel<<<1, 32, 0, h->stream>>>(h->ctl);
+  step_begin_kernel<<<(h->nprob + 127) / 128, 128, 0, h->stream>>>(h->ctl, h->nprob);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int s = 0; s < 3; ++s) {
     const void *Uin = s == 0 ? h->U0 : h->U1;
     void *Uout = s == 2 ? h->U0 : h->U1;
-    if (h->nv == 4) {
-      e = launch(h, MODE_XSWEEP, true, Uin, h->U0, nullptr, h->D, nullptr, s, 0.0, h->ctl);
+    if (!h->batch) {
+      if (h->nv == 4) {
+        e = launch(h, MODE_XSWEEP, true, Uin, h->U0, nullptr, h->D, nullptr, s, 0.0, h->ctl);
+        if (e != cudaSuccess) return e;
+        e = launch(h, MODE_FINAL, false, Uin, h->U0, h->D, nullptr, Uout, s, 0.0, h->ctl);
+      } else {
+        e = launch(h, MODE_FINAL, true, Uin, h->U0, nullptr, nullptr, Uout, s, 0.0, h->ctl);
+      }
       if (e != cudaSuccess) return e;
-      e = launch(h, MODE_FINAL, false, Uin, h->U0, h->D, nullptr, Uout, s, 0.0, h->ctl);
-    } else {
-      e = launch(h, MODE_FINAL, true, Uin, h->U0, nullptr, nullptr, Uout, s, 0.0, h->ctl);
+      continue;
     }
-    if (e != cudaSuccess) return e;
+    for (const LineGroup &g : h->groups) {   // x groups come first
+      if (!g.xdir) continue;
+      if (h->nv == 4) e = launch_group(h, g, MODE_XSWEEP, Uin, h->U0, nullptr, h->D, nullptr, s);
+      else e = launch_group(h, g, MODE_FINAL, Uin, h->U0, nullptr, nullptr, Uout, s);
+      if (e != cudaSuccess) return e;
+    }
+    for (const LineGroup &g : h->groups) {
+      if (g.xdir) continue;
+      e = launch_group(h, g, MODE_FINAL, Uin, h->U0, h->D, nullptr, Uout, s);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
 
 int build_graph(pp_cweno_s *h) {
   if (h->graph) return PP_OK;
-  // make sure every kernel attribute is set outside the capture
   cudaGraph_t g;
   cudaStream_t cap;
   if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return PP_ERR_CUDA;
@@ -308,38 +424,100 @@ int build_graph(pp_cweno_s *h) {
   return cuerr(e);
 }
 
+// reductions (min rho, max rate, violations) of a state into ctl[0..nprob)
 int reduce_state(pp_cweno_s *h, const void *U, Ctl *ctl, bool split_planes) {
-  Ctl z;
-  memset(&z, 0, sizeof(z));
-  z.minrho[2] = 0x7ff0000000000000ull;  // +inf
-  z.first_bad = ~0ull;
-  cudaError_t e = cudaMemcpyAsync(ctl, &z, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream);
+  std::vector<Ctl> z((size_t)h->nprob);
+  for (auto &c : z) {
+    memset(&c, 0, sizeof(c));
+    c.minrho[2] = 0x7ff0000000000000ull;  // +inf
+    c.first_bad = ~0ull;
+  }
+  cudaError_t e = cudaMemcpyAsync(ctl, z.data(), sizeof(Ctl) * z.size(), cudaMemcpyHostToDevice,
+                                  h->stream);
   if (e != cudaSuccess) return PP_ERR_CUDA;
-  int blocks = (int)fmin(1184.0, (double)((h->ncell + 255) / 256));
-  if (blocks < 1) blocks = 1;
   const float *lo = split_planes ? lo_of(h, const_cast<void *>(U)) : nullptr;
-  if (h->nv == 4)
-    state_reduce_kernel<4><<<blocks, 256, 0, h->stream>>>(U, lo, h->ncell, h->nx, h->dx, h->dy,
-                                                          h->cfg.gamma, ctl);
-  else
-    state_reduce_kernel<3><<<blocks, 256, 0, h->stream>>>(U, lo, h->ncell, h->nx, h->dx, h->dy,
-                                                          h->cfg.gamma, ctl);
-  return cuerr(cudaGetLastError());
+  if (h->batch) {
+    if (h->nv == 4)
+      batch_reduce_kernel<4><<<h->nprob, 256, 0, h->stream>>>(U, lo, h->probs, h->cfg.gamma, ctl);
+    else
+      batch_reduce_kernel<3><<<h->nprob, 256, 0, h->stream>>>(U, lo, h->probs, h->cfg.gamma, ctl);
+  } else {
+    int blocks = (int)fmin(1184.0, (double)((h->ncell + 255) / 256));
+    if (blocks < 1) blocks = 1;
+    if (h->nv == 4)
+      state_reduce_kernel<4><<<blocks, 256, 0, h->stream>>>(U, lo, h->ncell, h->nx, h->dx, h->dy,
+                                                            h->cfg.gamma, ctl);
+    else
+      state_reduce_kernel<3><<<blocks, 256, 0, h->stream>>>(U, lo, h->ncell, h->nx, h->dx, h->dy,
+                                                            h->cfg.gamma, ctl);
+  }
+  e = cudaStreamSynchronize(h->stream);   // z must outlive the copy
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return cuerr(e);
 }
 
 int pull_ctl(pp_cweno_s *h) {
-  if (cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+  if (cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl) * h->nprob, cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess)
     return PP_ERR_CUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
   return PP_OK;
 }
 
 int push_ctl(pp_cweno_s *h) {
-  return cuerr(cudaMemcpyAsync(h->ctl, h->hctl, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+  return cuerr(cudaMemcpyAsync(h->ctl, h->hctl, sizeof(Ctl) * h->nprob, cudaMemcpyHostToDevice,
+                               h->stream));
 }
 
-double effective_cfl(const pp_cweno_config &c) {
-  return c.cfl_positivity_cap ? fmin(c.cfl, c.gl_weight) : c.cfl;
+int status_after(pp_cweno_s *h) {
+  int rc = PP_OK;
+  for (int p = 0; p < h->nprob; ++p) {
+    const Ctl *c = h->hctl + p;
+    if (c->nviol || c->err_rate) return PP_ERR_NONPHYSICAL;
+    if (c->err_steps) rc = PP_ERR_STEPS;
+  }
+  return rc;
+}
+
+bool any_violation(const pp_cweno_s *h) {
+  for (int p = 0; p < h->nprob; ++p)
+    if (h->hctl[p].nviol) return true;
+  return false;
+}
+
+// common creation: allocations, kernel attributes, launch count
+int finish_create(pp_cweno_s *h) {
+  size_t bytes = sizeof(double) * (size_t)nvals(h);
+  size_t dbytes = (h->cfg.precision == PP_PREC_FP64 ? sizeof(double) : sizeof(float)) *
+                  (size_t)nvals(h);
+  cudaError_t e = cudaMalloc(&h->U0, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->U1, bytes);
+  if (e == cudaSuccess && h->nv == 4) e = cudaMalloc(&h->D, dbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->ctl, sizeof(Ctl) * h->nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&h->ctl_scratch, sizeof(Ctl) * h->nprob);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->hctl, sizeof(Ctl) * h->nprob);
+  if (e != cudaSuccess) return PP_ERR_CUDA;
+  memset(h->hctl, 0, sizeof(Ctl) * h->nprob);
+  // kernel attributes (dynamic shared memory, cluster size) are set here,
+  // never inside a stream capture
+  const int modes[3] = {MODE_XSWEEP, MODE_FINAL, MODE_OPERATOR};
+  for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
+    if (h->nv == 3 && modes[m] == MODE_XSWEEP) continue;
+    for (int per = 0; per < 2 && e == cudaSuccess; ++per) {
+      SweepArgs a;
+      memset(&a, 0, sizeof(a));
+      a.R = 1;
+      e = dispatch(h, modes[m], per != 0, a, 0, true);
+    }
+  }
+  if (e != cudaSuccess) return PP_ERR_CUDA;
+  if (h->batch) {
+    h->launches_per_step = 1;
+    for (int s = 0; s < 3; ++s) h->launches_per_step += (long long)h->groups.size();
+  } else {
+    h->launches_per_step = 1 + 3 * (h->nv == 4 ? 2 : 1);
+  }
+  return PP_OK;
 }
 
 }  // namespace
@@ -376,6 +554,7 @@ int pp_cweno_create(const pp_cweno_config *cfg, void *cuda_stream, pp_cweno_t *o
   pp_cweno_s *h = new (std::nothrow) pp_cweno_s();
   if (!h) return PP_ERR_CUDA;
   h->cfg = *cfg;
+  h->cfgs.push_back(*cfg);
   h->stream = (cudaStream_t)cuda_stream;
   h->nv = cfg->ndim == 2 ? 4 : 3;
   h->nx = cfg->nx;
@@ -383,54 +562,111 @@ int pp_cweno_create(const pp_cweno_config *cfg, void *cuda_stream, pp_cweno_t *o
   h->ncell = h->nx * h->ny;
   h->dx = (cfg->x1 - cfg->x0) / (double)h->nx;
   h->dy = cfg->ndim == 2 ? (cfg->y1 - cfg->y0) / (double)h->ny : 1.0;
-  size_t bytes = sizeof(double) * (size_t)h->nv * (size_t)h->ncell;
-  size_t dbytes = (cfg->precision == PP_PREC_FP64 ? sizeof(double) : sizeof(float)) *
-                  (size_t)h->nv * (size_t)h->ncell;
-  cudaError_t e = cudaMalloc(&h->U0, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&h->U1, bytes);
-  if (e == cudaSuccess && h->nv == 4) e = cudaMalloc(&h->D, dbytes);
-  if (e == cudaSuccess) e = cudaMalloc(&h->ctl, sizeof(Ctl));
-  if (e == cudaSuccess) e = cudaMalloc(&h->ctl_scratch, sizeof(Ctl));
-  if (e == cudaSuccess) e = cudaMallocHost(&h->hctl, sizeof(Ctl));
-  if (e != cudaSuccess) {
+  if ((rc = finish_create(h))) {
     pp_cweno_destroy(h);
-    return PP_ERR_CUDA;
+    return rc;
   }
-  memset(h->hctl, 0, sizeof(Ctl));
-  // kernel attributes (dynamic shared memory, cluster size) are set here,
-  // never inside a stream capture
-  {
-    const int modes_2d[3] = {MODE_XSWEEP, MODE_FINAL, MODE_OPERATOR};
-    for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
-      if (h->nv == 3 && modes_2d[m] == MODE_XSWEEP) continue;
-      e = launch(h, modes_2d[m], true, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0.0,
-                 nullptr, true);
-      if (e == cudaSuccess && h->nv == 4)
-        e = launch(h, modes_2d[m], false, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0.0,
-                   nullptr, true);
-    }
-    if (e != cudaSuccess) {
-      pp_cweno_destroy(h);
-      return PP_ERR_CUDA;
-    }
-  }
-  h->launches_per_step = 1 + 3 * (h->nv == 4 ? 2 : 1);
   *out = h;
   return PP_OK;
 }
 
 int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda_stream,
                           pp_cweno_t *out) {
-  if (!out || !cfgs || nprob < 1) return PP_ERR_ARG;
+  if (!out || !cfgs || nprob < 1 || nprob > (1 << 24)) return PP_ERR_ARG;
   *out = nullptr;
-  if (nprob == 1) return pp_cweno_create(cfgs, cuda_stream, out);
-  return PP_ERR_UNSUPPORTED;
+  const pp_cweno_config &c0 = cfgs[0];
+  for (int64_t p = 0; p < nprob; ++p) {
+    int rc = check_config(cfgs + p);
+    if (rc) return rc;
+    const pp_cweno_config &c = cfgs[p];
+    if (c.ndim != c0.ndim || c.gamma != c0.gamma || c.precision != c0.precision ||
+        c.gl_weight != c0.gl_weight || c.eps_weno != c0.eps_weno || c.eps_pos != c0.eps_pos ||
+        c.limiter != c0.limiter)
+      return PP_ERR_ARG;
+  }
+  pp_cweno_s *h = new (std::nothrow) pp_cweno_s();
+  if (!h) return PP_ERR_CUDA;
+  h->batch = true;
+  h->cfg = c0;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->nv = c0.ndim == 2 ? 4 : 3;
+  h->nprob = (int)nprob;
+  long long off = 0, cells = 0;
+  // line groups keyed by (direction, cluster size, periodic)
+  std::vector<std::vector<LineRef>> glines;
+  auto group_of = [&](bool xdir, int R, bool per) -> size_t {
+    for (size_t g = 0; g < h->groups.size(); ++g)
+      if (h->groups[g].xdir == xdir && h->groups[g].R == R && h->groups[g].periodic == per) return g;
+    LineGroup lg;
+    lg.R = R;
+    lg.periodic = per;
+    lg.xdir = xdir;
+    h->groups.push_back(lg);
+    glines.emplace_back();
+    return h->groups.size() - 1;
+  };
+  for (int p = 0; p < h->nprob; ++p) {
+    const pp_cweno_config &c = cfgs[p];
+    h->cfgs.push_back(c);
+    ProbDesc d;
+    memset(&d, 0, sizeof(d));
+    d.nx = (int)c.nx;
+    d.ny = c.ndim == 2 ? (int)c.ny : 1;
+    d.ncell = (long long)d.nx * d.ny;
+    d.off = off;
+    d.dx = (c.x1 - c.x0) / (double)d.nx;
+    d.dy = c.ndim == 2 ? (c.y1 - c.y0) / (double)d.ny : 1.0;
+    for (int k = 0; k < 4; ++k) d.bc[k] = c.bc[k];
+    h->probs_h.push_back(d);
+    off += (long long)h->nv * d.ncell;
+    cells += d.ncell;
+    size_t gx = group_of(true, seg_count(d.nx), c.bc[0] == PP_BC_PERIODIC);
+    for (int j = 0; j < d.ny; ++j) glines[gx].push_back({p, j});
+    if (c.ndim == 2) {
+      size_t gy = group_of(false, seg_count(d.ny), c.bc[2] == PP_BC_PERIODIC);
+      for (int i = 0; i < d.nx; ++i) glines[gy].push_back({p, i});
+    }
+  }
+  h->ncell = cells;
+  h->nx = cells;
+  h->ny = 1;
+  // x groups before y groups, larger clusters first
+  std::vector<size_t> order(h->groups.size());
+  for (size_t g = 0; g < order.size(); ++g) order[g] = g;
+  std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    if (h->groups[a].xdir != h->groups[b].xdir) return h->groups[a].xdir;
+    return h->groups[a].R > h->groups[b].R;
+  });
+  std::vector<LineGroup> sorted;
+  std::vector<std::vector<LineRef>> slines;
+  for (size_t g : order) {
+    sorted.push_back(h->groups[g]);
+    slines.push_back(glines[g]);
+  }
+  h->groups = sorted;
+  cudaError_t e = cudaMalloc(&h->probs, sizeof(ProbDesc) * h->nprob);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->probs, h->probs_h.data(), sizeof(ProbDesc) * h->nprob, cudaMemcpyHostToDevice);
+  for (size_t g = 0; g < h->groups.size() && e == cudaSuccess; ++g) {
+    h->groups[g].nlines = (long long)slines[g].size();
+    e = cudaMalloc(&h->groups[g].lines, sizeof(LineRef) * slines[g].size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->groups[g].lines, slines[g].data(), sizeof(LineRef) * slines[g].size(),
+                     cudaMemcpyHostToDevice);
+  }
+  int rc = e == cudaSuccess ? finish_create(h) : PP_ERR_CUDA;
+  if (rc) {
+    pp_cweno_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return PP_OK;
 }
 
 int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) {
   if (!h || !U || !isfinite(t0)) return PP_ERR_ARG;
-  size_t bytes = sizeof(double) * (size_t)h->nv * (size_t)h->ncell;
-  long long nval = (long long)h->nv * h->ncell;
+  size_t bytes = sizeof(double) * (size_t)nvals(h);
+  long long nval = nvals(h);
   cudaError_t e;
   if (is_mixed(h)) {
     const double *src = U;
@@ -449,22 +685,25 @@ int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) 
   int rc = reduce_state(h, h->U0, h->ctl, is_mixed(h));
   if (rc) return rc;
   if ((rc = pull_ctl(h))) return rc;
-  Ctl *c = h->hctl;
-  int bad = c->nviol != 0;
-  c->t = t0;
-  c->t_final = t0;
-  c->dt = 0.0;
-  c->last_dt = 0.0;
-  c->cfl = effective_cfl(h->cfg);
-  c->dt_cap = INFINITY;
-  c->step = 0;
-  c->step_limit = 0;
-  c->active = 0;
-  c->done = 1;
-  c->err_steps = 0;
-  c->err_rate = 0;
-  c->eps_pos = h->cfg.eps_pos;
-  c->theta1 = c->theta2 = 0;
+  bool bad = false;
+  for (int p = 0; p < h->nprob; ++p) {
+    Ctl *c = h->hctl + p;
+    bad = bad || c->nviol != 0;
+    c->t = t0;
+    c->t_final = t0;
+    c->dt = 0.0;
+    c->last_dt = 0.0;
+    c->cfl = effective_cfl(h->cfgs[p]);
+    c->dt_cap = INFINITY;
+    c->step = 0;
+    c->step_limit = 0;
+    c->active = 0;
+    c->done = 1;
+    c->err_steps = 0;
+    c->err_rate = 0;
+    c->eps_pos = h->cfg.eps_pos;
+    c->theta1 = c->theta2 = 0;
+  }
   if ((rc = push_ctl(h))) return rc;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
   return bad ? PP_ERR_STATE : PP_OK;
@@ -472,8 +711,8 @@ int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) 
 
 int pp_cweno_get_state(pp_cweno_t h, double *U, int on_device, double *t, int64_t *steps) {
   if (!h || !U) return PP_ERR_ARG;
-  size_t bytes = sizeof(double) * (size_t)h->nv * (size_t)h->ncell;
-  long long nval = (long long)h->nv * h->ncell;
+  size_t bytes = sizeof(double) * (size_t)nvals(h);
+  long long nval = nvals(h);
   cudaError_t e;
   if (is_mixed(h)) {
     double *dst = on_device ? U : reinterpret_cast<double *>(h->U1);
@@ -488,16 +727,14 @@ int pp_cweno_get_state(pp_cweno_t h, double *U, int on_device, double *t, int64_
   if (e != cudaSuccess) return PP_ERR_CUDA;
   int rc = pull_ctl(h);
   if (rc) return rc;
-  if (t) *t = h->hctl->t;
-  if (steps) *steps = h->hctl->step;
-  return PP_OK;
-}
-
-static int status_after(pp_cweno_s *h) {
-  Ctl *c = h->hctl;
-  if (c->nviol) return PP_ERR_NONPHYSICAL;
-  if (c->err_rate) return PP_ERR_NONPHYSICAL;
-  if (c->err_steps) return PP_ERR_STEPS;
+  double tmax = h->hctl[0].t;
+  long long smax = h->hctl[0].step;
+  for (int p = 1; p < h->nprob; ++p) {
+    tmax = fmax(tmax, h->hctl[p].t);
+    smax = smax > h->hctl[p].step ? smax : h->hctl[p].step;
+  }
+  if (t) *t = tmax;
+  if (steps) *steps = smax;
   return PP_OK;
 }
 
@@ -505,22 +742,26 @@ int pp_cweno_step(pp_cweno_t h, double dt_max, double *dt_taken) {
   if (!h || !(dt_max > 0.0)) return PP_ERR_ARG;
   int rc = pull_ctl(h);
   if (rc) return rc;
-  Ctl *c = h->hctl;
-  if (c->nviol) return PP_ERR_NONPHYSICAL;
-  c->t_final = INFINITY;
-  c->dt_cap = dt_max;
-  c->done = 0;
-  c->step_limit = c->step + 1;
-  c->err_steps = 0;
+  if (any_violation(h)) return PP_ERR_NONPHYSICAL;
+  for (int p = 0; p < h->nprob; ++p) {
+    Ctl *c = h->hctl + p;
+    c->t_final = INFINITY;
+    c->dt_cap = dt_max;
+    c->done = 0;
+    c->step_limit = c->step + 1;
+    c->err_steps = 0;
+  }
   if ((rc = push_ctl(h))) return rc;
-  cudaError_t e = enqueue_step(h);
-  if (e != cudaSuccess) return PP_ERR_CUDA;
+  if (enqueue_step(h) != cudaSuccess) return PP_ERR_CUDA;
   if ((rc = pull_ctl(h))) return rc;
-  c->t_final = c->t;
-  c->dt_cap = INFINITY;
-  c->done = 1;
+  for (int p = 0; p < h->nprob; ++p) {
+    Ctl *c = h->hctl + p;
+    c->t_final = c->t;
+    c->dt_cap = INFINITY;
+    c->done = 1;
+  }
+  if (dt_taken) *dt_taken = h->hctl[0].last_dt;
   if ((rc = push_ctl(h))) return rc;
-  if (dt_taken) *dt_taken = c->last_dt;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
   return status_after(h);
 }
@@ -529,23 +770,37 @@ int pp_cweno_advance(pp_cweno_t h, double t_final, int64_t max_steps, int64_t *s
   if (!h || !isfinite(t_final) || max_steps < 0) return PP_ERR_ARG;
   int rc = pull_ctl(h);
   if (rc) return rc;
-  Ctl *c = h->hctl;
-  if (c->nviol) return PP_ERR_NONPHYSICAL;
-  long long start = c->step;
-  c->t_final = t_final;
-  c->dt_cap = INFINITY;
-  c->done = c->t >= t_final;
-  c->step_limit = c->step + max_steps;
-  c->err_steps = 0;
-  c->err_rate = 0;
+  if (any_violation(h)) return PP_ERR_NONPHYSICAL;
+  std::vector<long long> start((size_t)h->nprob);
+  for (int p = 0; p < h->nprob; ++p) {
+    Ctl *c = h->hctl + p;
+    start[p] = c->step;
+    c->t_final = t_final;
+    c->dt_cap = INFINITY;
+    c->done = c->t >= t_final;
+    c->step_limit = c->step + max_steps;
+    c->err_steps = 0;
+    c->err_rate = 0;
+  }
   if ((rc = push_ctl(h))) return rc;
   if ((rc = build_graph(h))) return rc;
   for (;;) {
     if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return PP_ERR_CUDA;
     if ((rc = pull_ctl(h))) return rc;
-    if (c->done || c->nviol || c->err_steps || c->err_rate) break;
+    bool finished = true;
+    for (int p = 0; p < h->nprob; ++p) {
+      const Ctl *c = h->hctl + p;
+      if (c->nviol || c->err_rate) { finished = true; break; }
+      if (!(c->done || c->err_steps)) finished = false;
+    }
+    if (finished) break;
   }
-  if (steps_taken) *steps_taken = c->step - start;
+  long long taken = 0;
+  for (int p = 0; p < h->nprob; ++p) {
+    long long d = h->hctl[p].step - start[p];
+    taken = d > taken ? d : taken;
+  }
+  if (steps_taken) *steps_taken = taken;
   return status_after(h);
 }
 
@@ -553,12 +808,14 @@ int pp_cweno_enqueue_steps(pp_cweno_t h, int64_t nsteps) {
   if (!h || nsteps < 0) return PP_ERR_ARG;
   int rc = pull_ctl(h);
   if (rc) return rc;
-  Ctl *c = h->hctl;
-  c->t_final = INFINITY;
-  c->dt_cap = INFINITY;
-  c->done = 0;
-  c->step_limit = c->step + nsteps;
-  c->err_steps = 0;
+  for (int p = 0; p < h->nprob; ++p) {
+    Ctl *c = h->hctl + p;
+    c->t_final = INFINITY;
+    c->dt_cap = INFINITY;
+    c->done = 0;
+    c->step_limit = c->step + nsteps;
+    c->err_steps = 0;
+  }
   if ((rc = push_ctl(h))) return rc;
   if ((rc = build_graph(h))) return rc;
   int64_t left = nsteps;
@@ -575,10 +832,11 @@ int pp_cweno_enqueue_steps(pp_cweno_t h, int64_t nsteps) {
 
 int pp_cweno_operator(pp_cweno_t h, const double *U_dev, double *L_dev, double eps) {
   if (!h || !U_dev || !L_dev) return PP_ERR_ARG;
+  if (h->batch) return PP_ERR_UNSUPPORTED;
   int rc;
   const void *Uin = U_dev;
   if (is_mixed(h)) {   // the line kernels read FP32 hi / lo planes
-    long long nval = (long long)h->nv * h->ncell;
+    long long nval = nvals(h);
     split_kernel<<<grid_for(nval), 256, 0, h->stream>>>(U_dev, hi_of(h->U1), lo_of(h, h->U1), nval);
     if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
     Uin = h->U1;
@@ -586,11 +844,9 @@ int pp_cweno_operator(pp_cweno_t h, const double *U_dev, double *L_dev, double e
   if (!(eps > 0.0)) {
     if ((rc = reduce_state(h, U_dev, h->ctl_scratch, false))) return rc;
     Ctl tmp;
-    if (cudaMemcpyAsync(&tmp, h->ctl_scratch, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    if (cudaMemcpy(&tmp, h->ctl_scratch, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess)
       return PP_ERR_CUDA;
-    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
-    double mr = bits_to_double(tmp.minrho[2]);
-    eps = fmin(h->cfg.eps_pos, mr);
+    eps = fmin(h->cfg.eps_pos, bits_to_double(tmp.minrho[2]));
     if (!(eps > 0.0)) return PP_ERR_STATE;
   }
   Ctl z;
@@ -616,36 +872,45 @@ int pp_cweno_stats(pp_cweno_t h, pp_cweno_stats_t *out) {
   if (!h || !out) return PP_ERR_ARG;
   int rc = pull_ctl(h);
   if (rc) return rc;
-  // current-state reductions come from a fresh pass over U^n
-  Ctl *c = h->hctl;
   memset(out, 0, sizeof(*out));
-  out->steps = c->step;
-  out->stages = 3 * c->step;
-  out->theta1_active = (int64_t)c->theta1;
-  out->theta2_active = (int64_t)c->theta2;
-  out->violations = (int64_t)c->nviol;
-  out->first_bad_cell = c->nviol ? (int64_t)c->first_bad : -1;
-  out->t = c->t;
-  out->last_dt = c->last_dt;
+  out->first_bad_cell = -1;
+  out->t = h->hctl[0].t;
+  for (int p = 0; p < h->nprob; ++p) {
+    const Ctl *c = h->hctl + p;
+    out->steps = out->steps > c->step ? out->steps : c->step;
+    out->theta1_active += (int64_t)c->theta1;
+    out->theta2_active += (int64_t)c->theta2;
+    out->violations += (int64_t)c->nviol;
+    if (c->nviol && out->first_bad_cell < 0)
+      out->first_bad_cell = (int64_t)c->first_bad + (h->batch ? h->probs_h[p].off / h->nv : 0);
+    out->t = fmax(out->t, c->t);
+    out->last_dt = c->last_dt;
+  }
+  out->stages = 3 * out->steps;
+  // reductions of the current state from a fresh pass over U^n
   if ((rc = reduce_state(h, h->U0, h->ctl_scratch, is_mixed(h)))) return rc;
-  Ctl tmp;
-  if (cudaMemcpyAsync(&tmp, h->ctl_scratch, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+  std::vector<Ctl> tmp((size_t)h->nprob);
+  if (cudaMemcpy(tmp.data(), h->ctl_scratch, sizeof(Ctl) * h->nprob, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
     return PP_ERR_CUDA;
-  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
-  out->max_rate = bits_to_double(tmp.rate);
-  out->min_rho = bits_to_double(tmp.minrho[2]);
+  out->max_rate = 0.0;
+  out->min_rho = INFINITY;
+  for (const Ctl &c : tmp) {
+    out->max_rate = fmax(out->max_rate, bits_to_double(c.rate));
+    out->min_rho = fmin(out->min_rho, bits_to_double(c.minrho[2]));
+  }
   return PP_OK;
 }
 
 int pp_cweno_num_problems(pp_cweno_t h, int64_t *nprob) {
   if (!h || !nprob) return PP_ERR_ARG;
-  *nprob = 1;
+  *nprob = h->nprob;
   return PP_OK;
 }
 
 int pp_cweno_problem_cells(pp_cweno_t h, int64_t k, int64_t *ncell) {
-  if (!h || !ncell || k != 0) return PP_ERR_ARG;
-  *ncell = h->ncell;
+  if (!h || !ncell || k < 0 || k >= h->nprob) return PP_ERR_ARG;
+  *ncell = h->batch ? h->probs_h[k].ncell : h->ncell;
   return PP_OK;
 }
 
@@ -657,6 +922,7 @@ int pp_cweno_launches_per_step(pp_cweno_t h, int64_t *n) {
 
 int pp_cweno_profile_step(pp_cweno_t h, float *ms, int nmax, int *nk) {
   if (!h || !ms || !nk || nmax < 1) return PP_ERR_ARG;
+  if (h->batch) return PP_ERR_UNSUPPORTED;
   int rc = pull_ctl(h);
   if (rc) return rc;
   Ctl *c = h->hctl;
@@ -672,7 +938,7 @@ int pp_cweno_profile_step(pp_cweno_t h, float *ms, int nmax, int *nk) {
     if (cudaEventCreate(&ev[k]) != cudaSuccess) return PP_ERR_CUDA;
   cudaError_t e = cudaEventRecord(ev[0], h->stream);
   int idx = 0;
-  step_begin_kernel<<<1, 32, 0, h->stream>>>(h->ctl);
+  step_begin_kernel<<<1, 128, 0, h->stream>>>(h->ctl, 1);
   cudaEventRecord(ev[++idx], h->stream);
   for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
     const void *Uin = s == 0 ? h->U0 : h->U1;
@@ -746,6 +1012,8 @@ int pp_cweno_destroy(pp_cweno_t h) {
   cudaFree(h->D);
   cudaFree(h->ctl);
   cudaFree(h->ctl_scratch);
+  cudaFree(h->probs);
+  for (auto &g : h->groups) cudaFree(g.lines);
   if (h->hctl) cudaFreeHost(h->hctl);
   delete h;
   return PP_OK;
