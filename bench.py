@@ -113,16 +113,22 @@ def _barrier(ws: int):
         dist.barrier()
 
 
-# per-kernel algorithmic bytes per cell of the two-pass 2-D stage (4
-# conserved variables; a state value is 8 B: FP64, or an FP32 hi + lo pair):
-#   x sweep: reads U_k (the mixed form reads only the 4 B hi parts) and
-#            writes D (8 B FP64 / 4 B FP32 per variable);
-#   y sweep: reads U_k and D, reads U^n in stages 2 and 3 (2/3 on average)
-#            and writes U_{k+1}.
-def _kernel_bytes(prec: int) -> dict:
-    if prec == 0:
-        return {"x": 32 + 32, "y": 32 + 32 + 32 * 2.0 / 3.0 + 32}
-    return {"x": 16 + 16, "y": 32 + 16 + 32 * 2.0 / 3.0 + 32}
+# Per-kernel algorithmic bytes per cell of a 2-D stage (4 conserved
+# variables; a state value is 8 B: FP64, or an FP32 hi + lo pair).
+# Plain form (2 sweeps per stage):
+#   x sweep  reads U_k, writes D_x (8 B / variable)                   64 B
+#   y sweep  reads U_k and D_x, U^n in stages 2-3 (2/3 on average),
+#            writes U_{k+1}                                          117.3 B
+# Mixed form (3 kernels per stage):
+#   x sweep  reads the FP32 hi parts of U_k, writes D_x (FP32)        32 B
+#   y sweep  reads the transposed hi parts, writes D_y transposed     32 B
+#   combine  reads U_k, U^n (2/3), D_x, D_y; writes U_{k+1} and its
+#            transposed hi parts                                     133.3 B
+KERNEL_BYTES = {
+    0: [("x_sweep", 64.0), ("y_sweep", 32 + 32 + 32 * 2.0 / 3.0 + 32)],
+    1: [("x_sweep", 32.0), ("y_sweep_transposed", 32.0),
+        ("stage_combine", 32 + 32 * 2.0 / 3.0 + 16 + 16 + 32 + 16)],
+}
 
 
 def run_native(args, ws, rank, local):
@@ -148,6 +154,7 @@ def run_native(args, ws, rank, local):
         prof = [s.profile_step() for _ in range(args.profile_steps)]
         torch.cuda.synchronize()
         launches = s.launches_per_step()
+        m_rows = s.rows_per_chunk()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         _barrier(ws)
         torch.cuda.synchronize()
@@ -160,6 +167,7 @@ def run_native(args, ws, rank, local):
         ms = ev0.elapsed_time(ev1)
         st = s.stats()
         results[prec] = dict(ms=ms, steps=steps, prof=prof, launches=launches, clk=clk.summary(),
+                             rows_per_chunk=m_rows,
                              violations=st.violations, t=st.t, theta2=st.theta2_active)
         s.close()
 
@@ -196,19 +204,23 @@ def run_native(args, ws, rank, local):
 
 
 def _roofline(r, prec, ncell, hbm_peak, peak_kind):
+    """HBM roofline of the kernel with the largest share of the step time:
+    its algorithmic bytes per launch over its mean CUDA-event duration."""
     import numpy as np
-    prof = np.array(r["prof"])           # [steps, kernels]: dt kernel, then x, y per stage
-    kb = _kernel_bytes(prec)
-    xs = prof[:, 1::2].ravel()
-    ys = prof[:, 2::2].ravel()
-    dom, t_ms, per_cell = ("y_sweep", ys.mean(), kb["y"]) if ys.sum() >= xs.sum() else \
-        ("x_sweep", xs.mean(), kb["x"])
+    prof = np.array(r["prof"])          # [steps, launches]: dt kernel, then per stage
+    kinds = KERNEL_BYTES[prec]
+    per = prof[:, 1:].reshape(prof.shape[0], 3, len(kinds))
+    tot = per.sum(axis=(0, 1))
+    k = int(np.argmax(tot))
+    name, per_cell = kinds[k]
+    t_ms = float(per[:, :, k].mean())
     achieved = per_cell * ncell / (t_ms * 1e-3) / 1e9
-    return {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
             "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
             "peak_source": peak_kind, "alg_bytes_per_cell": round(per_cell, 1),
-            "avg_launch_ms": round(float(t_ms), 4),
-            "share_x_y": [round(float(xs.sum() / prof.sum()), 3), round(float(ys.sum() / prof.sum()), 3)]}
+            "avg_launch_ms": round(t_ms, 4),
+            "kernel_ms": {kinds[i][0]: round(float(per[:, :, i].mean()), 4) for i in range(len(kinds))},
+            "shares": {kinds[i][0]: round(float(tot[i] / prof.sum()), 3) for i in range(len(kinds))}}
 
 
 def _cpu_baseline(seconds_target: float = 20.0):
@@ -281,8 +293,9 @@ def main():
                        "cfl": "min(0.5, 1/12): the stated CFL 0.5 exceeds the positivity bound "
                               "of eq. (CFL-CD) and breaks positivity on this workload; "
                               "throughput per cell-stage does not depend on the CFL number",
-                       "precision": "mixed: FP32 line arithmetic, FP64 state and stage combination",
+                       "precision": "mixed: FP32 line arithmetic, FP32 hi+lo compensated state, FP64 limiter factors",
                        "grid": [N_GRID, N_GRID], "cells": ncell,
+                       "rows_per_chunk": rm["rows_per_chunk"],
                        "l2": "no flush: the state (537 MB FP64) and stage buffers exceed L2",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": _roofline(rm, 1, ncell, hbm, kind),
@@ -293,6 +306,7 @@ def main():
                     "note": "set_state from host, K steps, get_state to host, wall clock"},
             "gpu_launches": int(rm["launches"] * rm["steps"]),
             "fp64_plain": {"value": value_fp64, "unit": UNIT, "steps": rd["steps"],
+                           "rows_per_chunk": rd["rows_per_chunk"],
                            "ms_per_step": ms_d / rd["steps"], "dtype": "f64",
                            "roofline": _roofline(rd, 0, ncell, hbm, kind), "clocks": rd["clk"]},
             "accuracy": {"case": "isentropic vortex 128^2, t = 1, L1 of density vs closed form",

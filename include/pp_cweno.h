@@ -145,6 +145,12 @@ int pp_cweno_stats(pp_cweno_t h, pp_cweno_stats_t *out);
 int pp_cweno_num_problems(pp_cweno_t h, int64_t *nprob);
 int pp_cweno_problem_cells(pp_cweno_t h, int64_t k, int64_t *ncell);
 
+/* Rows per thread chunk of the line kernels chosen for this handle (8 or
+ * 16).  The first set_state of a single-problem handle times one sweep with
+ * each choice on the handle's own data and keeps the faster (cached per
+ * precision, dimension and grid size); batches use 8. */
+int pp_cweno_rows_per_chunk(pp_cweno_t h, int *m);
+
 /* Kernel launches enqueued per step (for launch accounting). */
 int pp_cweno_launches_per_step(pp_cweno_t h, int64_t *n);
 

@@ -44,6 +44,7 @@ EXPORTS = [
     "pp_cweno_config_default", "pp_cweno_create", "pp_cweno_create_batch", "pp_cweno_set_state",
     "pp_cweno_get_state", "pp_cweno_step", "pp_cweno_advance", "pp_cweno_enqueue_steps",
     "pp_cweno_operator", "pp_cweno_stats", "pp_cweno_num_problems", "pp_cweno_problem_cells",
+    "pp_cweno_rows_per_chunk",
     "pp_cweno_launches_per_step", "pp_cweno_profile_step", "pp_cweno_fma_peak",
     "pp_cweno_destroy", "pp_cweno_strerror",
 ]
@@ -84,6 +85,7 @@ def lib(build_if_missing: bool = False):
     L.pp_cweno_num_problems.argtypes = [vp, i64p]
     L.pp_cweno_problem_cells.argtypes = [vp, C.c_int64, i64p]
     L.pp_cweno_launches_per_step.argtypes = [vp, i64p]
+    L.pp_cweno_rows_per_chunk.argtypes = [vp, C.POINTER(C.c_int)]
     L.pp_cweno_profile_step.argtypes = [vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
     L.pp_cweno_fma_peak.argtypes = [C.c_int, dp]
     L.pp_cweno_destroy.argtypes = [vp]
@@ -228,6 +230,11 @@ class Solver:
         nk = C.c_int()
         _check(lib().pp_cweno_profile_step(self.h, ms, 16, C.byref(nk)), "profile_step")
         return [ms[i] for i in range(nk.value)]
+
+    def rows_per_chunk(self) -> int:
+        m = C.c_int()
+        _check(lib().pp_cweno_rows_per_chunk(self.h, C.byref(m)), "rows_per_chunk")
+        return m.value
 
     def launches_per_step(self) -> int:
         n = C.c_int64()

@@ -45,8 +45,7 @@ namespace cg = cooperative_groups;
 
 namespace ppk {
 
-constexpr int KC = 64;          // chunks per conserved variable per CTA
-constexpr int WPV = KC / 32;    // warps per conserved variable
+constexpr int SEGC = 512;       // cells per CTA segment (all chunk lengths)
 
 // device-side control block of one problem (time, dt, reductions, flags)
 struct Ctl {
@@ -266,7 +265,7 @@ __device__ __forceinline__ Bwd<real> bwd_compose(const Bwd<real> &X, const Bwd<r
 }
 
 // ---------------------------------------------------------------- smem
-template <typename real, int NV>
+template <typename real, int NV, int WPV>
 struct Exch {
   Fwd<real> warp_fwd[NV][2][WPV];
   real warp_in[NV][2][WPV][3];   // incoming (c', d', z') of each warp
@@ -279,7 +278,9 @@ struct Exch {
 
 template <typename real, int NV, int M>
 struct Smem {
-  static constexpr int SEG = KC * M;
+  static constexpr int KC = SEGC / M;     // chunks per conserved variable
+  static constexpr int WPV = KC / 32;     // warps per conserved variable
+  static constexpr int SEG = SEGC;
   static constexpr size_t u_off = 0;                                    // real Us[NV][SEG+4]
   static constexpr size_t w_off = u_off + sizeof(real) * NV * (SEG + 4); // real Wt[NV][4][SEG]
   static constexpr size_t fm_off = w_off + sizeof(real) * NV * 4 * SEG;
@@ -287,7 +288,7 @@ struct Smem {
   static constexpr size_t fl_off = fp_off + sizeof(real) * NV * SEG;    // real Fl[NV][SEG+2]
   static constexpr size_t rm_off = fl_off + sizeof(real) * NV * (SEG + 2);  // remote stencils
   static constexpr size_t ex_off = (rm_off + sizeof(real) * NV * 2 * 6 + 15) / 16 * 16;
-  static constexpr size_t bytes = ex_off + sizeof(Exch<real, NV>);
+  static constexpr size_t bytes = ex_off + sizeof(Exch<real, NV, WPV>);
 };
 
 // line-variable k -> grid variable
@@ -303,11 +304,15 @@ __device__ __forceinline__ double bits_double(unsigned long long b) {
 }
 
 // ---------------------------------------------------------------- kernel
+// the mixed form asks for two resident CTAs per SM (128 registers at M = 8)
 template <typename real, int NV, int M, bool PER, int MODE>
-__global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args_in) {
+__global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
+    line_sweep(SweepArgs args_in) {
   constexpr bool MIXED = sizeof(real) == 4;
   using S = Smem<real, NV, M>;
   constexpr int SEG = S::SEG;
+  constexpr int KC = S::KC;
+  constexpr int WPV = S::WPV;
   constexpr int T = NV * KC;
   constexpr int UW = SEG + 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -317,7 +322,7 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args_in) {
   real *Fp = reinterpret_cast<real *>(smem_raw + S::fp_off);
   real *Fl = reinterpret_cast<real *>(smem_raw + S::fl_off);
   real *Rm = reinterpret_cast<real *>(smem_raw + S::rm_off);
-  Exch<real, NV> &ex = *reinterpret_cast<Exch<real, NV> *>(smem_raw + S::ex_off);
+  Exch<real, NV, WPV> &ex = *reinterpret_cast<Exch<real, NV, WPV> *>(smem_raw + S::ex_off);
 
   cg::cluster_group cluster = cg::this_cluster();
   SweepArgs args = args_in;
@@ -513,12 +518,12 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args_in) {
     real cp = real(0), dp = real(0), zp = real(0);
     if (sd == 0) {
       for (int q = 0; q < rank; ++q) {
-        Exch<real, NV> *rx = cluster.map_shared_rank(&ex, q);
+        Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
         fwd_apply<real, PER>(rx->seg_fwd[vv][0], cp, dp, zp);
       }
     } else {
       for (int q = R - 1; q > rank; --q) {
-        Exch<real, NV> *rx = cluster.map_shared_rank(&ex, q);
+        Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
         fwd_apply<real, PER>(rx->seg_fwd[vv][1], cp, dp, zp);
       }
     }
@@ -546,46 +551,36 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args_in) {
   real cmv[M], dmv[M], zmv[M], cpv[M], dpv[M], zpv[M];
   Bwd<real> bm, bp;
   {
-    real pim = real(1), A = real(0), Az = real(0);
+    // the two sides' recurrences are independent: advance them together
+    real pim = real(1), Am = real(0), Azm = real(0);
+    real pip = real(1), Ap = real(0), Azp = real(0);
 #pragma unroll
     for (int j = 0; j < M; ++j) {
       if (j < len) {
-        real zr;
-        Row<real> rm = row_of(s0 + j, 0, zr);
-        real ip = real(1) / (rm.b - rm.a * cpm);
-        cpm = rm.c * ip;
-        dpm = (rm.r - rm.a * dpm) * ip;
-        if (PER) zpm = (zr - rm.a * zpm) * ip;
-        cmv[j] = cpm;
-        dmv[j] = dpm;
-        zmv[j] = PER ? zpm : real(0);
-        A += pim * dpm;
-        if (PER) Az += pim * zpm;
+        real zrm, zrp;
+        Row<real> rm = row_of(s0 + j, 0, zrm);
+        Row<real> rp = row_of(s0 + len - 1 - j, 1, zrp);
+        real ipm = real(1) / (rm.b - rm.a * cpm);
+        real ipp = real(1) / (rp.b - rp.a * cpp);
+        cpm = rm.c * ipm;
+        cpp = rp.c * ipp;
+        dpm = (rm.r - rm.a * dpm) * ipm;
+        dpp = (rp.r - rp.a * dpp) * ipp;
+        if (PER) {
+          zpm = (zrm - rm.a * zpm) * ipm;
+          zpp = (zrp - rp.a * zpp) * ipp;
+        }
+        cmv[j] = cpm; dmv[j] = dpm; zmv[j] = PER ? zpm : real(0);
+        cpv[j] = cpp; dpv[j] = dpp; zpv[j] = PER ? zpp : real(0);
+        Am += pim * dpm;
+        Ap += pip * dpp;
+        if (PER) { Azm += pim * zpm; Azp += pip * zpp; }
         pim *= -cpm;
-      }
-    }
-    bm.A = A; bm.Az = Az; bm.B = pim;
-  }
-  {
-    real pip = real(1), A = real(0), Az = real(0);
-#pragma unroll
-    for (int pos = 0; pos < M; ++pos) {
-      if (pos < len) {
-        real zr;
-        Row<real> rp = row_of(s0 + len - 1 - pos, 1, zr);
-        real ip = real(1) / (rp.b - rp.a * cpp);
-        cpp = rp.c * ip;
-        dpp = (rp.r - rp.a * dpp) * ip;
-        if (PER) zpp = (zr - rp.a * zpp) * ip;
-        cpv[pos] = cpp;
-        dpv[pos] = dpp;
-        zpv[pos] = PER ? zpp : real(0);
-        A += pip * dpp;
-        if (PER) Az += pip * zpp;
         pip *= -cpp;
       }
     }
-    bp.A = A; bp.Az = Az; bp.B = pip;
+    bm.A = Am; bm.Az = Azm; bm.B = pim;
+    bp.A = Ap; bp.Az = Azp; bp.B = pip;
   }
 
   // ------------------------------------------- backward scans (F6)
@@ -631,7 +626,7 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args_in) {
     real x = real(0), z = real(0);
     if (sd == 0) {
       for (int q = R - 1; q > rank; --q) {
-        Exch<real, NV> *rx = cluster.map_shared_rank(&ex, q);
+        Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
         Bwd<real> b = rx->seg_bwd[vv][0];
         x = b.A + b.B * x;
         z = b.Az + b.B * z;
@@ -645,7 +640,7 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args_in) {
       }
     } else {
       for (int q = 0; q < rank; ++q) {
-        Exch<real, NV> *rx = cluster.map_shared_rank(&ex, q);
+        Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
         Bwd<real> b = rx->seg_bwd[vv][1];
         x = b.A + b.B * x;
         z = b.Az + b.B * z;
@@ -718,8 +713,8 @@ __global__ void __launch_bounds__(NV * KC, 1) line_sweep(SweepArgs args_in) {
     }
     cluster.sync();
     {
-      Exch<real, NV> *r0 = cluster.map_shared_rank(&ex, 0);
-      Exch<real, NV> *rl = cluster.map_shared_rank(&ex, R - 1);
+      Exch<real, NV, WPV> *r0 = cluster.map_shared_rank(&ex, 0);
+      Exch<real, NV, WPV> *rl = cluster.map_shared_rank(&ex, R - 1);
       double facm = (r0->sm[v][0][0] + r0->sm[v][0][4] * rl->sm[v][0][2]) /
                     (1.0 + r0->sm[v][0][1] + r0->sm[v][0][4] * rl->sm[v][0][3]);
       double facp = (rl->sm[v][1][0] + rl->sm[v][1][4] * r0->sm[v][1][2]) /

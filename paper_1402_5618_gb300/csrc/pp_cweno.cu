@@ -17,9 +17,11 @@
 
 #include <new>
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "../../include/pp_cweno.h"
+#include "dfloat.cuh"
 #include "sweeps.cuh"
 
 using namespace ppk;
@@ -157,6 +159,121 @@ __global__ void batch_reduce_kernel(const void *Uv, const float *lo, const ProbD
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed 2-D form: the y sweep runs over a transposed copy of the FP32 hi
+// planes (coalesced rows instead of 16 KB-strided columns) and writes its
+// flux difference transposed; the tiled kernels below move data between the
+// two layouts through shared memory.
+constexpr int TT = 32;   // tile edge
+
+// out[v][i][j] = in[v][j][i] for nv planes of ny x nx
+__global__ void transpose_planes_kernel(const float *in, float *out, int nx, int ny, long long ncell) {
+  __shared__ float tile[TT][TT + 1];
+  const int v = blockIdx.z;
+  const int i0 = blockIdx.x * TT, j0 = blockIdx.y * TT;
+  const float *src = in + v * ncell;
+  float *dst = out + v * ncell;
+  for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+    int j = j0 + r, i = i0 + threadIdx.x;
+    if (j < ny && i < nx) tile[r][threadIdx.x] = src[(long long)j * nx + i];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+    int i = i0 + r, j = j0 + threadIdx.x;
+    if (i < nx && j < ny) dst[(long long)i * ny + j] = tile[threadIdx.x][r];
+  }
+}
+
+// Stage combination of the mixed 2-D form on 32 x 32 tiles: L = D_x + D_y
+// (D_y read from its transposed layout), compensated SSP-RK3 update of the
+// hi + lo state, the transposed hi copy of the result for the next y sweep,
+// and the grid-wide reductions (min rho, max rate, cells outside G).
+template <int NV>
+__global__ void combine_t_kernel(const float *Ukh, const float *Ukl, const float *U0h,
+                                 const float *U0l, const float *Dx, const float *DyT, float *Uoh,
+                                 float *Uol, float *UT, int nx, int ny, long long ncell, int stage,
+                                 float hx, float hy, float gg1, Ctl *ctl) {
+  __shared__ float tin[NV][TT][TT + 1];
+  __shared__ float tout[NV][TT][TT + 1];
+  if (!ctl->active) return;
+  const int i0 = blockIdx.x * TT, j0 = blockIdx.y * TT;
+  // D_y tile: DyT[v][i][j], read along j
+  for (int v = 0; v < NV; ++v)
+    for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+      int i = i0 + r, j = j0 + threadIdx.x;
+      if (i < nx && j < ny) tin[v][threadIdx.x][r] = DyT[v * ncell + (long long)i * ny + j];
+    }
+  __syncthreads();
+  const double dt = ctl->dt;
+  const dfl dtd = {float(dt), float(dt - double(float(dt)))};
+  const dfl third = {0.333333343f, -9.93410776e-09f};
+  const dfl two3 = {0.666666687f, -1.98682155e-08f};
+  double mymin = 1e300, mymax = 0.0;
+  unsigned int nbad = 0;
+  unsigned long long firstbad = ~0ull;
+  for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+    int j = j0 + r, i = i0 + threadIdx.x;
+    if (j >= ny || i >= nx) continue;
+    long long addr = (long long)j * nx + i;
+    float Th[NV], Tl[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      long long a = v * ncell + addr;
+      float L = Dx[a] + tin[v][r][threadIdx.x];
+      dfl uk = {Ukh[a], Ukl[a]};
+      dfl s = df_add(uk, df_mul_f(dtd, L));
+      dfl un;
+      if (stage == 0) {
+        un = s;
+      } else {
+        dfl u0 = {U0h[a], U0l[a]};
+        if (stage == 1) un = df_add(df_mul_f(u0, 0.75f), df_mul_f(s, 0.25f));
+        else un = df_add(df_mul(u0, third), df_mul(s, two3));
+      }
+      Uoh[a] = un.hi;
+      Uol[a] = un.lo;
+      Th[v] = un.hi;
+      Tl[v] = un.lo;
+      tout[v][r][threadIdx.x] = un.hi;
+    }
+    float rho = Th[0], mx = Th[1], my = Th[2], E = Th[NV - 1];
+    dfl rE = df_mul({Th[0], Tl[0]}, {Th[NV - 1], Tl[NV - 1]});
+    dfl m2 = df_add(df_mul({Th[1], Tl[1]}, {Th[1], Tl[1]}), df_mul({Th[2], Tl[2]}, {Th[2], Tl[2]}));
+    dfl gq = df_add(rE, {-0.5f * m2.hi, -0.5f * m2.lo});
+    bool ok = rho > 0.0f && gq.hi > 0.0f && isfinite(E) && isfinite(mx) && isfinite(my);
+    if (!ok) {
+      ++nbad;
+      firstbad = min(firstbad, (unsigned long long)addr);
+    } else {
+      mymin = fmin(mymin, (double)rho);
+      float a = sqrtf(gg1 * (gq.hi / (rho * rho)));
+      float rate = (fabsf(mx / rho) + a) / hx + (fabsf(my / rho) + a) / hy;
+      mymax = fmax(mymax, (double)rate);
+    }
+  }
+  __syncthreads();
+  for (int v = 0; v < NV; ++v)
+    for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+      int i = i0 + r, j = j0 + threadIdx.x;
+      if (i < nx && j < ny) UT[v * ncell + (long long)i * ny + j] = tout[v][threadIdx.x][r];
+    }
+  for (int d = 16; d > 0; d >>= 1) {
+    mymin = fmin(mymin, __shfl_down_sync(0xffffffffu, mymin, d));
+    mymax = fmax(mymax, __shfl_down_sync(0xffffffffu, mymax, d));
+    nbad += __shfl_down_sync(0xffffffffu, nbad, d);
+    unsigned long long fb = __shfl_down_sync(0xffffffffu, firstbad, d);
+    firstbad = fb < firstbad ? fb : firstbad;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&ctl->minrho[stage], dbits(mymin));
+    if (stage == 2) atomicMax(&ctl->rate, dbits(mymax));
+    if (nbad) {
+      atomicAdd(&ctl->nviol, (unsigned long long)nbad);
+      atomicMin(&ctl->first_bad, firstbad);
+    }
+  }
+}
+
 // FP64 planes <-> FP32 hi / lo plane pairs (mixed form state)
 __global__ void split_kernel(const double *in, float *hi, float *lo, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -209,6 +326,11 @@ struct pp_cweno_s {
   Ctl *hctl = nullptr;   // pinned mirror [nprob]
   cudaGraphExec_t graph = nullptr;
   long long launches_per_step = 0;
+  int m = 8;                  // rows per thread chunk of the line kernels (autotuned)
+  // mixed 2-D single problem: transposed hi planes and transposed y-sweep output
+  bool ytrans = false;
+  float *UT = nullptr, *DT = nullptr;
+  bool tuned = false;
   // batch
   bool batch = false;
   int nprob = 1;
@@ -303,8 +425,8 @@ cudaError_t dispatch(const pp_cweno_s *h, int mode, bool periodic, const SweepAr
   c.periodic = periodic;
   c.mode = mode;
   c.attrs_only = attrs_only;
-  return h->cfg.precision == PP_PREC_FP64 ? launch_sweep_f64(c, a, nlines, h->stream)
-                                         : launch_sweep_f32(c, a, nlines, h->stream);
+  c.m = h->m;
+  return launch_sweep(c, a, nlines, h->stream);
 }
 
 // Single-problem launch.  Uin, U0, Uout are state buffers (FP64 planes or
@@ -368,21 +490,82 @@ cudaError_t launch_group(const pp_cweno_s *h, const LineGroup &g, int mode, cons
   return dispatch(h, mode, g.periodic, a, g.nlines, attrs_only);
 }
 
-// enqueue one step: the per-problem dt kernel, then 3 stages
-cudaError_t enqueue_step(pp_cweno_s *h) {
+// y sweep of the mixed 2-D form over the transposed hi planes: a row sweep
+// of the transposed grid writing D_y transposed
+cudaError_t launch_ysweep_t(const pp_cweno_s *h, int stage) {
+  SweepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.Uh = h->UT;
+  fill_common(h, a, stage, 0.0, h->ctl);
+  a.Dout = h->DT;
+  a.ncell = h->ncell;
+  a.n = (int)h->ny;
+  a.cell_stride = 1;
+  a.line_stride = h->ny;
+  a.vn = 2;
+  a.vt = 1;
+  a.bclo = h->cfg.bc[2];
+  a.bchi = h->cfg.bc[3];
+  a.h = h->dy;
+  a.h_other = h->dx;
+  a.R = seg_count(a.n);
+  return dispatch(h, MODE_XSWEEP, a.bclo == PP_BC_PERIODIC, a, h->nx, false);
+}
+
+cudaError_t launch_combine_t(const pp_cweno_s *h, const void *Uin, void *Uout, int stage) {
+  dim3 grid((unsigned)((h->nx + TT - 1) / TT), (unsigned)((h->ny + TT - 1) / TT));
+  const float *Ukh = hi_of(const_cast<void *>(Uin)), *Ukl = lo_of(h, const_cast<void *>(Uin));
+  const float *U0h = hi_of(h->U0), *U0l = lo_of(h, h->U0);
+  float *Uoh = hi_of(Uout), *Uol = lo_of(h, Uout);
+  combine_t_kernel<4><<<grid, dim3(TT, 8), 0, h->stream>>>(
+      Ukh, Ukl, U0h, U0l, reinterpret_cast<const float *>(h->D), h->DT, Uoh, Uol, h->UT, (int)h->nx,
+      (int)h->ny, h->ncell, stage, (float)h->dx, (float)h->dy,
+      (float)(h->cfg.gamma * (h->cfg.gamma - 1.0)), h->ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t transpose_state_hi(const pp_cweno_s *h) {
+  dim3 grid((unsigned)((h->nx + TT - 1) / TT), (unsigned)((h->ny + TT - 1) / TT), (unsigned)h->nv);
+  transpose_planes_kernel<<<grid, dim3(TT, 8), 0, h->stream>>>(hi_of(h->U0), h->UT, (int)h->nx,
+                                                               (int)h->ny, h->ncell);
+  return cudaGetLastError();
+}
+
+// enqueue one step: the per-problem dt kernel, then 3 stages; with ev, an
+// event is recorded after every launch (ev[0] before the first)
+cudaError_t enqueue_step(pp_cweno_s *h, cudaEvent_t *ev = nullptr, int *nev = nullptr) {
+  int k = 0;
+  auto mark = [&]() {
+    if (ev) cudaEventRecord(ev[k++], h->stream);
+  };
+  mark();
   step_begin_kernel<<<(h->nprob + 127) / 128, 128, 0, h->stream>>>(h->ctl, h->nprob);
   cudaError_t e = cudaGetLastError();
+  mark();
   if (e != cudaSuccess) return e;
   for (int s = 0; s < 3; ++s) {
     const void *Uin = s == 0 ? h->U0 : h->U1;
     void *Uout = s == 2 ? h->U0 : h->U1;
+    if (h->ytrans) {
+      e = launch(h, MODE_XSWEEP, true, Uin, h->U0, nullptr, h->D, nullptr, s, 0.0, h->ctl);
+      mark();
+      if (e == cudaSuccess) e = launch_ysweep_t(h, s);
+      mark();
+      if (e == cudaSuccess) e = launch_combine_t(h, Uin, Uout, s);
+      mark();
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     if (!h->batch) {
       if (h->nv == 4) {
         e = launch(h, MODE_XSWEEP, true, Uin, h->U0, nullptr, h->D, nullptr, s, 0.0, h->ctl);
+        mark();
         if (e != cudaSuccess) return e;
         e = launch(h, MODE_FINAL, false, Uin, h->U0, h->D, nullptr, Uout, s, 0.0, h->ctl);
+        mark();
       } else {
         e = launch(h, MODE_FINAL, true, Uin, h->U0, nullptr, nullptr, Uout, s, 0.0, h->ctl);
+        mark();
       }
       if (e != cudaSuccess) return e;
       continue;
@@ -399,6 +582,7 @@ cudaError_t enqueue_step(pp_cweno_s *h) {
       if (e != cudaSuccess) return e;
     }
   }
+  if (nev) *nev = k;
   return cudaSuccess;
 }
 
@@ -496,27 +680,100 @@ int finish_create(pp_cweno_s *h) {
   if (e == cudaSuccess) e = cudaMalloc(&h->ctl, sizeof(Ctl) * h->nprob);
   if (e == cudaSuccess) e = cudaMalloc(&h->ctl_scratch, sizeof(Ctl) * h->nprob);
   if (e == cudaSuccess) e = cudaMallocHost(&h->hctl, sizeof(Ctl) * h->nprob);
+  h->ytrans = is_mixed(h) && h->nv == 4 && !h->batch;
+  if (e == cudaSuccess && h->ytrans) e = cudaMalloc(&h->UT, sizeof(float) * (size_t)nvals(h));
+  if (e == cudaSuccess && h->ytrans) e = cudaMalloc(&h->DT, sizeof(float) * (size_t)nvals(h));
   if (e != cudaSuccess) return PP_ERR_CUDA;
   memset(h->hctl, 0, sizeof(Ctl) * h->nprob);
   // kernel attributes (dynamic shared memory, cluster size) are set here,
   // never inside a stream capture
   const int modes[3] = {MODE_XSWEEP, MODE_FINAL, MODE_OPERATOR};
-  for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
-    if (h->nv == 3 && modes[m] == MODE_XSWEEP) continue;
-    for (int per = 0; per < 2 && e == cudaSuccess; ++per) {
-      SweepArgs a;
-      memset(&a, 0, sizeof(a));
-      a.R = 1;
-      e = dispatch(h, modes[m], per != 0, a, 0, true);
+  const int keep_m = h->m;
+  for (int mm = 8; mm <= 16 && e == cudaSuccess; mm += 8) {
+    h->m = mm;
+    for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
+      if (h->nv == 3 && modes[m] == MODE_XSWEEP) continue;
+      for (int per = 0; per < 2 && e == cudaSuccess; ++per) {
+        SweepArgs a;
+        memset(&a, 0, sizeof(a));
+        a.R = 1;
+        e = dispatch(h, modes[m], per != 0, a, 0, true);
+      }
     }
   }
+  h->m = keep_m;
   if (e != cudaSuccess) return PP_ERR_CUDA;
   if (h->batch) {
     h->launches_per_step = 1;
     for (int s = 0; s < 3; ++s) h->launches_per_step += (long long)h->groups.size();
   } else {
-    h->launches_per_step = 1 + 3 * (h->nv == 4 ? 2 : 1);
+    h->launches_per_step = 1 + 3 * (h->ytrans ? 3 : (h->nv == 4 ? 2 : 1));
   }
+  return PP_OK;
+}
+
+// Autotuner: the rows per thread chunk (M = 8: more threads and a deeper
+// parallel scan; M = 16: longer serial elimination runs, one warp per
+// variable) is picked per handle by timing the first sweep of a stage on the
+// handle's own state, with CUDA events on its stream.  The sweep writes only
+// scratch (the x-sweep output buffer, or the stage buffer as an operator
+// output), and the choice is cached per (precision, ndim, nx, ny, periodic).
+struct TuneKey {
+  int prec, ndim;
+  long long nx, ny;
+  int per;
+  bool operator==(const TuneKey &o) const {
+    return prec == o.prec && ndim == o.ndim && nx == o.nx && ny == o.ny && per == o.per;
+  }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, int>> g_tune_cache;
+
+int autotune(pp_cweno_s *h) {
+  if (h->tuned) return PP_OK;
+  h->tuned = true;
+  if (h->batch) return PP_OK;   // batches keep the default chunk length
+  TuneKey key{h->cfg.precision, h->nv == 4 ? 2 : 1, h->nx, h->ny, h->cfg.bc[0] == PP_BC_PERIODIC};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto &kv : g_tune_cache)
+      if (kv.first == key) { h->m = kv.second; return PP_OK; }
+  }
+  Ctl z;
+  memset(&z, 0, sizeof(z));
+  z.active = 1;
+  if (cudaMemcpyAsync(h->ctl_scratch, &z, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return PP_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PP_ERR_CUDA;
+  float best = 1e30f;
+  int best_m = 8;
+  cudaError_t e = cudaSuccess;
+  for (int mm = 8; mm <= 16 && e == cudaSuccess; mm += 8) {
+    h->m = mm;
+    float t_min = 1e30f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      if (h->nv == 4)
+        e = launch(h, MODE_XSWEEP, true, h->U0, h->U0, nullptr, h->D, nullptr, 0, 1e-13,
+                   h->ctl_scratch);
+      else
+        e = launch(h, MODE_OPERATOR, true, h->U0, h->U0, nullptr, nullptr, nullptr, 0, 1e-13,
+                   h->ctl_scratch, false, reinterpret_cast<double *>(h->U1));
+      cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0 && t < t_min) t_min = t;   // first launch is a warm-up
+    }
+    if (t_min < best) { best = t_min; best_m = mm; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->m = best_m;
+  if (e != cudaSuccess) return PP_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.push_back({key, best_m});
   return PP_OK;
 }
 
@@ -677,6 +934,7 @@ int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) 
     }
     split_kernel<<<grid_for(nval), 256, 0, h->stream>>>(src, hi_of(h->U0), lo_of(h, h->U0), nval);
     e = cudaGetLastError();
+    if (e == cudaSuccess && h->ytrans) e = transpose_state_hi(h);
   } else {
     e = cudaMemcpyAsync(h->U0, U, bytes,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
@@ -706,7 +964,16 @@ int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) 
   }
   if ((rc = push_ctl(h))) return rc;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
-  return bad ? PP_ERR_STATE : PP_OK;
+  if (bad) return PP_ERR_STATE;
+  if (!h->tuned) {
+    int m0 = h->m;
+    if ((rc = autotune(h))) return rc;
+    if (h->m != m0 && h->graph) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+  }
+  return PP_OK;
 }
 
 int pp_cweno_get_state(pp_cweno_t h, double *U, int on_device, double *t, int64_t *steps) {
@@ -914,6 +1181,12 @@ int pp_cweno_problem_cells(pp_cweno_t h, int64_t k, int64_t *ncell) {
   return PP_OK;
 }
 
+int pp_cweno_rows_per_chunk(pp_cweno_t h, int *m) {
+  if (!h || !m) return PP_ERR_ARG;
+  *m = h->m;
+  return PP_OK;
+}
+
 int pp_cweno_launches_per_step(pp_cweno_t h, int64_t *n) {
   if (!h || !n) return PP_ERR_ARG;
   *n = h->launches_per_step;
@@ -932,36 +1205,20 @@ int pp_cweno_profile_step(pp_cweno_t h, float *ms, int nmax, int *nk) {
   c->step_limit = c->step + 1;
   c->err_steps = 0;
   if ((rc = push_ctl(h))) return rc;
-  const int nker = 1 + 3 * (h->nv == 4 ? 2 : 1);
-  cudaEvent_t ev[16];
-  for (int k = 0; k <= nker; ++k)
+  const int nev = (int)h->launches_per_step + 1;
+  std::vector<cudaEvent_t> ev((size_t)nev);
+  for (int k = 0; k < nev; ++k)
     if (cudaEventCreate(&ev[k]) != cudaSuccess) return PP_ERR_CUDA;
-  cudaError_t e = cudaEventRecord(ev[0], h->stream);
-  int idx = 0;
-  step_begin_kernel<<<1, 128, 0, h->stream>>>(h->ctl, 1);
-  cudaEventRecord(ev[++idx], h->stream);
-  for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
-    const void *Uin = s == 0 ? h->U0 : h->U1;
-    void *Uout = s == 2 ? h->U0 : h->U1;
-    if (h->nv == 4) {
-      e = launch(h, MODE_XSWEEP, true, Uin, h->U0, nullptr, h->D, nullptr, s, 0.0, h->ctl);
-      cudaEventRecord(ev[++idx], h->stream);
-      if (e == cudaSuccess)
-        e = launch(h, MODE_FINAL, false, Uin, h->U0, h->D, nullptr, Uout, s, 0.0, h->ctl);
-      cudaEventRecord(ev[++idx], h->stream);
-    } else {
-      e = launch(h, MODE_FINAL, true, Uin, h->U0, nullptr, nullptr, Uout, s, 0.0, h->ctl);
-      cudaEventRecord(ev[++idx], h->stream);
-    }
-  }
+  int got = 0;
+  cudaError_t e = enqueue_step(h, ev.data(), &got);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   int n = 0;
-  for (int k = 0; k < nker && k < nmax && e == cudaSuccess; ++k) {
+  for (int k = 0; k + 1 < got && n < nmax && e == cudaSuccess; ++k) {
     float t = 0.f;
     e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
     ms[n++] = t;
   }
-  for (int k = 0; k <= nker; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < nev; ++k) cudaEventDestroy(ev[k]);
   *nk = n;
   if (e != cudaSuccess) return PP_ERR_CUDA;
   if ((rc = pull_ctl(h))) return rc;
@@ -1013,6 +1270,8 @@ int pp_cweno_destroy(pp_cweno_t h) {
   cudaFree(h->ctl);
   cudaFree(h->ctl_scratch);
   cudaFree(h->probs);
+  cudaFree(h->UT);
+  cudaFree(h->DT);
   for (auto &g : h->groups) cudaFree(g.lines);
   if (h->hctl) cudaFreeHost(h->hctl);
   delete h;

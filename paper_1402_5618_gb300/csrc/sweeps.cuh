@@ -8,8 +8,7 @@
 
 namespace ppk {
 
-constexpr int M_ROWS = 8;   // rows per thread chunk
-constexpr int SEG_CELLS = KC * M_ROWS;
+constexpr int SEG_CELLS = SEGC;   // cells per CTA of a line's cluster
 
 struct LaunchCfg {
   int precision;   // 0 fp64, 1 mixed (fp32 line arithmetic)
@@ -17,19 +16,31 @@ struct LaunchCfg {
   bool periodic;
   int mode;        // MODE_*
   bool attrs_only; // set the kernel's attributes, launch nothing
+  int m;           // rows per thread chunk: 8 or 16 (picked by the autotuner)
 };
 
-// Launch one sweep over nlines lines with R CTAs per line (cluster of R).
-// Implemented in the per-precision translation units.
-cudaError_t launch_sweep_f64(const LaunchCfg &c, const SweepArgs &a, long long nlines,
-                             cudaStream_t st);
-cudaError_t launch_sweep_f32(const LaunchCfg &c, const SweepArgs &a, long long nlines,
-                             cudaStream_t st);
+// Launch one sweep over nlines lines with R CTAs per line (cluster of R);
+// one entry per (precision, chunk length), each in its own translation unit.
+cudaError_t launch_sweep_f64_m8(const LaunchCfg &c, const SweepArgs &a, long long nlines,
+                                cudaStream_t st);
+cudaError_t launch_sweep_f64_m16(const LaunchCfg &c, const SweepArgs &a, long long nlines,
+                                 cudaStream_t st);
+cudaError_t launch_sweep_f32_m8(const LaunchCfg &c, const SweepArgs &a, long long nlines,
+                                cudaStream_t st);
+cudaError_t launch_sweep_f32_m16(const LaunchCfg &c, const SweepArgs &a, long long nlines,
+                                 cudaStream_t st);
 
-template <typename real, int NV, bool PER, int MODE>
-cudaError_t launch_one(const SweepArgs &a, long long nlines, cudaStream_t st, bool attrs_only) {
-  using S = Smem<real, NV, M_ROWS>;
-  auto kern = line_sweep<real, NV, M_ROWS, PER, MODE>;
+inline cudaError_t launch_sweep(const LaunchCfg &c, const SweepArgs &a, long long nlines,
+                                cudaStream_t st) {
+  if (c.precision == 0) return c.m == 16 ? launch_sweep_f64_m16(c, a, nlines, st)
+                                        : launch_sweep_f64_m8(c, a, nlines, st);
+  return c.m == 16 ? launch_sweep_f32_m16(c, a, nlines, st) : launch_sweep_f32_m8(c, a, nlines, st);
+}
+
+template <typename real, int NV, int M, bool PER, int MODE>
+cudaError_t launch_m(const SweepArgs &a, long long nlines, cudaStream_t st, bool attrs_only) {
+  using S = Smem<real, NV, M>;
+  auto kern = line_sweep<real, NV, M, PER, MODE>;
   if (attrs_only) {   // called at handle creation, outside any stream capture
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::bytes);
@@ -38,7 +49,7 @@ cudaError_t launch_one(const SweepArgs &a, long long nlines, cudaStream_t st, bo
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nlines * a.R), 1, 1);
-  cfg.blockDim = dim3(NV * KC, 1, 1);
+  cfg.blockDim = dim3(NV * S::KC, 1, 1);
   cfg.dynamicSmemBytes = S::bytes;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -51,28 +62,28 @@ cudaError_t launch_one(const SweepArgs &a, long long nlines, cudaStream_t st, bo
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <typename real>
+template <typename real, int M>
 cudaError_t launch_dispatch(const LaunchCfg &c, const SweepArgs &a, long long nlines,
                             cudaStream_t st) {
   if (c.nv == 3) {
     if (c.mode == MODE_FINAL)
-      return c.periodic ? launch_one<real, 3, true, MODE_FINAL>(a, nlines, st, c.attrs_only)
-                        : launch_one<real, 3, false, MODE_FINAL>(a, nlines, st, c.attrs_only);
+      return c.periodic ? launch_m<real, 3, M, true, MODE_FINAL>(a, nlines, st, c.attrs_only)
+                        : launch_m<real, 3, M, false, MODE_FINAL>(a, nlines, st, c.attrs_only);
     if (c.mode == MODE_OPERATOR)
-      return c.periodic ? launch_one<real, 3, true, MODE_OPERATOR>(a, nlines, st, c.attrs_only)
-                        : launch_one<real, 3, false, MODE_OPERATOR>(a, nlines, st, c.attrs_only);
+      return c.periodic ? launch_m<real, 3, M, true, MODE_OPERATOR>(a, nlines, st, c.attrs_only)
+                        : launch_m<real, 3, M, false, MODE_OPERATOR>(a, nlines, st, c.attrs_only);
     return cudaErrorInvalidValue;
   }
   if (c.nv == 4) {
     if (c.mode == MODE_XSWEEP)
-      return c.periodic ? launch_one<real, 4, true, MODE_XSWEEP>(a, nlines, st, c.attrs_only)
-                        : launch_one<real, 4, false, MODE_XSWEEP>(a, nlines, st, c.attrs_only);
+      return c.periodic ? launch_m<real, 4, M, true, MODE_XSWEEP>(a, nlines, st, c.attrs_only)
+                        : launch_m<real, 4, M, false, MODE_XSWEEP>(a, nlines, st, c.attrs_only);
     if (c.mode == MODE_FINAL)
-      return c.periodic ? launch_one<real, 4, true, MODE_FINAL>(a, nlines, st, c.attrs_only)
-                        : launch_one<real, 4, false, MODE_FINAL>(a, nlines, st, c.attrs_only);
+      return c.periodic ? launch_m<real, 4, M, true, MODE_FINAL>(a, nlines, st, c.attrs_only)
+                        : launch_m<real, 4, M, false, MODE_FINAL>(a, nlines, st, c.attrs_only);
     if (c.mode == MODE_OPERATOR)
-      return c.periodic ? launch_one<real, 4, true, MODE_OPERATOR>(a, nlines, st, c.attrs_only)
-                        : launch_one<real, 4, false, MODE_OPERATOR>(a, nlines, st, c.attrs_only);
+      return c.periodic ? launch_m<real, 4, M, true, MODE_OPERATOR>(a, nlines, st, c.attrs_only)
+                        : launch_m<real, 4, M, false, MODE_OPERATOR>(a, nlines, st, c.attrs_only);
   }
   return cudaErrorInvalidValue;
 }
