@@ -165,6 +165,33 @@ int pp_cweno_profile_step(pp_cweno_t h, float *ms, int nmax, int *nk);
  * dependent-chain-free kernel filling every SM.  Synchronises. */
 int pp_cweno_fma_peak(int fp64, double *gflops);
 
+/* The spatial operator of one FP64 problem with no device allocation at all
+ * (the paper has no counterpart; this is a service of this library).
+ *
+ * For callers that cannot call cudaMalloc: code that runs while a CUDA graph
+ * is being captured, inside a fixed memory budget or a pool that must not
+ * grow, or in a loop that may not synchronise the device (cudaMalloc and
+ * cudaFree can).  Such a caller passes its own U and L (device pointers,
+ * FP64 planes in the state layout) and gets L = L(U) as pp_cweno_operator
+ * computes it, with the same kernels; cfg describes the grid as for
+ * pp_cweno_create and must select PP_PREC_FP64.  eps > 0 is the limiter
+ * epsilon; eps <= 0 takes min(eps_pos, min rho) on the device, and then a
+ * state with a cell outside G leaves L unwritten.
+ *
+ * Scratch: the x-sweep flux difference and a control block live in one
+ * fixed 32 MiB device array inside the library (every GPU that loads the
+ * library holds it until exit), so a 2-D grid may have at most
+ * (32 MiB - 256 B) / 32 B, about 1.05 million cells (1024 x 1023); larger
+ * grids return PP_ERR_UNSUPPORTED.  1-D grids need no scratch beyond the
+ * control block.  Every call shares the array: calls whose work overlaps on
+ * the GPU (other streams, other host threads on the same device) race.  The
+ * first call on a device resolves the array's device address and sets the
+ * kernels' launch attributes with that device current; make it before any
+ * stream capture.  The work is enqueued on cuda_stream (NULL = legacy
+ * default stream) and the call returns without synchronising. */
+int pp_cweno_operator_noalloc(const pp_cweno_config *cfg, const double *U_dev, double *L_dev,
+                              double eps, void *cuda_stream);
+
 /* Free all device memory of the handle (h may be NULL). */
 int pp_cweno_destroy(pp_cweno_t h);
 

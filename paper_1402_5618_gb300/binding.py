@@ -46,7 +46,7 @@ EXPORTS = [
     "pp_cweno_operator", "pp_cweno_stats", "pp_cweno_num_problems", "pp_cweno_problem_cells",
     "pp_cweno_rows_per_chunk",
     "pp_cweno_launches_per_step", "pp_cweno_profile_step", "pp_cweno_fma_peak",
-    "pp_cweno_destroy", "pp_cweno_strerror",
+    "pp_cweno_operator_noalloc", "pp_cweno_destroy", "pp_cweno_strerror",
 ]
 
 _lib = None
@@ -88,6 +88,7 @@ def lib(build_if_missing: bool = False):
     L.pp_cweno_rows_per_chunk.argtypes = [vp, C.POINTER(C.c_int)]
     L.pp_cweno_profile_step.argtypes = [vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
     L.pp_cweno_fma_peak.argtypes = [C.c_int, dp]
+    L.pp_cweno_operator_noalloc.argtypes = [cfgp, vp, vp, C.c_double, vp]
     L.pp_cweno_destroy.argtypes = [vp]
     L.pp_cweno_strerror.argtypes = [C.c_int]
     L.pp_cweno_strerror.restype = C.c_char_p
@@ -136,6 +137,16 @@ def fma_peak(fp64: bool) -> float:
     g = C.c_double()
     _check(lib().pp_cweno_fma_peak(int(fp64), C.byref(g)), "fma_peak")
     return g.value
+
+
+def operator_noalloc(cfg, U_dev, L_dev, eps: float = 0.0, stream=None) -> None:
+    """L = L(U) of one FP64 problem using the library's fixed device scratch
+    (no allocation); asynchronous on the given stream."""
+    pu, du = _ptr(U_dev)
+    pl, dl = _ptr(L_dev)
+    assert du and dl, "operator_noalloc() takes device tensors"
+    st = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+    _check(lib().pp_cweno_operator_noalloc(C.byref(cfg), pu, pl, eps, st), "operator_noalloc")
 
 
 def _ptr(a):

@@ -305,6 +305,32 @@ __global__ void fma_peak_kernel(T *out, int iters, T a, T b) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Fixed device scratch for pp_cweno_operator_noalloc: the x-sweep flux
+// difference of one 2-D problem (FP64) and one control block.  The array
+// lives for as long as the library is loaded, on every GPU that loads it.
+constexpr size_t NOALLOC_BYTES = size_t(32) << 20;   // 32 MiB
+constexpr size_t NOALLOC_CTL_BYTES = 256;
+static_assert(sizeof(Ctl) <= NOALLOC_CTL_BYTES, "control block must fit its slot");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// control block of a single operator evaluation: reductions reset, the
+// limiter epsilon min(eps_pos, min rho) taken from the preceding reduction
+// (or the caller's eps), active set
+__global__ void noalloc_ctl_reset(Ctl *ctl) {
+  if (threadIdx.x != 0) return;
+  unsigned char *b = reinterpret_cast<unsigned char *>(ctl);
+  for (size_t i = 0; i < sizeof(Ctl); ++i) b[i] = 0;
+  ctl->minrho[2] = 0x7ff0000000000000ull;
+  ctl->first_bad = ~0ull;
+}
+
+__global__ void noalloc_ctl_arm(Ctl *ctl, double eps_pos, double eps) {
+  if (threadIdx.x != 0) return;
+  ctl->eps0 = eps > 0.0 ? eps : fmin(eps_pos, bitsd(ctl->minrho[2]));
+  ctl->active = ctl->nviol == 0 && ctl->eps0 > 0.0;
+}
+
 // a batched launch group: lines of equal cluster size and boundary kind
 struct LineGroup {
   int R;
@@ -1259,6 +1285,91 @@ int pp_cweno_fma_peak(int fp64, double *gflops) {
   double flops = 2.0 * 8.0 * (double)iters * (double)threads * (double)blocks;
   *gflops = flops / (best * 1e-3) / 1e9;
   return PP_OK;
+}
+
+// Per-device address of g_noalloc_scratch.  Host code may not use the
+// symbol itself as a device address; the first call on a device resolves it
+// (and sets the kernels' launch attributes) with that device current.
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[128];
+static bool g_noalloc_ready[128];
+
+int pp_cweno_operator_noalloc(const pp_cweno_config *cfg, const double *U_dev, double *L_dev,
+                              double eps, void *cuda_stream) {
+  if (!cfg || !U_dev || !L_dev) return PP_ERR_ARG;
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (cfg->precision != PP_PREC_FP64) return PP_ERR_UNSUPPORTED;
+  const int nv = cfg->ndim == 2 ? 4 : 3;
+  const long long nx = cfg->nx, ny = cfg->ndim == 2 ? cfg->ny : 1;
+  const size_t dbytes = cfg->ndim == 2 ? sizeof(double) * (size_t)nv * (size_t)(nx * ny) : 0;
+  if (dbytes > NOALLOC_BYTES - NOALLOC_CTL_BYTES) return PP_ERR_UNSUPPORTED;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return PP_ERR_CUDA;
+
+  // a stack handle that borrows the fixed scratch: nothing is allocated
+  pp_cweno_s h;
+  h.cfg = *cfg;
+  h.stream = (cudaStream_t)cuda_stream;
+  h.nv = nv;
+  h.nx = nx;
+  h.ny = ny;
+  h.ncell = nx * ny;
+  h.dx = (cfg->x1 - cfg->x0) / (double)nx;
+  h.dy = cfg->ndim == 2 ? (cfg->y1 - cfg->y0) / (double)ny : 1.0;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ready[dev]) {
+      void *ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return PP_ERR_CUDA;
+      const int modes[3] = {MODE_XSWEEP, MODE_FINAL, MODE_OPERATOR};
+      for (int ndim = 1; ndim <= 2; ++ndim) {
+        pp_cweno_s t;
+        t.cfg = *cfg;
+        t.cfg.precision = PP_PREC_FP64;
+        t.nv = ndim == 2 ? 4 : 3;
+        for (int m = 0; m < 3; ++m) {
+          if (t.nv == 3 && modes[m] == MODE_XSWEEP) continue;
+          for (int per = 0; per < 2; ++per) {
+            SweepArgs a;
+            memset(&a, 0, sizeof(a));
+            a.R = 1;
+            if (dispatch(&t, modes[m], per != 0, a, 0, true) != cudaSuccess) return PP_ERR_CUDA;
+          }
+        }
+      }
+      g_noalloc_ptr[dev] = ptr;
+      g_noalloc_ready[dev] = true;
+    }
+  }
+  unsigned char *base = reinterpret_cast<unsigned char *>(g_noalloc_ptr[dev]);
+  Ctl *ctl = reinterpret_cast<Ctl *>(base);
+  void *D = base + NOALLOC_CTL_BYTES;
+
+  noalloc_ctl_reset<<<1, 32, 0, h.stream>>>(ctl);
+  if (!(eps > 0.0)) {
+    h.nprob = 1;
+    const int blocks = (int)fmin(1184.0, (double)((h.ncell + 255) / 256));
+    if (nv == 4)
+      state_reduce_kernel<4><<<blocks < 1 ? 1 : blocks, 256, 0, h.stream>>>(
+          U_dev, nullptr, h.ncell, h.nx, h.dx, h.dy, cfg->gamma, ctl);
+    else
+      state_reduce_kernel<3><<<blocks < 1 ? 1 : blocks, 256, 0, h.stream>>>(
+          U_dev, nullptr, h.ncell, h.nx, h.dx, h.dy, cfg->gamma, ctl);
+  }
+  noalloc_ctl_arm<<<1, 32, 0, h.stream>>>(ctl, cfg->eps_pos, eps);
+  if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
+  cudaError_t e;
+  if (nv == 4) {
+    e = launch(&h, MODE_XSWEEP, true, U_dev, U_dev, nullptr, D, nullptr, 0, 0.0, ctl);
+    if (e == cudaSuccess)
+      e = launch(&h, MODE_OPERATOR, false, U_dev, U_dev, D, nullptr, nullptr, 0, 0.0, ctl, false,
+                 L_dev);
+  } else {
+    e = launch(&h, MODE_OPERATOR, true, U_dev, U_dev, nullptr, nullptr, nullptr, 0, 0.0, ctl,
+               false, L_dev);
+  }
+  return cuerr(e);
 }
 
 int pp_cweno_destroy(pp_cweno_t h) {

@@ -1,0 +1,77 @@
+"""pp_cweno_operator_noalloc: the operator evaluated with the library's fixed
+device scratch instead of allocated memory, for callers that cannot call
+cudaMalloc.  It must give what pp_cweno_operator gives (same tolerance as the
+other operator tests), on two calls in a row sharing the scratch array.
+
+This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+from paper_1402_5618_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_5618_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _scale(p, U):
+    nv = U.shape[0]
+    flat = U.reshape(nv, -1)
+    rho = flat[0]
+    vel = np.sqrt(np.sum(flat[1:nv - 1] ** 2, axis=0)) / rho
+    pr = (p.gamma - 1) * (flat[nv - 1] - 0.5 * rho * vel ** 2)
+    smax = np.max(vel + np.sqrt(p.gamma * np.maximum(pr, 0) / rho))
+    mom = np.abs(rho * vel * vel + pr).max()
+    F = [np.abs(rho * vel).max(), mom] + ([mom] if nv == 4 else [])
+    F.append(np.abs(vel * (flat[nv - 1] + pr)).max())
+    h = min(p.dx, p.dy) if p.ndim == 2 else p.dx
+    return np.array([(F[v] + np.abs(flat[v]).max() * smax) / h for v in range(nv)])
+
+
+def _handle_operator(B, p, Ud, eps):
+    s = B.Solver(B.config_from_problem(p))
+    L = torch.zeros_like(Ud)
+    s.operator(Ud, L, eps)
+    s.close()
+    return L.cpu().numpy().reshape(p.U0.shape)
+
+
+@pytest.mark.parametrize("name,make,eps", [
+    ("jumps_2d_300x200", lambda: W.random_jumps_2d(300, 200, stream=71), 1e-13),
+    ("vortex_2d_64_device_eps", lambda: W.vortex_2d(64), 0.0),
+    ("riemann_1d_1300", lambda: W.riemann_1d(1300, (1.0, 0.4, 1.0), (0.2, -0.2, 0.1), bc=(2, 1)), 1e-13),
+])
+def test_noalloc_operator_matches_handle_operator_twice(B, name, make, eps):
+    p = make()
+    Ud = torch.from_numpy(np.ascontiguousarray(p.U0).ravel()).cuda()
+    ref = _handle_operator(B, p, Ud, eps if eps > 0 else min(1e-13, p.U0[0].min()))
+    scale = _scale(p, p.U0)
+    cfg = B.config_from_problem(p)
+    for _ in range(2):
+        L = torch.full_like(Ud, float("nan"))
+        B.operator_noalloc(cfg, Ud, L, eps)
+        torch.cuda.synchronize()
+        got = L.cpu().numpy().reshape(p.U0.shape)
+        for v in range(p.U0.shape[0]):
+            assert np.abs(got[v] - ref[v]).max() <= 1e-12 * scale[v], (name, v)
+
+
+def test_noalloc_rejects_oversized_and_mixed(B):
+    big = B.make_config(ndim=2, nx=2048, ny=2048, bc=(1, 1, 1, 1))
+    U = torch.zeros(4 * 2048 * 2048, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.PPError) as e:
+        B.operator_noalloc(big, U, U)
+    assert e.value.code == B.PP_ERR_UNSUPPORTED
+    mixed = B.make_config(ndim=1, nx=64, precision=B.PREC_MIXED)
+    u = torch.zeros(3 * 64, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.PPError) as e:
+        B.operator_noalloc(mixed, u, u)
+    assert e.value.code == B.PP_ERR_UNSUPPORTED
