@@ -255,7 +255,13 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", choices=["mixed", "fp64"], default=None,
+                    help="only run --steps steps of the blast on an --n^2 grid (for ncu)")
+    ap.add_argument("--n", type=int, default=N_GRID)
     args = ap.parse_args()
+    if args.profile_only:
+        profile_only(args)
+        return
     ws, rank, local = _dist()
     if ws > 1:
         import torch
@@ -320,6 +326,26 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def profile_only(args):
+    """The blast on an n^2 grid, `steps` steps, nothing else (a small case for
+    ncu captures of the line kernels)."""
+    import numpy as np
+    import torch
+
+    from paper_1402_5618_gb300 import binding as B
+    from paper_1402_5618_gb300 import workloads as W
+    prec = B.PREC_MIXED if args.profile_only == "mixed" else B.PREC_FP64
+    p = W.blast_2d(args.n)
+    s = B.Solver(B.config_from_problem(p, prec, cfl_positivity_cap=True))
+    s.set_state(np.ascontiguousarray(p.U0).ravel())
+    s.enqueue_steps(args.steps)
+    torch.cuda.synchronize()
+    st = s.stats()
+    print(json.dumps({"profile_only": args.profile_only, "n": args.n, "steps": st.steps,
+                      "violations": st.violations, "rows_per_chunk": s.rows_per_chunk()}))
+    s.close()
 
 
 def run_reference(args, ws):
