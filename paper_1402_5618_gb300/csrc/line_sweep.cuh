@@ -209,11 +209,23 @@ __device__ __forceinline__ void fwd_push_right(Fwd<real> &f, const Row<real> &w,
   f.mu = -w.a * o.mu;
 }
 
+// power of two near 1/m (exact scaling, no division): 2^-(exponent of m)
+__device__ __forceinline__ float pow2_inv(float m) {
+  int e = (__float_as_int(m) >> 23) & 0xff;
+  return (e > 0 && e < 254) ? __int_as_float((254 - e) << 23) : 1.0f;
+}
+__device__ __forceinline__ double pow2_inv(double m) {
+  long long e = (__double_as_longlong(m) >> 52) & 0x7ff;
+  return (e > 0 && e < 2046) ? __longlong_as_double((2046 - e) << 52) : 1.0;
+}
+
+// rescale the map (its projective action is unchanged) so that the largest
+// entry of G lies in [1, 2)
 template <typename real>
 __device__ __forceinline__ void fwd_normalise(Fwd<real> &f) {
   real m = fmax(fmax(fabs(f.g00), fabs(f.g01)), fmax(fabs(f.g10), fabs(f.g11)));
   if (m > real(0)) {
-    real s = real(1) / m;
+    real s = pow2_inv(m);
     f.g00 *= s; f.g01 *= s; f.g10 *= s; f.g11 *= s;
     f.dP *= s; f.dQ *= s; f.mu *= s; f.zP *= s; f.zQ *= s;
   }
@@ -384,10 +396,36 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
     return neg ? -x : x;
   };
 
-  for (int idx = tid; idx < NV * UW; idx += T) {
-    int kv = idx / UW, j = idx % UW;
-    int i = lo - 2 + j;
-    Us[kv * UW + j] = (i < hi + 2) ? cell_val(kv, i) : real(0);
+  bool vec = false;
+  if constexpr (MIXED) {
+    // contiguous line with 16-byte aligned segments: the segment's cells
+    // come in as float4, only the halo and a ragged tail cell by cell
+    vec = cs == 1 && !args.lines && ((lbase + lo) & 3) == 0 && (args.ncell & 3) == 0 &&
+          ((reinterpret_cast<unsigned long long>(args.Uh) & 15) == 0);
+    if (vec) {
+      const int nq = (hi - lo) >> 2;
+      for (int idx = tid; idx < NV * nq; idx += T) {
+        int kv = idx / nq, q = idx - kv * nq;
+        int g = gvar(kv, NV, args.vn, args.vt);
+        float4 x = *reinterpret_cast<const float4 *>(args.Uh + g * args.ncell + lbase + lo + 4 * q);
+        real *d = Us + kv * UW + 2 + 4 * q;
+        d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
+      }
+      const int nr = UW - 4 * nq;
+      for (int idx = tid; idx < NV * nr; idx += T) {
+        int kv = idx / nr, r = idx - kv * nr;
+        int j = r < 2 ? r : 4 * nq + r;
+        int i = lo - 2 + j;
+        Us[kv * UW + j] = (i < hi + 2) ? cell_val(kv, i) : real(0);
+      }
+    }
+  }
+  if (!vec) {
+    for (int idx = tid; idx < NV * UW; idx += T) {
+      int kv = idx / UW, j = idx % UW;
+      int i = lo - 2 + j;
+      Us[kv * UW + j] = (i < hi + 2) ? cell_val(kv, i) : real(0);
+    }
   }
   if (PER) {
     // stencils of the two "position 0" cells (minus: cell 0, plus: cell n-1)
@@ -470,15 +508,46 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
   };
 
   // ------------------------------------------- weights + chunk maps (F1)
+  // the chunk's cells and their two-cell halo come from shared memory once
+  // into registers; weights are stored for the elimination pass (F5) and the
+  // rows built from the registers
   Fwd<real> fm = fwd_identity<real>(), fp = fwd_identity<real>();
-  for (int j = 0; j < len; ++j) weights_of(s0 + j);
-  // each thread reads back only the weights it wrote (no barrier needed)
-  for (int j = 0; j < len; ++j) {
-    real zm, zp;
-    Row<real> rm = row_of(s0 + j, 0, zm);
-    Row<real> rp = row_of(s0 + j, 1, zp);
-    fwd_push_left<real, PER>(fm, rm, zm);
-    fwd_push_right<real, PER>(fp, rp, zp);
+  {
+    real win[M + 4];
+#pragma unroll
+    for (int q = 0; q < M + 4; ++q) win[q] = u[s0 - lo - 2 + q];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      if (j < len) {
+        const int i = s0 + j;
+        real zm = real(0), zp = real(0);
+        Row<real> rm, rp;
+        if (bounded && (i == 0 || i == n - 1)) {
+          weights_of(i);
+          rm = row_of(i, 0, zm);
+          rp = row_of(i, 1, zp);
+        } else {
+          real q0, q1, q2, one, w0, w1, w2, v0, v1, v2;
+          zratios_any(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w, q0, q1, q2, one);
+          zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
+          zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, v0, v1, v2, one);
+          real *o = wt + (i - lo);
+          o[0] = w0;
+          o[SEG] = w2;
+          o[2 * SEG] = v0;
+          o[3 * SEG] = v2;
+          if (PER && (i == 0 || i == n - 1)) {
+            rm = row_of(i, 0, zm);
+            rp = row_of(i, 1, zp);
+          } else {
+            rm = compact_row02(w0, w2, win[j + 1], win[j + 2], win[j + 3]);
+            rp = compact_row02(v0, v2, win[j + 3], win[j + 2], win[j + 1]);
+          }
+        }
+        fwd_push_left<real, PER>(fm, rm, zm);
+        fwd_push_right<real, PER>(fp, rp, zp);
+      }
+    }
   }
   fwd_normalise(fm);
   fwd_normalise(fp);
