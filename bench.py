@@ -97,12 +97,34 @@ def _dist():
     return ws, rank, local
 
 
+def _init_dist(ws: int, local: int):
+    """One process per GPU under torchrun: NCCL when CUDA is present, else
+    gloo (the host-side logic of the replica path runs on CPU that way)."""
+    if ws == 1:
+        return
+    import torch
+    import torch.distributed as dist
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist.init_process_group("gloo")
+
+
+def _close_dist(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def _barrier_max(x: float, ws: int) -> float:
+    """Max of a per-rank scalar over the ranks (the slowest replica's time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -111,6 +133,12 @@ def _barrier(ws: int):
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def replica_value(ws: int, ncell: int, steps: int, ms_max: float) -> float:
+    """Whole-job throughput of N independent replicas: the cell-stages of all
+    ranks over the slowest rank's time (three stages per SSP-RK3 step)."""
+    return ws * ncell * 3 * steps / (ms_max * 1e-3)
 
 
 # Per-kernel algorithmic bytes per cell of a 2-D stage (4 conserved
@@ -263,19 +291,12 @@ def main():
         profile_only(args)
         return
     ws, rank, local = _dist()
-    if ws > 1:
-        import torch
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-
     if args.impl == "reference":
+        # rank 0 alone times the oracle on the host cores; other ranks exit
         if rank == 0:
             run_reference(args, ws)
-        if ws > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
         return
+    _init_dist(ws, local)
 
     out = run_native(args, ws, rank, local)
     ncell = out["ncell"]
@@ -286,8 +307,8 @@ def main():
     e2e = _barrier_max(out["e2e_s"], ws)
     if rank == 0:
         hbm, kind = _peaks()
-        value = ws * ncell * 3 * rm["steps"] / (ms_m * 1e-3)
-        value_fp64 = ws * ncell * 3 * rd["steps"] / (ms_d * 1e-3)
+        value = replica_value(ws, ncell, rm["steps"], ms_m)
+        value_fp64 = replica_value(ws, ncell, rd["steps"], ms_d)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
@@ -306,7 +327,7 @@ def main():
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": _roofline(rm, 1, ncell, hbm, kind),
             "clocks": rm["clk"],
-            "e2e": {"value": ws * ncell * 3 * args.steps / e2e, "unit": UNIT,
+            "e2e": {"value": replica_value(ws, ncell, args.steps, e2e * 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": out["state_bytes"] / args.steps,
                     "d2h_bytes_per_step": out["state_bytes"] / args.steps,
                     "note": "set_state from host, K steps, get_state to host, wall clock"},
@@ -323,9 +344,7 @@ def main():
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline()
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    _close_dist(ws)
 
 
 def profile_only(args):
