@@ -158,6 +158,41 @@ KERNEL_BYTES = {
         ("stage_combine", 32 + 32 * 2.0 / 3.0 + 16 + 16 + 32 + 16)],
 }
 
+# Algorithmic arithmetic per cell of one line sweep (2-D, 4 variables),
+# counted on the scheme's formulas as the FP64 oracle writes them (+, -, *,
+# /, sqrt, |.|, min, max one operation each):
+#   per variable  smoothness indicators 33, WENO-Z weights of both sides 44,
+#                 rows of both compact systems 42, Thomas elimination and
+#                 back substitution of both systems 16                  135
+#   per cell      limiter (the unlimited path) 121, HLLC at one face 118,
+#                 flux difference 8                                     247
+#   x sweep, transposed y sweep: 4 x 135 + 247 = 787; the FP64 y sweep adds
+#   the SSP-RK3 stage combination (20) and the admissibility check (15): 822.
+# The stage combination of the mixed form is a stream (bound by HBM).
+KERNEL_FLOPS = {
+    0: {"x_sweep": 787.0, "y_sweep": 822.0},
+    1: {"x_sweep": 787.0, "y_sweep_transposed": 787.0},
+}
+# ALU peaks from unit counts and clocks: FP32 152 SMs x 128 lanes x 2 flop x
+# 2.07 GHz; FP64 the GB300 nominal 1.25 TFLOP/s.
+ALU_PEAK_TFLOPS = {1: 152 * 128 * 2 * 2.07e9 / 1e12, 0: 1.25}
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per cell of the
+# dominant kernel, from one ncu capture, valid only for the kernel sources it
+# was taken on (their SHA-256 below); any change to them voids it.
+TRAFFIC_PER_CELL = {}          # {(precision, kernel): bytes per cell}
+TRAFFIC_SRC_SHA256 = None
+KERNEL_SOURCES = ("line_sweep.cuh", "physics.cuh", "dfloat.cuh")
+
+
+def _kernel_src_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1402_5618_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
 
 def run_native(args, ws, rank, local):
     import numpy as np
@@ -232,23 +267,56 @@ def run_native(args, ws, rank, local):
 
 
 def _roofline(r, prec, ncell, hbm_peak, peak_kind):
-    """HBM roofline of the kernel with the largest share of the step time:
-    its algorithmic bytes per launch over its mean CUDA-event duration."""
+    """Roofline of the kernel with the largest share of the step time: its
+    algorithmic work per launch over its mean CUDA-event duration (the line
+    sweeps against the ALU peak of their precision, the stage combination
+    against HBM), with the HBM view of every kernel beside it."""
     import numpy as np
     prof = np.array(r["prof"])          # [steps, launches]: dt kernel, then per stage
     kinds = KERNEL_BYTES[prec]
     per = prof[:, 1:].reshape(prof.shape[0], 3, len(kinds))
     tot = per.sum(axis=(0, 1))
+    table = {}
+    for i, (name, per_cell) in enumerate(kinds):
+        t_ms = float(per[:, :, i].mean())
+        gbs = per_cell * ncell / (t_ms * 1e-3) / 1e9
+        row = {"avg_launch_ms": round(t_ms, 4), "share": round(float(tot[i] / prof.sum()), 3),
+               "alg_bytes_per_cell": round(per_cell, 1), "hbm_gbs": round(gbs, 1),
+               "hbm_frac": round(gbs / hbm_peak, 4)}
+        fl = KERNEL_FLOPS[prec].get(name)
+        if fl is not None:
+            tf = fl * ncell / (t_ms * 1e-3) / 1e12
+            row.update(bound="alu", alg_flops_per_cell=fl, tflops=round(tf, 3),
+                       alu_frac=round(tf / ALU_PEAK_TFLOPS[prec], 4))
+        else:
+            row.update(bound="hbm")
+        table[name] = row
     k = int(np.argmax(tot))
-    name, per_cell = kinds[k]
-    t_ms = float(per[:, :, k].mean())
-    achieved = per_cell * ncell / (t_ms * 1e-3) / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
-            "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
-            "peak_source": peak_kind, "alg_bytes_per_cell": round(per_cell, 1),
-            "avg_launch_ms": round(t_ms, 4),
-            "kernel_ms": {kinds[i][0]: round(float(per[:, :, i].mean()), 4) for i in range(len(kinds))},
-            "shares": {kinds[i][0]: round(float(tot[i] / prof.sum()), 3) for i in range(len(kinds))}}
+    name = kinds[k][0]
+    row = table[name]
+    traffic = None
+    tpc = TRAFFIC_PER_CELL.get((prec, name))
+    if tpc is not None and TRAFFIC_SRC_SHA256 == _kernel_src_sha256():
+        traffic = round(tpc * ncell)
+    if row["bound"] == "alu":
+        out = {"kernel": name, "bound": "alu", "achieved": row["tflops"],
+               "peak": round(ALU_PEAK_TFLOPS[prec], 2), "unit": "TFLOP/s",
+               "frac": row["alu_frac"], "traffic": traffic,
+               "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if prec == 1
+                               else "nominal GB300 FP64 1.25 TFLOP/s"),
+               "alg_flops_per_cell": row["alg_flops_per_cell"]}
+    else:
+        out = {"kernel": name, "bound": "hbm", "achieved": row["hbm_gbs"], "peak": hbm_peak,
+               "unit": "GB/s", "frac": row["hbm_frac"], "traffic": traffic,
+               "peak_source": peak_kind}
+    out.update(avg_launch_ms=row["avg_launch_ms"],
+               hbm={"achieved": row["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": row["hbm_frac"], "alg_bytes_per_cell": row["alg_bytes_per_cell"],
+                    "peak_source": peak_kind},
+               kernels=table,
+               kernel_ms={n: table[n]["avg_launch_ms"] for n in table},
+               shares={n: table[n]["share"] for n in table})
+    return out
 
 
 def _cpu_baseline(seconds_target: float = 20.0):

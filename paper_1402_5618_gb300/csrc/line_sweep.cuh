@@ -70,6 +70,7 @@ struct ProbDesc {
   long long off, ncell;
   int nx, ny;
   double dx, dy;
+  double idx, idy;    // 1/dx, 1/dy
   int bc[4];
 };
 
@@ -96,6 +97,7 @@ struct SweepArgs {
   int vn, vt;         // grid index of the normal / tangential momentum (vt < 0 in 1-D)
   int bclo, bchi;
   double h, h_other;  // cell size along the line / across (0 in 1-D)
+  double ih;          // 1 / h (from the host: no FP64 division per thread)
   double gamma, wgl, eps_weno;
   int stage;          // 0, 1, 2
   double eps_fixed;   // > 0: fixed limiter epsilon, no control-block checks (operator evaluation)
@@ -121,11 +123,11 @@ __device__ __forceinline__ void bind_line(SweepArgs &a, long long &line) {
   if (a.xdir) {
     a.n = pd.nx; a.cell_stride = 1; a.line_stride = pd.nx;
     a.bclo = pd.bc[0]; a.bchi = pd.bc[1];
-    a.h = pd.dx; a.h_other = NV == 4 ? pd.dy : 0.0;
+    a.h = pd.dx; a.h_other = NV == 4 ? pd.dy : 0.0; a.ih = pd.idx;
   } else {
     a.n = pd.ny; a.cell_stride = pd.nx; a.line_stride = 1;
     a.bclo = pd.bc[2]; a.bchi = pd.bc[3];
-    a.h = pd.dy; a.h_other = pd.dx;
+    a.h = pd.dy; a.h_other = pd.dx; a.ih = pd.idy;
   }
   const long long o = pd.off;
   if (a.U) a.U += o;
@@ -245,14 +247,18 @@ __device__ __forceinline__ void fwd_apply(const Fwd<real> &f, real &cp, real &dp
 }
 
 template <typename real>
-__device__ __forceinline__ real shfl_up_r(real v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ real shfl_up_r(real v, int d, int width = 32) {
+  return __shfl_up_sync(0xffffffffu, v, d, width);
+}
 template <typename real>
-__device__ __forceinline__ real shfl_down_r(real v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ real shfl_down_r(real v, int d, int width = 32) {
+  return __shfl_down_sync(0xffffffffu, v, d, width);
+}
 
 template <typename real, bool PER, bool UP>
-__device__ __forceinline__ Fwd<real> fwd_shfl(const Fwd<real> &f, int d) {
+__device__ __forceinline__ Fwd<real> fwd_shfl(const Fwd<real> &f, int d, int width = 32) {
   Fwd<real> o;
-#define PPK_SH(x) o.x = UP ? shfl_up_r(f.x, d) : shfl_down_r(f.x, d)
+#define PPK_SH(x) o.x = UP ? shfl_up_r(f.x, d, width) : shfl_down_r(f.x, d, width)
   PPK_SH(g00); PPK_SH(g01); PPK_SH(g10); PPK_SH(g11); PPK_SH(dP); PPK_SH(dQ); PPK_SH(mu);
   if (PER) { PPK_SH(zP); PPK_SH(zQ); } else { o.zP = real(0); o.zQ = real(0); }
 #undef PPK_SH
@@ -276,6 +282,104 @@ __device__ __forceinline__ Bwd<real> bwd_compose(const Bwd<real> &X, const Bwd<r
   return r;
 }
 
+// split cluster barrier: arrive (release this CTA's shared-memory writes to
+// the cluster) and wait (acquire the other CTAs'), with independent work
+// between the two halves
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive_relaxed() {   // publishes no data
+  asm volatile("barrier.cluster.arrive.relaxed;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------- pairs
+// The mixed form advances the minus (.x) and plus (.y) systems together with
+// paired FP32 instructions (one instruction, two lanes' worth of FP32 work;
+// each component rounds as the scalar fused multiply-add does).
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 p_set(float a) { return make_float2(a, a); }
+
+// forward maps of both systems
+struct Fwd2 {
+  float2 g00, g01, g10, g11, dP, dQ, mu, zP, zQ;
+};
+
+__device__ __forceinline__ Fwd2 fwd2_pack(const Fwd<float> &m, const Fwd<float> &p) {
+  Fwd2 f;
+  f.g00 = make_float2(m.g00, p.g00); f.g01 = make_float2(m.g01, p.g01);
+  f.g10 = make_float2(m.g10, p.g10); f.g11 = make_float2(m.g11, p.g11);
+  f.dP = make_float2(m.dP, p.dP); f.dQ = make_float2(m.dQ, p.dQ);
+  f.mu = make_float2(m.mu, p.mu); f.zP = make_float2(m.zP, p.zP); f.zQ = make_float2(m.zQ, p.zQ);
+  return f;
+}
+
+__device__ __forceinline__ void fwd2_unpack(const Fwd2 &f, Fwd<float> &m, Fwd<float> &p) {
+  m.g00 = f.g00.x; m.g01 = f.g01.x; m.g10 = f.g10.x; m.g11 = f.g11.x;
+  m.dP = f.dP.x; m.dQ = f.dQ.x; m.mu = f.mu.x; m.zP = f.zP.x; m.zQ = f.zQ.x;
+  p.g00 = f.g00.y; p.g01 = f.g01.y; p.g10 = f.g10.y; p.g11 = f.g11.y;
+  p.dP = f.dP.y; p.dQ = f.dQ.y; p.mu = f.mu.y; p.zP = f.zP.y; p.zQ = f.zQ.y;
+}
+
+// Y o X (X first), both systems
+template <bool PER>
+__device__ __forceinline__ Fwd2 fwd2_compose(const Fwd2 &Y, const Fwd2 &X) {
+  Fwd2 f;
+  f.g00 = p_fma(Y.g01, X.g10, p_mul(Y.g00, X.g00));
+  f.g01 = p_fma(Y.g01, X.g11, p_mul(Y.g00, X.g01));
+  f.g10 = p_fma(Y.g11, X.g10, p_mul(Y.g10, X.g00));
+  f.g11 = p_fma(Y.g11, X.g11, p_mul(Y.g10, X.g01));
+  f.dP = p_fma(Y.mu, X.dP, p_fma(Y.dQ, X.g10, p_mul(Y.dP, X.g00)));
+  f.dQ = p_fma(Y.mu, X.dQ, p_fma(Y.dQ, X.g11, p_mul(Y.dP, X.g01)));
+  f.mu = p_mul(Y.mu, X.mu);
+  if (PER) {
+    f.zP = p_fma(Y.mu, X.zP, p_fma(Y.zQ, X.g10, p_mul(Y.zP, X.g00)));
+    f.zQ = p_fma(Y.mu, X.zQ, p_fma(Y.zQ, X.g11, p_mul(Y.zP, X.g01)));
+  } else {
+    f.zP = p_set(0.0f); f.zQ = p_set(0.0f);
+  }
+  return f;
+}
+
+__device__ __forceinline__ void fwd2_normalise(Fwd2 &f) {
+  float mx = fmaxf(fmaxf(fabsf(f.g00.x), fabsf(f.g01.x)), fmaxf(fabsf(f.g10.x), fabsf(f.g11.x)));
+  float my = fmaxf(fmaxf(fabsf(f.g00.y), fabsf(f.g01.y)), fmaxf(fabsf(f.g10.y), fabsf(f.g11.y)));
+  const float2 sc = make_float2(pow2_inv(mx), pow2_inv(my));   // 1 for 0, inf, nan
+  f.g00 = p_mul(f.g00, sc); f.g01 = p_mul(f.g01, sc); f.g10 = p_mul(f.g10, sc);
+  f.g11 = p_mul(f.g11, sc); f.dP = p_mul(f.dP, sc); f.dQ = p_mul(f.dQ, sc);
+  f.mu = p_mul(f.mu, sc); f.zP = p_mul(f.zP, sc); f.zQ = p_mul(f.zQ, sc);
+}
+
+// back-substitution maps of both systems
+struct Bwd2 {
+  float2 A, B, Az;
+};
+
+__device__ __forceinline__ Bwd2 bwd2_compose(const Bwd2 &X, const Bwd2 &Y) {
+  Bwd2 r;
+  r.A = p_fma(X.B, Y.A, X.A);
+  r.Az = p_fma(X.B, Y.Az, X.Az);
+  r.B = p_mul(X.B, Y.B);
+  return r;
+}
+
+// the compact row of both systems from their (w0, w2) and neighbour averages
+__device__ __forceinline__ void row2(float2 w0, float2 w2, float2 up, float2 u0, float2 un,
+                                     float2 &a, float2 &b, float2 &c, float2 &r) {
+  const float2 th = p_set(1.0f / 3.0f), sx = p_set(1.0f / 6.0f);
+  a = p_mul(p_add(p_set(1.0f), p_add(w0, p_neg(w2))), th);
+  b = p_mul(p_add(p_set(2.0f), p_neg(w0)), th);
+  c = p_mul(w2, th);
+  const float2 k0 = p_fma(p_set(-4.0f), w2, p_set(5.0f));                 // 5 - 4 w2
+  const float2 k1 = p_fma(p_set(4.0f), w2, p_add(p_set(1.0f), p_neg(w0)));  // 1 - w0 + 4 w2
+  r = p_mul(p_fma(k1, un, p_fma(k0, u0, p_mul(w0, up))), sx);
+}
+
 // ---------------------------------------------------------------- smem
 template <typename real, int NV, int WPV>
 struct Exch {
@@ -288,16 +392,27 @@ struct Exch {
   double sm[NV][2][6];           // y_f, z_f, y_l, z_l, -a0/b0 (periodic)
 };
 
+// Segment planes in shared memory carry one pad word per 128 bytes: segment
+// cell c (c >= -2) sits at pad(c) = c + (c >> PSH) of its plane.  Lanes of a
+// warp then hit distinct banks both when each lane walks its own chunk of M
+// cells (lane stride M) and when consecutive lanes take consecutive cells;
+// a chunk (M divides 128 bytes) never straddles a pad word.
 template <typename real, int NV, int M>
 struct Smem {
   static constexpr int KC = SEGC / M;     // chunks per conserved variable
   static constexpr int WPV = KC / 32;     // warps per conserved variable
   static constexpr int SEG = SEGC;
-  static constexpr size_t u_off = 0;                                    // real Us[NV][SEG+4]
-  static constexpr size_t w_off = u_off + sizeof(real) * NV * (SEG + 4); // real Wt[NV][4][SEG]
-  static constexpr size_t fm_off = w_off + sizeof(real) * NV * 4 * SEG;
-  static constexpr size_t fp_off = fm_off + sizeof(real) * NV * SEG;    // real Fm, Fp[NV][SEG]
-  static constexpr size_t fl_off = fp_off + sizeof(real) * NV * SEG;    // real Fl[NV][SEG+2]
+  static constexpr int PSH = sizeof(real) == 4 ? 5 : 4;
+  __host__ __device__ static constexpr int pad(int c) { return c + (c >> PSH); }
+  static constexpr int UH = 3;                         // pad(-2) = -3
+  static constexpr int UWP = UH + pad(SEG + 1) + 1;    // cells -2 .. SEG+1
+  static constexpr int WP = pad(SEG - 1) + 1;          // cells 0 .. SEG-1
+  static_assert(((32 * 4 / (int)sizeof(real)) % M) == 0, "a chunk must not straddle a pad word");
+  static constexpr size_t u_off = 0;                                     // real Us[NV][UWP]
+  static constexpr size_t w_off = u_off + sizeof(real) * NV * UWP;       // real Wt[NV][4][WP]
+  static constexpr size_t fm_off = w_off + sizeof(real) * NV * 4 * WP;
+  static constexpr size_t fp_off = fm_off + sizeof(real) * NV * WP;      // real Fm, Fp[NV][WP]
+  static constexpr size_t fl_off = fp_off + sizeof(real) * NV * WP;      // real Fl[NV][SEG+2]
   static constexpr size_t rm_off = fl_off + sizeof(real) * NV * (SEG + 2);  // remote stencils
   static constexpr size_t ex_off = (rm_off + sizeof(real) * NV * 2 * 6 + 15) / 16 * 16;
   static constexpr size_t bytes = ex_off + sizeof(Exch<real, NV, WPV>);
@@ -316,9 +431,16 @@ __device__ __forceinline__ double bits_double(unsigned long long b) {
 }
 
 // ---------------------------------------------------------------- kernel
-// the mixed form asks for two resident CTAs per SM (128 registers at M = 8)
+// Resident CTAs per SM the kernel is compiled for: the mixed form is bound by
+// latency, so it asks for three at M = 8 (85 registers a thread; the shared
+// memory of three segments fits) and two at M = 16; the FP64 form is bound by
+// the FP64 pipe and its shared memory allows one.
+#ifndef PPK_MIXED_CTAS_M8
+#define PPK_MIXED_CTAS_M8 3
+#endif
 template <typename real, int NV, int M, bool PER, int MODE>
-__global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(NV * (SEGC / M),
+                                  sizeof(real) == 4 ? (M == 8 ? PPK_MIXED_CTAS_M8 : 2) : 1)
     line_sweep(SweepArgs args_in) {
   constexpr bool MIXED = sizeof(real) == 4;
   using S = Smem<real, NV, M>;
@@ -326,7 +448,8 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
   constexpr int KC = S::KC;
   constexpr int WPV = S::WPV;
   constexpr int T = NV * KC;
-  constexpr int UW = SEG + 4;
+  constexpr int UW = SEG + 4;            // cells -2 .. SEG+1
+  constexpr int UH = S::UH, UWP = S::UWP, WP = S::WP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real *Us = reinterpret_cast<real *>(smem_raw + S::u_off);
   real *Wt = reinterpret_cast<real *>(smem_raw + S::w_off);
@@ -408,7 +531,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
         int kv = idx / nq, q = idx - kv * nq;
         int g = gvar(kv, NV, args.vn, args.vt);
         float4 x = *reinterpret_cast<const float4 *>(args.Uh + g * args.ncell + lbase + lo + 4 * q);
-        real *d = Us + kv * UW + 2 + 4 * q;
+        real *d = Us + kv * UWP + UH + S::pad(4 * q);
         d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
       }
       const int nr = UW - 4 * nq;
@@ -416,7 +539,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
         int kv = idx / nr, r = idx - kv * nr;
         int j = r < 2 ? r : 4 * nq + r;
         int i = lo - 2 + j;
-        Us[kv * UW + j] = (i < hi + 2) ? cell_val(kv, i) : real(0);
+        Us[kv * UWP + UH + S::pad(j - 2)] = (i < hi + 2) ? cell_val(kv, i) : real(0);
       }
     }
   }
@@ -424,7 +547,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
     for (int idx = tid; idx < NV * UW; idx += T) {
       int kv = idx / UW, j = idx % UW;
       int i = lo - 2 + j;
-      Us[kv * UW + j] = (i < hi + 2) ? cell_val(kv, i) : real(0);
+      Us[kv * UWP + UH + S::pad(j - 2)] = (i < hi + 2) ? cell_val(kv, i) : real(0);
     }
   }
   if (PER) {
@@ -439,29 +562,22 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
   __syncthreads();
 
   // ---------------------------------------------------------------- rows
-  const real *u = Us + v * UW + 2;            // u[i - lo], valid i - lo in [-2, hi-lo+2)
-  real *wt = Wt + v * 4 * SEG;                // wt[q*SEG + c]: w0-, w2-, w0+, w2+
+  const real *uv = Us + v * UWP + UH;         // u of segment cell c at uv[pad(c)], c in [-2, SEG+2)
+  real *wt = Wt + v * 4 * WP;                 // wt[q*WP + pad(c)]: w0-, w2-, w0+, w2+
   const int s0 = lo + k * M;                  // first cell of this thread's chunk
   const int len = max(0, min(M, hi - s0));
+  const int cb = S::pad(k * M);               // padded offset of the chunk's first cell
   const bool bounded = !PER;
+  auto u_at = [&](int i) -> real { return uv[S::pad(i - lo)]; };
 
-  // weights of cell i for both sides (stored), or the closure values
-  auto weights_of = [&](int i) {
-    const real *x = u + (i - lo);
-    real *o = wt + (i - lo);
-    if (bounded && (i == 0 || i == n - 1)) {
-      o[0] = weno5z_face(x[-2], x[-1], x[0], x[1], x[2], eps_w);
-      o[2 * SEG] = weno5z_face(x[2], x[1], x[0], x[-1], x[-2], eps_w);
-      return;
-    }
-    real q0, q1, q2, one, w0, w1, w2;
-    zratios_any(x[-2], x[-1], x[0], x[1], x[2], eps_w, q0, q1, q2, one);
-    zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
-    o[0] = w0;
-    o[SEG] = w2;
-    zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, w0, w1, w2, one);
-    o[2 * SEG] = w0;
-    o[3 * SEG] = w2;
+  // the chunk's cells with a two-cell halo, from shared memory into registers
+  auto load_window = [&](real *win) {
+    win[0] = uv[S::pad(k * M - 2)];
+    win[1] = uv[S::pad(k * M - 1)];
+#pragma unroll
+    for (int q = 0; q < M; ++q) win[q + 2] = uv[cb + q];
+    win[M + 2] = uv[S::pad(k * M + M)];
+    win[M + 3] = uv[S::pad(k * M + M + 1)];
   };
 
   // a, b of the unmodified position-0 row of side 0 (cell 0) or 1 (cell n-1),
@@ -477,45 +593,37 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
     b0 = r.b;
   };
 
-  // row of cell i, side 0 (minus: prev = i-1) or 1 (plus: prev = i+1), from
-  // the stored weights; zr = the Sherman-Morrison right-hand side entry
-  auto row_of = [&](int i, int side, real &zr) -> Row<real> {
-    const real *x = u + (i - lo);
-    const real *o = wt + (i - lo) + 2 * side * SEG;
-    Row<real> r;
+  // row of the periodic end cell i (0 or n-1), side 0 (minus) or 1 (plus),
+  // from the stored weights; zr = the Sherman-Morrison right-hand side entry
+  auto per_row = [&](int i, int side, real &zr) -> Row<real> {
+    const real *o = wt + 2 * side * WP + S::pad(i - lo);
+    const real xm = u_at(i - 1), x0 = u_at(i), xp = u_at(i + 1);
+    Row<real> r = side == 0 ? compact_row02(o[0], o[WP], xm, x0, xp)
+                            : compact_row02(o[0], o[WP], xp, x0, xm);
+    const int first = side == 0 ? 0 : n - 1, last = side == 0 ? n - 1 : 0;
     zr = real(0);
-    if (bounded && (i == 0 || i == n - 1)) {
-      r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
-      return r;
-    }
-    if (side == 0) r = compact_row02(o[0], o[SEG], x[-1], x[0], x[1]);
-    else r = compact_row02(o[0], o[SEG], x[1], x[0], x[-1]);
-    if (PER) {
-      const int first = side == 0 ? 0 : n - 1, last = side == 0 ? n - 1 : 0;
-      if (i == first) {          // T = A - u v^T with g = -b at position 0
-        zr = -r.b;
-        r.b = r.b + r.b;
-        r.a = real(0);
-      } else if (i == last) {    // corner removed, b reduced by c a0 / g
-        real a0, b0;
-        far_row(side, a0, b0);
-        zr = r.c;
-        r.b = r.b + r.c * a0 / b0;
-        r.c = real(0);
-      }
+    if (i == first) {          // T = A - u v^T with g = -b at position 0
+      zr = -r.b;
+      r.b = r.b + r.b;
+      r.a = real(0);
+    } else if (i == last) {    // corner removed, b reduced by c a0 / g
+      real a0, b0;
+      far_row(side, a0, b0);
+      zr = r.c;
+      r.b = r.b + r.c * a0 / b0;
+      r.c = real(0);
     }
     return r;
   };
 
   // ------------------------------------------- weights + chunk maps (F1)
-  // the chunk's cells and their two-cell halo come from shared memory once
-  // into registers; weights are stored for the elimination pass (F5) and the
-  // rows built from the registers
+  // weights are stored for the elimination pass (F5); the rows come from the
+  // register window.  The bounded closure cells store their explicit
+  // WENO5-Z face values in the w0 slots instead (rows 0 x + 1 x + 0 x = f).
   Fwd<real> fm = fwd_identity<real>(), fp = fwd_identity<real>();
   {
     real win[M + 4];
-#pragma unroll
-    for (int q = 0; q < M + 4; ++q) win[q] = u[s0 - lo - 2 + q];
+    load_window(win);
 #pragma unroll
     for (int j = 0; j < M; ++j) {
       if (j < len) {
@@ -523,22 +631,24 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
         real zm = real(0), zp = real(0);
         Row<real> rm, rp;
         if (bounded && (i == 0 || i == n - 1)) {
-          weights_of(i);
-          rm = row_of(i, 0, zm);
-          rp = row_of(i, 1, zp);
+          real fmv = weno5z_face(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w);
+          real fpv = weno5z_face(win[j + 4], win[j + 3], win[j + 2], win[j + 1], win[j], eps_w);
+          wt[cb + j] = fmv;
+          wt[2 * WP + cb + j] = fpv;
+          rm.a = real(0); rm.b = real(1); rm.c = real(0); rm.r = fmv;
+          rp.a = real(0); rp.b = real(1); rp.c = real(0); rp.r = fpv;
         } else {
           real q0, q1, q2, one, w0, w1, w2, v0, v1, v2;
           zratios_any(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w, q0, q1, q2, one);
           zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
           zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, v0, v1, v2, one);
-          real *o = wt + (i - lo);
-          o[0] = w0;
-          o[SEG] = w2;
-          o[2 * SEG] = v0;
-          o[3 * SEG] = v2;
+          wt[cb + j] = w0;
+          wt[WP + cb + j] = w2;
+          wt[2 * WP + cb + j] = v0;
+          wt[3 * WP + cb + j] = v2;
           if (PER && (i == 0 || i == n - 1)) {
-            rm = row_of(i, 0, zm);
-            rp = row_of(i, 1, zp);
+            rm = per_row(i, 0, zm);
+            rp = per_row(i, 1, zp);
           } else {
             rm = compact_row02(w0, w2, win[j + 1], win[j + 2], win[j + 3]);
             rp = compact_row02(v0, v2, win[j + 3], win[j + 2], win[j + 1]);
@@ -553,17 +663,39 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
   fwd_normalise(fp);
 
   // ------------------------------------------- warp inclusive scans (F2)
+  // minus maps accumulate from the lower lanes, plus maps from the higher
+  if constexpr (MIXED) {
+    Fwd2 f2 = fwd2_pack(fm, fp);
+    const float2 one2 = p_set(1.0f), zero2 = p_set(0.0f);
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    Fwd<real> o = fwd_shfl<real, PER, true>(fm, d);
-    if (lane >= d) { fm = fwd_compose<real, PER>(fm, o); fwd_normalise(fm); }
-    Fwd<real> q = fwd_shfl<real, PER, false>(fp, d);
-    if (lane + d < 32) { fp = fwd_compose<real, PER>(fp, q); fwd_normalise(fp); }
+    for (int d = 1; d < 32; d <<= 1) {
+      const bool am = lane >= d, ap = lane + d < 32;
+      Fwd2 o;
+      // every lane executes both shuffles; the select comes after
+#define PPK_SH2(fld, idv)                                                    \
+  {                                                                          \
+    const float tm_ = __shfl_up_sync(0xffffffffu, f2.fld.x, d);              \
+    const float tp_ = __shfl_down_sync(0xffffffffu, f2.fld.y, d);            \
+    o.fld.x = am ? tm_ : idv.x;                                              \
+    o.fld.y = ap ? tp_ : idv.y;                                              \
   }
-  Fwd<real> fm_ex = fwd_shfl<real, PER, true>(fm, 1);
-  if (lane == 0) fm_ex = fwd_identity<real>();
-  Fwd<real> fp_ex = fwd_shfl<real, PER, false>(fp, 1);
-  if (lane == 31) fp_ex = fwd_identity<real>();
+      PPK_SH2(g00, one2); PPK_SH2(g01, zero2); PPK_SH2(g10, zero2); PPK_SH2(g11, one2);
+      PPK_SH2(dP, zero2); PPK_SH2(dQ, zero2); PPK_SH2(mu, one2);
+      if (PER) { PPK_SH2(zP, zero2); PPK_SH2(zQ, zero2); } else { o.zP = zero2; o.zQ = zero2; }
+#undef PPK_SH2
+      f2 = fwd2_compose<PER>(f2, o);   // with the identity where a lane has no partner
+      fwd2_normalise(f2);
+    }
+    fwd2_unpack(f2, fm, fp);
+  } else {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      Fwd<real> o = fwd_shfl<real, PER, true>(fm, d);
+      if (lane >= d) { fm = fwd_compose<real, PER>(fm, o); fwd_normalise(fm); }
+      Fwd<real> q = fwd_shfl<real, PER, false>(fp, d);
+      if (lane + d < 32) { fp = fwd_compose<real, PER>(fp, q); fwd_normalise(fp); }
+    }
+  }
   if (lane == 31) ex.warp_fwd[v][0][w] = fm;
   if (lane == 0) ex.warp_fwd[v][1][w] = fp;
   __syncthreads();
@@ -582,70 +714,229 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
   cluster.sync();
 
   // ------------------------------------------- incoming states (F4)
-  if (tid < 2 * NV) {
-    int vv = tid >> 1, sd = tid & 1;
-    real cp = real(0), dp = real(0), zp = real(0);
-    if (sd == 0) {
-      for (int q = 0; q < rank; ++q) {
+  // The segment maps of the CTAs ahead of this one on each side (minus: the
+  // lower ranks, applied in rank order; plus: the higher ranks, from the
+  // last one down) applied to the zero state that enters a line end.
+  // Mixed form (latency bound): composed by a tree over 16 lanes, lane q
+  // holding rank q's map (the identity where rank q is not ahead), so the
+  // remote reads happen at once.  FP64 form (bound by the FP64 pipe): one
+  // thread per side and variable applies them in turn, the fewest FP64
+  // operations.
+  real cin = real(0), din = real(0), zin = real(0);
+  int fvv = -1, fsd = 0;
+  if constexpr (MIXED) {
+    if (tid < 2 * NV * 16) {   // whole warps: T >= 2 NV 16 for M <= 16
+      const int grp = tid >> 4, q = tid & 15;
+      const int vv = grp >> 1, sd = grp & 1;
+      Fwd<real> mq = fwd_identity<real>();
+      if (q < R && (sd == 0 ? q < rank : q > rank)) {
         Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
-        fwd_apply<real, PER>(rx->seg_fwd[vv][0], cp, dp, zp);
+        mq = rx->seg_fwd[vv][sd];
       }
-    } else {
-      for (int q = R - 1; q > rank; --q) {
-        Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
-        fwd_apply<real, PER>(rx->seg_fwd[vv][1], cp, dp, zp);
+#pragma unroll
+      for (int d = 1; d < 16; d <<= 1) {
+        Fwd<real> o = fwd_shfl<real, PER, false>(mq, d, 16);   // ranks q + d ...
+        if ((q & (2 * d - 1)) == 0) {
+          mq = sd == 0 ? fwd_compose<real, PER>(o, mq) : fwd_compose<real, PER>(mq, o);
+          fwd_normalise(mq);
+        }
+      }
+      if (q == 0) {
+        fwd_apply<real, PER>(mq, cin, din, zin);
+        fvv = vv;
+        fsd = sd;
       }
     }
+  } else {
+    if (tid < 2 * NV) {
+      const int vv = tid >> 1, sd = tid & 1;
+      if (sd == 0) {
+        for (int q = 0; q < rank; ++q) {
+          Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
+          fwd_apply<real, PER>(rx->seg_fwd[vv][0], cin, din, zin);
+        }
+      } else {
+        for (int q = R - 1; q > rank; --q) {
+          Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
+          fwd_apply<real, PER>(rx->seg_fwd[vv][1], cin, din, zin);
+        }
+      }
+      fvv = vv;
+      fsd = sd;
+    }
+  }
+  if (fvv >= 0) {   // the state entering each warp of this segment
     for (int ww = 0; ww < WPV; ++ww) {
-      int wi = sd == 0 ? ww : WPV - 1 - ww;
-      ex.warp_in[vv][sd][wi][0] = cp;
-      ex.warp_in[vv][sd][wi][1] = dp;
-      ex.warp_in[vv][sd][wi][2] = zp;
-      fwd_apply<real, PER>(ex.warp_fwd[vv][sd][wi], cp, dp, zp);
+      int wi = fsd == 0 ? ww : WPV - 1 - ww;
+      ex.warp_in[fvv][fsd][wi][0] = cin;
+      ex.warp_in[fvv][fsd][wi][1] = din;
+      ex.warp_in[fvv][fsd][wi][2] = zin;
+      fwd_apply<real, PER>(ex.warp_fwd[fvv][fsd][wi], cin, din, zin);
     }
   }
   __syncthreads();
 
-  real cpm = ex.warp_in[v][0][w][0], dpm = ex.warp_in[v][0][w][1], zpm = ex.warp_in[v][0][w][2];
-  fwd_apply<real, PER>(fm_ex, cpm, dpm, zpm);
-  real cpp = ex.warp_in[v][1][w][0], dpp = ex.warp_in[v][1][w][1], zpp = ex.warp_in[v][1][w][2];
-  fwd_apply<real, PER>(fp_ex, cpp, dpp, zpp);
+  // the state after each lane's chunk (its inclusive map applied to the
+  // warp's incoming state), handed to the next lane in elimination order
+  real cpm, dpm, zpm, cpp, dpp, zpp;
+  {
+    const real cw = ex.warp_in[v][0][w][0], dw = ex.warp_in[v][0][w][1], zw = ex.warp_in[v][0][w][2];
+    real c = cw, d = dw, z = zw;
+    fwd_apply<real, PER>(fm, c, d, z);
+    cpm = shfl_up_r(c, 1);
+    dpm = shfl_up_r(d, 1);
+    zpm = PER ? shfl_up_r(z, 1) : real(0);
+    if (lane == 0) { cpm = cw; dpm = dw; zpm = zw; }
+  }
+  {
+    const real cw = ex.warp_in[v][1][w][0], dw = ex.warp_in[v][1][w][1], zw = ex.warp_in[v][1][w][2];
+    real c = cw, d = dw, z = zw;
+    fwd_apply<real, PER>(fp, c, d, z);
+    cpp = shfl_down_r(c, 1);
+    dpp = shfl_down_r(d, 1);
+    zpp = PER ? shfl_down_r(z, 1) : real(0);
+    if (lane == 31) { cpp = cw; dpp = dw; zpp = zw; }
+  }
 
   // ------------------------------------------- chunk elimination (F5)
-  // Thomas elimination of the chunk from the incoming state, keeping c', d'
-  // (and z') per row for the back substitution, and the chunk's back
-  // substitution map x_first = A + B x_after accumulated in the same pass:
-  // A = sum_j (prod_{l<j} -c'_l) d'_j, B = prod_l -c'_l.
-  // minus: position j <-> cell s0 + j; plus: position j <-> cell s0+len-1-j.
-  real cmv[M], dmv[M], zmv[M], cpv[M], dpv[M], zpv[M];
+  // Thomas elimination of the chunk from the incoming state, and the chunk's
+  // back-substitution map x_first = A + B x_after accumulated in the same
+  // pass: A = sum_j (prod_{l<j} -c'_l) d'_j, B = prod_l -c'_l.  The minus
+  // system runs over the chunk's cells left to right, the plus system right
+  // to left.  c', d' of a cell overwrite its two weights (read just before by
+  // the same thread); z' stays in registers (periodic lines).
+  // Mixed form: the recurrence runs on the projective state (P, Q, D, Z),
+  // c' = P/Q, d' = D/Q, z' = Z/Q, mapped linearly by a row (P <- c Q,
+  // Q <- b Q - a P, D <- r Q - a D), so consecutive rows depend on each other
+  // through two multiply-adds and the reciprocals 1/Q are off that chain
+  // (over one chunk Q changes by at most M factors b - a c': no rescaling).
+  // FP64 form: the plain recurrence with one division per row, the fewest
+  // FP64 operations.
+  real zmv[PER ? M : 1], zpv[PER ? M : 1];
   Bwd<real> bm, bp;
-  {
-    // the two sides' recurrences are independent: advance them together
+  // a full chunk without a line-end cell: every row is a plain compact row
+  const bool plain = len == M && s0 > 0 && s0 + M < n;
+  bool done5 = false;
+  if constexpr (MIXED) {
+    if (plain) {   // both systems together in paired FP32, no guards
+      float win[M + 4];
+      load_window(win);
+      float *om = wt + cb, *op = wt + 2 * WP + cb;
+      float2 P = make_float2(cpm, cpp), Q = p_set(1.0f), D = make_float2(dpm, dpp);
+      float2 Z = make_float2(zpm, zpp);
+      float2 pi = p_set(1.0f), A = p_set(0.0f), Az = p_set(0.0f);
+#pragma unroll
+      for (int jj = 0; jj < M; ++jj) {
+        const int jm = jj, jp = M - 1 - jj;    // minus left to right, plus right to left
+        float2 a, b, c, r;
+        row2(make_float2(om[jm], op[jp]), make_float2(om[WP + jm], op[WP + jp]),
+             make_float2(win[jm + 1], win[jp + 3]), make_float2(win[jm + 2], win[jp + 2]),
+             make_float2(win[jm + 3], win[jp + 1]), a, b, c, r);
+        const float2 na = p_neg(a);
+        const float2 nq = p_fma(na, P, p_mul(b, Q));
+        D = p_fma(na, D, p_mul(r, Q));
+        if (PER) Z = p_mul(na, Z);            // zero right-hand side away from the ends
+        P = p_mul(c, Q);
+        Q = nq;
+        const float2 iq = make_float2(1.0f / Q.x, 1.0f / Q.y);
+        const float2 co = p_mul(P, iq), dd = p_mul(D, iq);
+        om[jm] = co.x;
+        om[WP + jm] = dd.x;
+        op[jp] = co.y;
+        op[WP + jp] = dd.y;
+        A = p_fma(pi, dd, A);
+        if (PER) {
+          const float2 zz = p_mul(Z, iq);
+          zmv[jm] = zz.x;
+          zpv[jp] = zz.y;
+          Az = p_fma(pi, zz, Az);
+        }
+        pi = p_mul(pi, p_neg(co));
+      }
+      bm.A = A.x; bm.Az = Az.x; bm.B = pi.x;
+      bp.A = A.y; bp.Az = Az.y; bp.B = pi.y;
+      done5 = true;
+    }
+  }
+  if (!done5) {
+    real win[M + 4];
+    load_window(win);
+    // projective state (mixed) or (c', -, d', z') (FP64) of each side
+    real Pm = cpm, Qm = real(1), Dm = dpm, Zm = zpm;
+    real Pp = cpp, Qp = real(1), Dp = dpp, Zp = zpp;
     real pim = real(1), Am = real(0), Azm = real(0);
     real pip = real(1), Ap = real(0), Azp = real(0);
+    auto elim = [&](const Row<real> &r, real zr, real &P, real &Qs, real &D, real &Z,
+                    real &co, real &dout, real &zo) {
+      if constexpr (MIXED) {
+        real nq = r.b * Qs - r.a * P;
+        D = r.r * Qs - r.a * D;
+        if (PER) Z = zr * Qs - r.a * Z;
+        P = r.c * Qs;
+        Qs = nq;
+        real iq = real(1) / Qs;
+        co = P * iq;
+        dout = D * iq;
+        zo = PER ? Z * iq : real(0);
+      } else {
+        real ip = real(1) / (r.b - r.a * P);
+        D = (r.r - r.a * D) * ip;
+        if (PER) Z = (zr - r.a * Z) * ip;
+        P = r.c * ip;
+        co = P;
+        dout = D;
+        zo = Z;
+      }
+    };
 #pragma unroll
-    for (int j = 0; j < M; ++j) {
-      if (j < len) {
-        real zrm, zrp;
-        Row<real> rm = row_of(s0 + j, 0, zrm);
-        Row<real> rp = row_of(s0 + len - 1 - j, 1, zrp);
-        real ipm = real(1) / (rm.b - rm.a * cpm);
-        real ipp = real(1) / (rp.b - rp.a * cpp);
-        cpm = rm.c * ipm;
-        cpp = rp.c * ipp;
-        dpm = (rm.r - rm.a * dpm) * ipm;
-        dpp = (rp.r - rp.a * dpp) * ipp;
-        if (PER) {
-          zpm = (zrm - rm.a * zpm) * ipm;
-          zpp = (zrp - rp.a * zpp) * ipp;
+    for (int jj = 0; jj < M; ++jj) {
+      {   // minus: cell s0 + jj
+        const int j = jj;
+        if (j < len) {
+          const int i = s0 + j;
+          real *o = wt + cb + j;
+          Row<real> r;
+          real zr = real(0);
+          if (bounded && (i == 0 || i == n - 1)) {
+            r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
+          } else if (PER && (i == 0 || i == n - 1)) {
+            r = per_row(i, 0, zr);
+          } else {
+            r = compact_row02(o[0], o[WP], win[j + 1], win[j + 2], win[j + 3]);
+          }
+          real co, dd, zz;
+          elim(r, zr, Pm, Qm, Dm, Zm, co, dd, zz);
+          o[0] = co;
+          o[WP] = dd;
+          if (PER) zmv[j] = zz;
+          Am += pim * dd;
+          if (PER) Azm += pim * zz;
+          pim *= -co;
         }
-        cmv[j] = cpm; dmv[j] = dpm; zmv[j] = PER ? zpm : real(0);
-        cpv[j] = cpp; dpv[j] = dpp; zpv[j] = PER ? zpp : real(0);
-        Am += pim * dpm;
-        Ap += pip * dpp;
-        if (PER) { Azm += pim * zpm; Azp += pip * zpp; }
-        pim *= -cpm;
-        pip *= -cpp;
+      }
+      {   // plus: cell s0 + M - 1 - jj
+        const int j = M - 1 - jj;
+        if (j < len) {
+          const int i = s0 + j;
+          real *o = wt + 2 * WP + cb + j;
+          Row<real> r;
+          real zr = real(0);
+          if (bounded && (i == 0 || i == n - 1)) {
+            r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
+          } else if (PER && (i == 0 || i == n - 1)) {
+            r = per_row(i, 1, zr);
+          } else {
+            r = compact_row02(o[0], o[WP], win[j + 3], win[j + 2], win[j + 1]);
+          }
+          real co, dd, zz;
+          elim(r, zr, Pp, Qp, Dp, Zp, co, dd, zz);
+          o[0] = co;
+          o[WP] = dd;
+          if (PER) zpv[j] = zz;
+          Ap += pip * dd;
+          if (PER) Azp += pip * zz;
+          pip *= -co;
+        }
       }
     }
     bm.A = Am; bm.Az = Azm; bm.B = pim;
@@ -653,25 +944,49 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
   }
 
   // ------------------------------------------- backward scans (F6)
+  // minus back maps accumulate from the higher lanes (its back substitution
+  // runs right to left), plus maps from the lower lanes
   Bwd<real> bm_in = bm, bp_in = bp;
+  if constexpr (MIXED) {
+    Bwd2 b2;
+    b2.A = make_float2(bm.A, bp.A);
+    b2.B = make_float2(bm.B, bp.B);
+    b2.Az = make_float2(bm.Az, bp.Az);
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    Bwd<real> o;
-    o.A = shfl_down_r(bm_in.A, d); o.B = shfl_down_r(bm_in.B, d);
-    o.Az = PER ? shfl_down_r(bm_in.Az, d) : real(0);
-    if (lane + d < 32) bm_in = bwd_compose(bm_in, o);
-    Bwd<real> q;
-    q.A = shfl_up_r(bp_in.A, d); q.B = shfl_up_r(bp_in.B, d);
-    q.Az = PER ? shfl_up_r(bp_in.Az, d) : real(0);
-    if (lane >= d) bp_in = bwd_compose(bp_in, q);
+    for (int d = 1; d < 32; d <<= 1) {
+      const bool am = lane + d < 32, ap = lane >= d;
+      Bwd2 o;
+      {
+        float tm = __shfl_down_sync(0xffffffffu, b2.A.x, d), tp = __shfl_up_sync(0xffffffffu, b2.A.y, d);
+        o.A = make_float2(am ? tm : 0.0f, ap ? tp : 0.0f);
+      }
+      {
+        float tm = __shfl_down_sync(0xffffffffu, b2.B.x, d), tp = __shfl_up_sync(0xffffffffu, b2.B.y, d);
+        o.B = make_float2(am ? tm : 1.0f, ap ? tp : 1.0f);
+      }
+      if (PER) {
+        float tm = __shfl_down_sync(0xffffffffu, b2.Az.x, d), tp = __shfl_up_sync(0xffffffffu, b2.Az.y, d);
+        o.Az = make_float2(am ? tm : 0.0f, ap ? tp : 0.0f);
+      } else {
+        o.Az = p_set(0.0f);
+      }
+      b2 = bwd2_compose(b2, o);   // with the identity where a lane has no partner
+    }
+    bm_in.A = b2.A.x; bm_in.B = b2.B.x; bm_in.Az = b2.Az.x;
+    bp_in.A = b2.A.y; bp_in.B = b2.B.y; bp_in.Az = b2.Az.y;
+  } else {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      Bwd<real> o;
+      o.A = shfl_down_r(bm_in.A, d); o.B = shfl_down_r(bm_in.B, d);
+      o.Az = PER ? shfl_down_r(bm_in.Az, d) : real(0);
+      if (lane + d < 32) bm_in = bwd_compose(bm_in, o);
+      Bwd<real> q;
+      q.A = shfl_up_r(bp_in.A, d); q.B = shfl_up_r(bp_in.B, d);
+      q.Az = PER ? shfl_up_r(bp_in.Az, d) : real(0);
+      if (lane >= d) bp_in = bwd_compose(bp_in, q);
+    }
   }
-  Bwd<real> bm_ex, bp_ex;
-  bm_ex.A = shfl_down_r(bm_in.A, 1); bm_ex.B = shfl_down_r(bm_in.B, 1);
-  bm_ex.Az = PER ? shfl_down_r(bm_in.Az, 1) : real(0);
-  if (lane == 31) { bm_ex.A = real(0); bm_ex.B = real(1); bm_ex.Az = real(0); }
-  bp_ex.A = shfl_up_r(bp_in.A, 1); bp_ex.B = shfl_up_r(bp_in.B, 1);
-  bp_ex.Az = PER ? shfl_up_r(bp_in.Az, 1) : real(0);
-  if (lane == 0) { bp_ex.A = real(0); bp_ex.B = real(1); bp_ex.Az = real(0); }
   if (lane == 0) ex.warp_bwd[v][0][w] = bm_in;
   if (lane == 31) ex.warp_bwd[v][1][w] = bp_in;
   __syncthreads();
@@ -690,70 +1005,151 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
     ex.seg_bwd[vv][sd] = sg;
   }
   cluster.sync();
-  if (tid < 2 * NV) {
-    int vv = tid >> 1, sd = tid & 1;
-    real x = real(0), z = real(0);
-    if (sd == 0) {
-      for (int q = R - 1; q > rank; --q) {
-        Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
-        Bwd<real> b = rx->seg_bwd[vv][0];
-        x = b.A + b.B * x;
-        z = b.Az + b.B * z;
-      }
-      for (int ww = WPV - 1; ww >= 0; --ww) {
-        ex.warp_xn[vv][0][ww][0] = x;
-        ex.warp_xn[vv][0][ww][1] = z;
-        Bwd<real> b = ex.warp_bwd[vv][0][ww];
-        x = b.A + b.B * x;
-        z = b.Az + b.B * z;
+  // back substitution entering this segment from the far side: the back maps
+  // of the CTAs behind it in that order (minus: the higher ranks, the last
+  // acting first; plus: the lower ranks, rank 0 acting first); x = 0 after
+  // the line end.  Mixed form: a tree over 16 lanes as in F4; FP64 form: one
+  // thread per side and variable.
+  {
+    real xb = real(0), zb = real(0);
+    int bvv = -1, bsd = 0;
+    if constexpr (MIXED) {
+      if (tid < 2 * NV * 16) {
+        const int grp = tid >> 4, q = tid & 15;
+        const int vv = grp >> 1, sd = grp & 1;
+        Bwd<real> bq;
+        bq.A = real(0); bq.B = real(1); bq.Az = real(0);
+        if (q < R && (sd == 0 ? q > rank : q < rank)) {
+          Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
+          bq = rx->seg_bwd[vv][sd];
+        }
+#pragma unroll
+        for (int d = 1; d < 16; d <<= 1) {
+          Bwd<real> o;
+          o.A = shfl_down_r(bq.A, d, 16);
+          o.B = shfl_down_r(bq.B, d, 16);
+          o.Az = PER ? shfl_down_r(bq.Az, d, 16) : real(0);
+          if ((q & (2 * d - 1)) == 0) bq = sd == 0 ? bwd_compose(bq, o) : bwd_compose(o, bq);
+        }
+        if (q == 0) {
+          xb = bq.A;
+          zb = bq.Az;
+          bvv = vv;
+          bsd = sd;
+        }
       }
     } else {
-      for (int q = 0; q < rank; ++q) {
-        Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
-        Bwd<real> b = rx->seg_bwd[vv][1];
-        x = b.A + b.B * x;
-        z = b.Az + b.B * z;
+      if (tid < 2 * NV) {
+        const int vv = tid >> 1, sd = tid & 1;
+        if (sd == 0) {
+          for (int q = R - 1; q > rank; --q) {
+            Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
+            Bwd<real> b = rx->seg_bwd[vv][0];
+            xb = b.A + b.B * xb;
+            zb = b.Az + b.B * zb;
+          }
+        } else {
+          for (int q = 0; q < rank; ++q) {
+            Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
+            Bwd<real> b = rx->seg_bwd[vv][1];
+            xb = b.A + b.B * xb;
+            zb = b.Az + b.B * zb;
+          }
+        }
+        bvv = vv;
+        bsd = sd;
       }
+    }
+    if (bvv >= 0) {
       for (int ww = 0; ww < WPV; ++ww) {
-        ex.warp_xn[vv][1][ww][0] = x;
-        ex.warp_xn[vv][1][ww][1] = z;
-        Bwd<real> b = ex.warp_bwd[vv][1][ww];
-        x = b.A + b.B * x;
-        z = b.Az + b.B * z;
+        int wi = bsd == 0 ? WPV - 1 - ww : ww;
+        ex.warp_xn[bvv][bsd][wi][0] = xb;
+        ex.warp_xn[bvv][bsd][wi][1] = zb;
+        Bwd<real> b = ex.warp_bwd[bvv][bsd][wi];
+        xb = b.A + b.B * xb;
+        zb = b.Az + b.B * zb;
       }
     }
   }
   __syncthreads();
 
   // ------------------------------------------- back substitution (F8)
-  real zmo[M], zpo[M];
+  // minus from the chunk's last cell down, plus from its first cell up; c', d'
+  // come from the weight slots, the solution goes to Fm / Fp.  The value
+  // entering a chunk is the value leaving the neighbouring lane's chunk (its
+  // inclusive back map applied to the warp's entering value).
+  real xm, zm_, xp, zp_;
   {
-    real xn = ex.warp_xn[v][0][w][0], zn = ex.warp_xn[v][0][w][1];
-    real x = bm_ex.A + bm_ex.B * xn;
-    real z = bm_ex.Az + bm_ex.B * zn;
-#pragma unroll
-    for (int jj = 0; jj < M; ++jj) {
-      int j = M - 1 - jj;
-      if (j < len) {
-        x = dmv[j] - cmv[j] * x;
-        if (PER) z = zmv[j] - cmv[j] * z;
-        Fm[v * SEG + (s0 + j - lo)] = x;
-        zmo[j] = z;
-      }
-    }
+    const real xn = ex.warp_xn[v][0][w][0], zn = ex.warp_xn[v][0][w][1];
+    const real xo = bm_in.A + bm_in.B * xn, zo = bm_in.Az + bm_in.B * zn;
+    xm = shfl_down_r(xo, 1);
+    zm_ = PER ? shfl_down_r(zo, 1) : real(0);
+    if (lane == 31) { xm = xn; zm_ = zn; }
   }
   {
-    real xn = ex.warp_xn[v][1][w][0], zn = ex.warp_xn[v][1][w][1];
-    real x = bp_ex.A + bp_ex.B * xn;
-    real z = bp_ex.Az + bp_ex.B * zn;
+    const real xn = ex.warp_xn[v][1][w][0], zn = ex.warp_xn[v][1][w][1];
+    const real xo = bp_in.A + bp_in.B * xn, zo = bp_in.Az + bp_in.B * zn;
+    xp = shfl_up_r(xo, 1);
+    zp_ = PER ? shfl_up_r(zo, 1) : real(0);
+    if (lane == 0) { xp = xn; zp_ = zn; }
+  }
+  real zmo[PER ? M : 1], zpo[PER ? M : 1];
+  bool done8 = false;
+  if constexpr (MIXED) {
+    if (plain) {   // both systems together, no guards
+      const float *om = wt + cb, *op = wt + 2 * WP + cb;
+      float *dm = Fm + v * WP + cb, *dp = Fp + v * WP + cb;
+      float2 x2 = make_float2(xm, xp), z2 = make_float2(zm_, zp_);
 #pragma unroll
-    for (int jj = 0; jj < M; ++jj) {
-      int pos = M - 1 - jj;     // plus positions from the chunk's left-most cell
-      if (pos < len) {
-        x = dpv[pos] - cpv[pos] * x;
-        if (PER) z = zpv[pos] - cpv[pos] * z;
-        Fp[v * SEG + (s0 + len - 1 - pos - lo)] = x;
-        zpo[pos] = z;
+      for (int jj = 0; jj < M; ++jj) {
+        const int jm = M - 1 - jj, jp = jj;
+        const float2 nc = make_float2(-om[jm], -op[jp]);
+        x2 = p_fma(nc, x2, make_float2(om[WP + jm], op[WP + jp]));
+        dm[jm] = x2.x;
+        dp[jp] = x2.y;
+        if (PER) {
+          z2 = p_fma(nc, z2, make_float2(zmv[jm], zpv[jp]));
+          zmo[jm] = z2.x;
+          zpo[jp] = z2.y;
+        }
+      }
+      done8 = true;
+    }
+  }
+  if (!done8) {
+    {
+      const real *o = wt + cb;
+      real *dst = Fm + v * WP + cb;
+      real x = xm, z = zm_;
+#pragma unroll
+      for (int jj = 0; jj < M; ++jj) {
+        const int j = M - 1 - jj;
+        if (j < len) {
+          const real c = o[j];
+          x = o[WP + j] - c * x;
+          dst[j] = x;
+          if (PER) {
+            z = zmv[j] - c * z;
+            zmo[j] = z;
+          }
+        }
+      }
+    }
+    {
+      const real *o = wt + 2 * WP + cb;
+      real *dst = Fp + v * WP + cb;
+      real x = xp, z = zp_;
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        if (j < len) {
+          const real c = o[j];
+          x = o[WP + j] - c * x;
+          dst[j] = x;
+          if (PER) {
+            z = zpv[j] - c * z;
+            zpo[j] = z;
+          }
+        }
       }
     }
   }
@@ -761,24 +1157,30 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
   if (PER) {
     // Sherman-Morrison correction x = y - (v.y)/(1 + v.z) z, with
     // v = e_first + (corner_first / g) e_last and corner_first / g = -a0/b0
-    // of the unmodified position-0 row; the scalars in FP64
+    // of the unmodified position-0 row; the scalars in FP64.  zmo, zpo are
+    // indexed by the chunk's cells.
+    real zm_last = real(0), zp_last = real(0);
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      if (j == len - 1) { zm_last = zmo[j]; zp_last = zpo[j]; }
+    }
     if (len > 0 && s0 == 0) {              // cell 0: minus first, plus last
       real a0, b0;
       far_row(0, a0, b0);
       ex.sm[v][0][4] = -(double)a0 / (double)b0;
-      ex.sm[v][0][0] = Fm[v * SEG + 0];
+      ex.sm[v][0][0] = Fm[v * WP + 0];
       ex.sm[v][0][1] = zmo[0];
-      ex.sm[v][1][2] = Fp[v * SEG + 0];
-      ex.sm[v][1][3] = zpo[len - 1];
+      ex.sm[v][1][2] = Fp[v * WP + 0];
+      ex.sm[v][1][3] = zpo[0];
     }
     if (len > 0 && s0 + len == n) {        // cell n-1: plus first, minus last
       real a0, b0;
       far_row(1, a0, b0);
       ex.sm[v][1][4] = -(double)a0 / (double)b0;
-      ex.sm[v][1][0] = Fp[v * SEG + (n - 1 - lo)];
-      ex.sm[v][1][1] = zpo[0];
-      ex.sm[v][0][2] = Fm[v * SEG + (n - 1 - lo)];
-      ex.sm[v][0][3] = zmo[len - 1];
+      ex.sm[v][1][0] = Fp[v * WP + S::pad(n - 1 - lo)];
+      ex.sm[v][1][1] = zp_last;
+      ex.sm[v][0][2] = Fm[v * WP + S::pad(n - 1 - lo)];
+      ex.sm[v][0][3] = zm_last;
     }
     cluster.sync();
     {
@@ -792,8 +1194,8 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
 #pragma unroll
       for (int j = 0; j < M; ++j) {
         if (j < len) {
-          Fm[v * SEG + (s0 + j - lo)] -= fm_ * zmo[j];
-          Fp[v * SEG + (s0 + j - lo)] -= fp_ * zpo[len - 1 - j];
+          Fm[v * WP + cb + j] -= fm_ * zmo[j];
+          Fp[v * WP + cb + j] -= fp_ * zpo[j];
         }
       }
     }
@@ -807,9 +1209,9 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
       real ub[NV], a[NV], b[NV];
 #pragma unroll
       for (int kv = 0; kv < NV; ++kv) {
-        ub[kv] = Us[kv * UW + c + 2];
-        a[kv] = Fm[kv * SEG + c];
-        b[kv] = Fp[kv * SEG + c];
+        ub[kv] = Us[kv * UWP + UH + S::pad(c)];
+        a[kv] = Fm[kv * WP + S::pad(c)];
+        b[kv] = Fp[kv * WP + S::pad(c)];
       }
       int f;
       if constexpr (MIXED) f = limit_cell_mixed<NV>(ub, a, b, wgl, eps_pos);
@@ -817,18 +1219,19 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
       if (f) {
 #pragma unroll
         for (int kv = 0; kv < NV; ++kv) {
-          Fm[kv * SEG + c] = a[kv];
-          Fp[kv * SEG + c] = b[kv];
+          Fm[kv * WP + S::pad(c)] = a[kv];
+          Fp[kv * WP + S::pad(c)] = b[kv];
         }
       }
       t1 += f & 1;
       t2 += (f >> 1) & 1;
     }
   }
-  cluster.sync();
-
   // ---------------------------------------------------------------- flux
-  for (int f = lo + tid; f <= hi; f += T) {
+  // HLLC at face f (between cells f-1 and f): the left state is U^- of cell
+  // f-1, the right state U^+ of cell f; the two segment-end faces read a
+  // neighbour CTA's value
+  auto face = [&](int f) {
     real Ul[NV], Ur[NV], F[NV];
     const real *srcL = nullptr;
     const real *srcR = nullptr;
@@ -847,11 +1250,11 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
     } else { srcR = Fp; ir = f - lo; }
     if (srcL) {
 #pragma unroll
-      for (int kv = 0; kv < NV; ++kv) Ul[kv] = srcL[kv * SEG + il];
+      for (int kv = 0; kv < NV; ++kv) Ul[kv] = srcL[kv * WP + S::pad(il)];
     }
     if (srcR) {
 #pragma unroll
-      for (int kv = 0; kv < NV; ++kv) Ur[kv] = srcR[kv * SEG + ir];
+      for (int kv = 0; kv < NV; ++kv) Ur[kv] = srcR[kv * WP + S::pad(ir)];
     }
     if (!srcL) {  // boundary face 0: exterior = BC(interior)
 #pragma unroll
@@ -866,14 +1269,42 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
     hllc<real, NV>(Ul, Ur, gam, F);
 #pragma unroll
     for (int kv = 0; kv < NV; ++kv) Fl[kv * (SEG + 2) + (f - lo)] = F[kv];
+  };
+  if constexpr (MIXED) {
+    // faces with both states in this CTA first, then (after the cluster
+    // barrier completes) the two segment-end faces, on two warps
+    __syncthreads();
+    cluster_arrive();   // this CTA's limited face values, for the neighbours
+    const bool lo_remote = PER || lo > 0, hi_remote = PER || hi < n;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {   // one call site of the face code
+      int f, fend;
+      if (pass == 0) {
+        f = lo + (lo_remote ? 1 : 0) + tid;
+        fend = hi - (hi_remote ? 1 : 0);
+      } else {
+        cluster_wait();
+        f = (tid == 0 && lo_remote) ? lo : ((tid == 32 && hi_remote) ? hi : hi + 1);
+        fend = hi;
+      }
+      for (; f <= fend; f += T) face(f);
+    }
+  } else {
+    // the FP64 form (one CTA per SM, bound by the FP64 pipe): a plain
+    // barrier, then every face in one pass
+    cluster.sync();
+    for (int f = lo + tid; f <= hi; f += T) face(f);
   }
-  cluster.sync();   // neighbours' face values are no longer read after this
+  __syncthreads();
+  // the neighbours' face values are no longer read: arrive now, wait before
+  // exit (a CTA's shared memory must outlive the neighbours' reads of it)
+  cluster_arrive_relaxed();
 
   // ---------------------------------------------------------------- update
   double mymin = 1.0e300, mymax = 0.0;
   unsigned int nbad = 0;
   unsigned long long firstbad = ~0ull;
-  const real ih = real(1.0 / args.h);
+  const real ih = real(args.ih);
   const double dt = (MODE == MODE_FINAL) ? ctl->dt : 0.0;
   const real *Din = reinterpret_cast<const real *>(args.Din);
   for (int c = tid; c < hi - lo; c += T) {
@@ -904,10 +1335,12 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
         else if (args.stage == 1) un = 0.75 * args.U0[g * args.ncell + addr] + 0.25 * uk + 0.25 * dt * L;
         else un = args.U0[g * args.ncell + addr] / 3.0 + 2.0 / 3.0 * uk + 2.0 / 3.0 * dt * L;
         args.Uout[g * args.ncell + addr] = un;
-        Ut[g] = un;
+        Ut[kv] = un;   // line-variable order (no run-time register index)
       }
-      double rho = Ut[0];
-      double mx = Ut[1], my = NV == 4 ? Ut[2] : 0.0, E = Ut[NV - 1];
+      // grid momenta: line variable 1 is the normal one (grid index vn)
+      double rho = Ut[0], E = Ut[NV - 1];
+      double mx = NV == 4 && args.vn != 1 ? Ut[2] : Ut[1];
+      double my = NV == 4 ? (args.vn != 1 ? Ut[1] : Ut[2]) : 0.0;
       double e = E / rho - 0.5 * (mx * mx + my * my) / (rho * rho);
       bool ok = (rho > 0.0) && (e > 0.0) && isfinite(E) && isfinite(mx) && isfinite(my);
       if (!ok) {
@@ -948,11 +1381,12 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
         }
         args.Uoh[a] = un.hi;
         args.Uol[a] = un.lo;
-        Th[g] = un.hi;
-        Tl[g] = un.lo;
+        Th[kv] = un.hi;   // line-variable order (no run-time register index)
+        Tl[kv] = un.lo;
       }
-      float rho = Th[0];
-      float mx = Th[1], my = NV == 4 ? Th[2] : 0.0f, E = Th[NV - 1];
+      float rho = Th[0], E = Th[NV - 1];
+      float mx = NV == 4 && args.vn != 1 ? Th[2] : Th[1];
+      float my = NV == 4 ? (args.vn != 1 ? Th[1] : Th[2]) : 0.0f;
       // g = rho E - |m|^2/2 with the compensated parts (its sign decides G)
       dfl rE = df_mul({Th[0], Tl[0]}, {Th[NV - 1], Tl[NV - 1]});
       dfl m2 = df_mul({Th[1], Tl[1]}, {Th[1], Tl[1]});
@@ -1012,6 +1446,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M), sizeof(real) == 4 ? 2 : 1)
       if (t2) atomicAdd(&ctl->theta2, (unsigned long long)t2);
     }
   }
+  cluster_wait();
 }
 
 }  // namespace ppk

@@ -452,7 +452,9 @@ cudaError_t dispatch(const pp_cweno_s *h, int mode, bool periodic, const SweepAr
   c.mode = mode;
   c.attrs_only = attrs_only;
   c.m = h->m;
-  return launch_sweep(c, a, nlines, h->stream);
+  SweepArgs b = a;
+  b.ih = a.h > 0.0 ? 1.0 / a.h : 0.0;   // batched launches take it per problem
+  return launch_sweep(c, b, nlines, h->stream);
 }
 
 // Single-problem launch.  Uin, U0, Uout are state buffers (FP64 planes or
@@ -899,6 +901,8 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
     d.off = off;
     d.dx = (c.x1 - c.x0) / (double)d.nx;
     d.dy = c.ndim == 2 ? (c.y1 - c.y0) / (double)d.ny : 1.0;
+    d.idx = 1.0 / d.dx;
+    d.idy = 1.0 / d.dy;
     for (int k = 0; k < 4; ++k) d.bc[k] = c.bc[k];
     h->probs_h.push_back(d);
     off += (long long)h->nv * d.ncell;

@@ -45,6 +45,11 @@ cudaError_t launch_m(const SweepArgs &a, long long nlines, cudaStream_t st, bool
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::bytes);
     if (e != cudaSuccess) return e;
+    // the largest shared-memory carveout, so that the resident-CTA count the
+    // kernel is compiled for is not cut by the L1 split
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }
   cudaLaunchConfig_t cfg = {};
