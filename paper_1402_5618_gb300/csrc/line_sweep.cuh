@@ -368,6 +368,24 @@ __device__ __forceinline__ Bwd2 bwd2_compose(const Bwd2 &X, const Bwd2 &Y) {
   return r;
 }
 
+// WENO-Z weights w0, w2 of the minus side (ratios q0, q1, q2, linear weights
+// 0.2, 0.5, 0.3) and v0, v2 of the plus side (the same ratios reversed), in
+// paired FP32; the middle term is common to both
+__device__ __forceinline__ void zweights_pair(float q0, float q1, float q2, float one, float &w0,
+                                              float &w2, float &v0, float &v2) {
+  const float2 o2 = p_set(one);
+  const float2 a0 = p_mul(p_set(0.2f), p_add(o2, make_float2(q0, q2)));
+  const float a1 = 0.5f * (one + q1);
+  const float2 a2 = p_mul(p_set(0.3f), p_add(o2, make_float2(q2, q0)));
+  const float2 sum = p_add(p_add(a0, a2), p_set(a1));
+  const float2 is = make_float2(1.0f / sum.x, 1.0f / sum.y);
+  const float2 W0 = p_mul(a0, is), W2 = p_mul(a2, is);
+  w0 = W0.x;
+  w2 = W2.x;
+  v0 = W0.y;
+  v2 = W2.y;
+}
+
 // the compact row of both systems from their (w0, w2) and neighbour averages
 __device__ __forceinline__ void row2(float2 w0, float2 w2, float2 up, float2 u0, float2 un,
                                      float2 &a, float2 &b, float2 &c, float2 &r) {
@@ -640,8 +658,13 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
         } else {
           real q0, q1, q2, one, w0, w1, w2, v0, v1, v2;
           zratios_any(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w, q0, q1, q2, one);
-          zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
-          zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, v0, v1, v2, one);
+          if constexpr (MIXED) {
+            zweights_pair(q0, q1, q2, one, w0, w2, v0, v2);
+            (void)w1; (void)v1;
+          } else {
+            zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
+            zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, v0, v1, v2, one);
+          }
           wt[cb + j] = w0;
           wt[WP + cb + j] = w2;
           wt[2 * WP + cb + j] = v0;
@@ -1204,6 +1227,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
 
   // ---------------------------------------------------------------- limit
   unsigned int t1 = 0, t2 = 0;
+  const real inv12 = real(1) / (real(1) - real(2) * wgl);
   if (args.limiter) {
     for (int c = tid; c < hi - lo; c += T) {
       real ub[NV], a[NV], b[NV];
@@ -1214,7 +1238,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
         b[kv] = Fp[kv * WP + S::pad(c)];
       }
       int f;
-      if constexpr (MIXED) f = limit_cell_mixed<NV>(ub, a, b, wgl, eps_pos);
+      if constexpr (MIXED) f = limit_cell_mixed<NV>(ub, a, b, wgl, inv12, eps_pos);
       else f = limit_cell<real, NV>(ub, a, b, wgl, eps_pos, unit_roundoff<real>());
       if (f) {
 #pragma unroll

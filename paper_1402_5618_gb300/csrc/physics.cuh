@@ -49,17 +49,14 @@ __device__ __forceinline__ void zratios_scaled(float um2, float um1, float u0, f
   float tau = fabsf(b2 - b0);
   float d0 = b0 + eps, d1 = b1 + eps, d2 = b2 + eps;
   float dmin = fminf(fminf(d0, d1), d2);
-  if (tau <= dmin) {
-    one = 1.0f;
-    q0 = sqr(tau / d0);
-    q1 = sqr(tau / d1);
-    q2 = sqr(tau / d2);
-  } else {
-    one = sqr(dmin / tau);
-    q0 = sqr(dmin / d0);
-    q1 = sqr(dmin / d1);
-    q2 = sqr(dmin / d2);
-  }
+  // branch-free: the numerator is min(tau, dmin); the constant term is 1
+  // while tau <= dmin (no rescaling), else (dmin/tau)^2
+  const float r = fminf(tau, dmin);
+  const float sc = dmin / tau;
+  one = tau <= dmin ? 1.0f : sc * sc;
+  q0 = sqr(r / d0);
+  q1 = sqr(r / d1);
+  q2 = sqr(r / d2);
 }
 
 // normalised weights from linear weights (d0, d1, d2) and ratios (q0, q1, q2);
@@ -318,39 +315,77 @@ __device__ __forceinline__ int limit_cell(const real *ub, real *um, real *up, re
 // allowances; only cells that may need limiting compute the scaling factors
 // theta_1, theta_2 in FP64 (with the FP32 allowance, since the limited faces
 // are stored in FP32).  Returns the limiter flags.
+// the FP64 factors of a cell that may need limiting: rare, so kept out of
+// line (its FP64 registers do not count against the line kernel's hot
+// path); the states travel by value
 template <int NV>
-__device__ __forceinline__ int limit_cell_mixed(const float *ub, float *um, float *up, float wgl,
-                                                float eps) {
-  const float uf = 5.9604645e-08f;
-  float inv12 = 1.0f / (1.0f - 2.0f * wgl);
-  float rho_star = (ub[0] - wgl * up[0] - wgl * um[0]) * inv12;
-  float rho_min = fminf(fminf(um[0], up[0]), rho_star);
-  bool need = rho_min < 2.0f * (eps + 8.0f * uf * (fabsf(ub[0]) + fabsf(rho_min)));
-  if (!need) {
-    float w3[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) w3[k] = (ub[k] - wgl * up[k] - wgl * um[k]) * inv12;
-    need = energy_form<float, NV>(um, eps) < 2.0f * energy_allowance<float, NV>(ub, um, uf) ||
-           energy_form<float, NV>(up, eps) < 2.0f * energy_allowance<float, NV>(ub, up, uf) ||
-           energy_form<float, NV>(w3, eps) < 2.0f * energy_allowance<float, NV>(ub, w3, uf);
-  }
-  if (!need) return 0;
+struct LimStates {
+  float b[NV], m[NV], p[NV];
+  int flags;
+};
+
+template <int NV>
+__device__ __noinline__ LimStates<NV> limit_cell_fp64(LimStates<NV> s, float wgl, float eps,
+                                                      float uf) {
   double b[NV], m[NV], p[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    b[k] = ub[k];
-    m[k] = um[k];
-    p[k] = up[k];
+    b[k] = s.b[k];
+    m[k] = s.m[k];
+    p[k] = s.p[k];
   }
-  int f = limit_cell<double, NV>(b, m, p, (double)wgl, (double)eps, (double)uf);
-  if (f) {
+  s.flags = limit_cell<double, NV>(b, m, p, (double)wgl, (double)eps, (double)uf);
+  if (s.flags) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      um[k] = (float)m[k];
-      up[k] = (float)p[k];
+      s.m[k] = (float)m[k];
+      s.p[k] = (float)p[k];
     }
   }
-  return f;
+  return s;
+}
+
+template <int NV>
+__device__ __forceinline__ int limit_cell_mixed(const float *ub, float *um, float *up, float wgl,
+                                                float inv12, float eps) {
+  const float uf = 5.9604645e-08f;
+  float w3[NV];   // the interior quadrature point implied by the cell average
+#pragma unroll
+  for (int k = 0; k < NV; ++k) w3[k] = (ub[k] - wgl * up[k] - wgl * um[k]) * inv12;
+  const float rho_min = fminf(fminf(um[0], up[0]), w3[0]);
+  bool need = rho_min < 2.0f * (eps + 8.0f * uf * (fabsf(ub[0]) + fabsf(rho_min)));
+  // one allowance for the three points, with each magnitude replaced by the
+  // largest over them: it bounds the three allowances, so the test (doubled
+  // for FP32) flags every cell the exact test would (a superset; the FP64
+  // pass decides)
+  const float rmx = fmaxf(fmaxf(fabsf(um[0]), fabsf(up[0])), fabsf(w3[0]));
+  const float emx = fmaxf(fmaxf(fabsf(um[NV - 1]), fabsf(up[NV - 1])), fabsf(w3[NV - 1]));
+  float sm = 0.0f;
+#pragma unroll
+  for (int k = 1; k < NV - 1; ++k) {
+    const float mk = fmaxf(fmaxf(fabsf(um[k]), fabsf(up[k])), fabsf(w3[k]));
+    sm += sqr(fabsf(ub[k]) + mk);
+  }
+  const float eta2 =
+      32.0f * uf * ((fabsf(ub[NV - 1]) + emx) * (fabsf(ub[0]) + rmx) + sm);
+  need = need | (energy_form<float, NV>(um, eps) < eta2) |
+         (energy_form<float, NV>(up, eps) < eta2) | (energy_form<float, NV>(w3, eps) < eta2);
+  if (!need) return 0;
+  LimStates<NV> st;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    st.b[k] = ub[k];
+    st.m[k] = um[k];
+    st.p[k] = up[k];
+  }
+  st.flags = 0;
+  st = limit_cell_fp64<NV>(st, wgl, eps, uf);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    um[k] = st.m[k];
+    up[k] = st.p[k];
+  }
+  return st.flags;
 }
 
 }  // namespace ppk
