@@ -188,19 +188,26 @@ __global__ void transpose_planes_kernel(const float *in, float *out, int nx, int
 // (D_y read from its transposed layout), compensated SSP-RK3 update of the
 // hi + lo state, the transposed hi copy of the result for the next y sweep,
 // and the grid-wide reductions (min rho, max rate, cells outside G).
-template <int NV>
-__global__ void combine_t_kernel(const float *Ukh, const float *Ukl, const float *U0h,
-                                 const float *U0l, const float *Dx, const float *DyT, float *Uoh,
-                                 float *Uol, float *UT, int nx, int ny, long long ncell, int stage,
-                                 float hx, float hy, float gg1, Ctl *ctl) {
+template <int NV, int RY>
+__global__ void __launch_bounds__(TT *RY)
+    combine_t_kernel(const float *Ukh, const float *Ukl, const float *U0h, const float *U0l,
+                     const float *Dx, const float *DyT, float *Uoh, float *Uol, float *UT, int nx,
+                     int ny, long long ncell, int stage, float ihx, float ihy, float gg1,
+                     Ctl *ctl) {
   __shared__ float tin[NV][TT][TT + 1];
   __shared__ float tout[NV][TT][TT + 1];
+  __shared__ float red_min[RY], red_max[RY];
+  __shared__ unsigned int red_bad[RY];
+  __shared__ unsigned long long red_first[RY];
   if (!ctl->active) return;
   const int i0 = blockIdx.x * TT, j0 = blockIdx.y * TT;
   // D_y tile: DyT[v][i][j], read along j
+#pragma unroll
   for (int v = 0; v < NV; ++v)
-    for (int r = threadIdx.y; r < TT; r += blockDim.y) {
-      int i = i0 + r, j = j0 + threadIdx.x;
+#pragma unroll
+    for (int rr = 0; rr < TT / RY; ++rr) {
+      const int r = threadIdx.y + rr * RY;
+      const int i = i0 + r, j = j0 + threadIdx.x;
       if (i < nx && j < ny) tin[v][threadIdx.x][r] = DyT[v * ncell + (long long)i * ny + j];
     }
   __syncthreads();
@@ -208,25 +215,27 @@ __global__ void combine_t_kernel(const float *Ukh, const float *Ukl, const float
   const dfl dtd = {float(dt), float(dt - double(float(dt)))};
   const dfl third = {0.333333343f, -9.93410776e-09f};
   const dfl two3 = {0.666666687f, -1.98682155e-08f};
-  double mymin = 1e300, mymax = 0.0;
+  float mymin = 3.0e38f, mymax = 0.0f;   // FP32 running extrema (converted once)
   unsigned int nbad = 0;
   unsigned long long firstbad = ~0ull;
-  for (int r = threadIdx.y; r < TT; r += blockDim.y) {
-    int j = j0 + r, i = i0 + threadIdx.x;
+#pragma unroll
+  for (int rr = 0; rr < TT / RY; ++rr) {
+    const int r = threadIdx.y + rr * RY;
+    const int j = j0 + r, i = i0 + threadIdx.x;
     if (j >= ny || i >= nx) continue;
-    long long addr = (long long)j * nx + i;
+    const long long addr = (long long)j * nx + i;
     float Th[NV], Tl[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      long long a = v * ncell + addr;
-      float L = Dx[a] + tin[v][r][threadIdx.x];
-      dfl uk = {Ukh[a], Ukl[a]};
-      dfl s = df_add(uk, df_mul_f(dtd, L));
+      const long long a = v * ncell + addr;
+      const float L = Dx[a] + tin[v][r][threadIdx.x];
+      const dfl uk = {Ukh[a], Ukl[a]};
+      const dfl s = df_add(uk, df_mul_f(dtd, L));
       dfl un;
       if (stage == 0) {
         un = s;
       } else {
-        dfl u0 = {U0h[a], U0l[a]};
+        const dfl u0 = {U0h[a], U0l[a]};
         if (stage == 1) un = df_add(df_mul_f(u0, 0.75f), df_mul_f(s, 0.25f));
         else un = df_add(df_mul(u0, third), df_mul(s, two3));
       }
@@ -236,37 +245,58 @@ __global__ void combine_t_kernel(const float *Ukh, const float *Ukl, const float
       Tl[v] = un.lo;
       tout[v][r][threadIdx.x] = un.hi;
     }
-    float rho = Th[0], mx = Th[1], my = Th[2], E = Th[NV - 1];
-    dfl rE = df_mul({Th[0], Tl[0]}, {Th[NV - 1], Tl[NV - 1]});
-    dfl m2 = df_add(df_mul({Th[1], Tl[1]}, {Th[1], Tl[1]}), df_mul({Th[2], Tl[2]}, {Th[2], Tl[2]}));
-    dfl gq = df_add(rE, {-0.5f * m2.hi, -0.5f * m2.lo});
-    bool ok = rho > 0.0f && gq.hi > 0.0f && isfinite(E) && isfinite(mx) && isfinite(my);
+    const float rho = Th[0], mx = Th[1], my = Th[2], E = Th[NV - 1];
+    const dfl rE = df_mul({Th[0], Tl[0]}, {Th[NV - 1], Tl[NV - 1]});
+    const dfl m2 =
+        df_add(df_mul({Th[1], Tl[1]}, {Th[1], Tl[1]}), df_mul({Th[2], Tl[2]}, {Th[2], Tl[2]}));
+    const dfl gq = df_add(rE, {-0.5f * m2.hi, -0.5f * m2.lo});
+    const bool ok = rho > 0.0f && gq.hi > 0.0f && isfinite(E) && isfinite(mx) && isfinite(my);
     if (!ok) {
       ++nbad;
       firstbad = min(firstbad, (unsigned long long)addr);
     } else {
-      mymin = fmin(mymin, (double)rho);
-      float a = sqrtf(gg1 * (gq.hi / (rho * rho)));
-      float rate = (fabsf(mx / rho) + a) / hx + (fabsf(my / rho) + a) / hy;
-      mymax = fmax(mymax, (double)rate);
+      mymin = fminf(mymin, rho);
+      const float irho = 1.0f / rho;
+      const float a = sqrtf(gg1 * (gq.hi * irho * irho));
+      const float rate = (fabsf(mx * irho) + a) * ihx + (fabsf(my * irho) + a) * ihy;
+      mymax = fmaxf(mymax, rate);
     }
   }
   __syncthreads();
+#pragma unroll
   for (int v = 0; v < NV; ++v)
-    for (int r = threadIdx.y; r < TT; r += blockDim.y) {
-      int i = i0 + r, j = j0 + threadIdx.x;
+#pragma unroll
+    for (int rr = 0; rr < TT / RY; ++rr) {
+      const int r = threadIdx.y + rr * RY;
+      const int i = i0 + r, j = j0 + threadIdx.x;
       if (i < nx && j < ny) UT[v * ncell + (long long)i * ny + j] = tout[v][threadIdx.x][r];
     }
+  // block reduction (one warp per threadIdx.y), then one set of atomics
+#pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
-    mymin = fmin(mymin, __shfl_down_sync(0xffffffffu, mymin, d));
-    mymax = fmax(mymax, __shfl_down_sync(0xffffffffu, mymax, d));
+    mymin = fminf(mymin, __shfl_down_sync(0xffffffffu, mymin, d));
+    mymax = fmaxf(mymax, __shfl_down_sync(0xffffffffu, mymax, d));
     nbad += __shfl_down_sync(0xffffffffu, nbad, d);
-    unsigned long long fb = __shfl_down_sync(0xffffffffu, firstbad, d);
+    const unsigned long long fb = __shfl_down_sync(0xffffffffu, firstbad, d);
     firstbad = fb < firstbad ? fb : firstbad;
   }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMin(&ctl->minrho[stage], dbits(mymin));
-    if (stage == 2) atomicMax(&ctl->rate, dbits(mymax));
+  if (threadIdx.x == 0) {
+    red_min[threadIdx.y] = mymin;
+    red_max[threadIdx.y] = mymax;
+    red_bad[threadIdx.y] = nbad;
+    red_first[threadIdx.y] = firstbad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    for (int y = 1; y < RY; ++y) {
+      mymin = fminf(mymin, red_min[y]);
+      mymax = fmaxf(mymax, red_max[y]);
+      nbad += red_bad[y];
+      firstbad = red_first[y] < firstbad ? red_first[y] : firstbad;
+    }
+    // an all-inadmissible block leaves the FP32 sentinel: report nothing
+    if (mymin < 3.0e38f) atomicMin(&ctl->minrho[stage], dbits((double)mymin));
+    if (stage == 2) atomicMax(&ctl->rate, dbits((double)mymax));
     if (nbad) {
       atomicAdd(&ctl->nviol, (unsigned long long)nbad);
       atomicMin(&ctl->first_bad, firstbad);
@@ -545,9 +575,9 @@ cudaError_t launch_combine_t(const pp_cweno_s *h, const void *Uin, void *Uout, i
   const float *Ukh = hi_of(const_cast<void *>(Uin)), *Ukl = lo_of(h, const_cast<void *>(Uin));
   const float *U0h = hi_of(h->U0), *U0l = lo_of(h, h->U0);
   float *Uoh = hi_of(Uout), *Uol = lo_of(h, Uout);
-  combine_t_kernel<4><<<grid, dim3(TT, 8), 0, h->stream>>>(
+  combine_t_kernel<4, 8><<<grid, dim3(TT, 8), 0, h->stream>>>(
       Ukh, Ukl, U0h, U0l, reinterpret_cast<const float *>(h->D), h->DT, Uoh, Uol, h->UT, (int)h->nx,
-      (int)h->ny, h->ncell, stage, (float)h->dx, (float)h->dy,
+      (int)h->ny, h->ncell, stage, (float)(1.0 / h->dx), (float)(1.0 / h->dy),
       (float)(h->cfg.gamma * (h->cfg.gamma - 1.0)), h->ctl);
   return cudaGetLastError();
 }
