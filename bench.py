@@ -180,8 +180,16 @@ ALU_PEAK_TFLOPS = {1: 152 * 128 * 2 * 2.07e9 / 1e12, 0: 1.25}
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per cell of the
 # dominant kernel, from one ncu capture, valid only for the kernel sources it
 # was taken on (their SHA-256 below); any change to them voids it.
-TRAFFIC_PER_CELL = {}          # {(precision, kernel): bytes per cell}
-TRAFFIC_SRC_SHA256 = None
+# Captured on the 3072^2 blast (`bench.py --profile-only mixed|fp64 --n 3072`,
+# the stage-1 sweeps of the first step): reads are the algorithmic bytes;
+# writes fall short of them by what is still dirty in L2 when the kernel ends.
+TRAFFIC_PER_CELL = {            # {(precision, kernel): bytes per cell}
+    (1, "x_sweep"): 27.68,
+    (1, "y_sweep_transposed"): 27.48,
+    (0, "x_sweep"): 60.00,
+    (0, "y_sweep"): 94.22,
+}
+TRAFFIC_SRC_SHA256 = "b37e78edfb56a45756c0e949778da75e85d856923ba30eaa70d2872cd0ecd3e0"
 KERNEL_SOURCES = ("line_sweep.cuh", "physics.cuh", "dfloat.cuh")
 
 

@@ -189,13 +189,13 @@ __global__ void transpose_planes_kernel(const float *in, float *out, int nx, int
 // hi + lo state, the transposed hi copy of the result for the next y sweep,
 // and the grid-wide reductions (min rho, max rate, cells outside G).
 template <int NV, int RY>
-__global__ void __launch_bounds__(TT *RY)
+__global__ void __launch_bounds__(TT *RY, 6)
     combine_t_kernel(const float *Ukh, const float *Ukl, const float *U0h, const float *U0l,
                      const float *Dx, const float *DyT, float *Uoh, float *Uol, float *UT, int nx,
                      int ny, long long ncell, int stage, float ihx, float ihy, float gg1,
                      Ctl *ctl) {
-  __shared__ float tin[NV][TT][TT + 1];
-  __shared__ float tout[NV][TT][TT + 1];
+  // D_y tile in, then (same element, same thread) the new hi part out
+  __shared__ float tile[NV][TT][TT + 1];
   __shared__ float red_min[RY], red_max[RY];
   __shared__ unsigned int red_bad[RY];
   __shared__ unsigned long long red_first[RY];
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(TT *RY)
     for (int rr = 0; rr < TT / RY; ++rr) {
       const int r = threadIdx.y + rr * RY;
       const int i = i0 + r, j = j0 + threadIdx.x;
-      if (i < nx && j < ny) tin[v][threadIdx.x][r] = DyT[v * ncell + (long long)i * ny + j];
+      if (i < nx && j < ny) tile[v][threadIdx.x][r] = DyT[v * ncell + (long long)i * ny + j];
     }
   __syncthreads();
   const double dt = ctl->dt;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(TT *RY)
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const long long a = v * ncell + addr;
-      const float L = Dx[a] + tin[v][r][threadIdx.x];
+      const float L = Dx[a] + tile[v][r][threadIdx.x];
       const dfl uk = {Ukh[a], Ukl[a]};
       const dfl s = df_add(uk, df_mul_f(dtd, L));
       dfl un;
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(TT *RY)
       Uol[a] = un.lo;
       Th[v] = un.hi;
       Tl[v] = un.lo;
-      tout[v][r][threadIdx.x] = un.hi;
+      tile[v][r][threadIdx.x] = un.hi;
     }
     const float rho = Th[0], mx = Th[1], my = Th[2], E = Th[NV - 1];
     const dfl rE = df_mul({Th[0], Tl[0]}, {Th[NV - 1], Tl[NV - 1]});
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(TT *RY)
     for (int rr = 0; rr < TT / RY; ++rr) {
       const int r = threadIdx.y + rr * RY;
       const int i = i0 + r, j = j0 + threadIdx.x;
-      if (i < nx && j < ny) UT[v * ncell + (long long)i * ny + j] = tout[v][threadIdx.x][r];
+      if (i < nx && j < ny) UT[v * ncell + (long long)i * ny + j] = tile[v][threadIdx.x][r];
     }
   // block reduction (one warp per threadIdx.y), then one set of atomics
 #pragma unroll
