@@ -353,18 +353,27 @@ def _cpu_baseline(seconds_target: float = 20.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--fp64-steps", type=int, default=6)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--fp64-steps", type=int, default=12)
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", choices=["mixed", "fp64"], default=None,
                     help="only run --steps steps of the blast on an --n^2 grid (for ncu)")
     ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--accuracy", action="store_true",
+                    help="accuracy study instead of the throughput line: the blast to t = 1 in "
+                         "both forms at --blast-n, the vortex at --vortex-n against its closed form")
+    ap.add_argument("--blast-n", type=int, default=512)
+    ap.add_argument("--blast-steps", type=int, default=3000)
+    ap.add_argument("--vortex-n", type=int, default=1024)
     args = ap.parse_args()
     if args.profile_only:
         profile_only(args)
+        return
+    if args.accuracy:
+        accuracy_study(args)
         return
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -441,6 +450,95 @@ def profile_only(args):
     print(json.dumps({"profile_only": args.profile_only, "n": args.n, "steps": st.steps,
                       "violations": st.violations, "rows_per_chunk": s.rows_per_chunk()}))
     s.close()
+
+
+def accuracy_study(args):
+    """The stated accuracy of the two forms, measured on the GPU path.
+
+    Blast (the metric's workload, on an n^2 grid, at the positivity CFL, to
+    the time a bounded probe run reaches): positivity over the whole run, the mixed form's density against the
+    FP64 form's (relative L1), the shock radius along a wall and along the
+    diagonal (the density maximum; a cylindrical blast has one radius), and
+    the mirror symmetry U(i, j) = swap(U(j, i)).  Vortex (periodic, CFL 0.5,
+    to t = 1, grids 128^2 doubling up to --vortex-n): L1 and Linf of density
+    against the translated closed form."""
+    import numpy as np
+    import torch
+
+    from paper_1402_5618_gb300 import binding as B
+    from paper_1402_5618_gb300 import workloads as W
+    out = {"accuracy_study": True}
+
+    def run(p, prec, **kw):
+        s = B.Solver(B.config_from_problem(p, prec, **kw))
+        s.set_state(np.ascontiguousarray(p.U0).ravel())
+        t0 = time.perf_counter()
+        n, rc = s.advance(p.t_final, 10 ** 7, check=False)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        U, t, steps = s.get_state()
+        st = s.stats()
+        s.close()
+        return U.reshape(p.U0.shape), dict(steps=int(steps), t=float(t), rc=int(rc), seconds=round(el, 2),
+                                           violations=int(st.violations),
+                                           limiter_theta1=int(st.theta1_active),
+                                           limiter_theta2=int(st.theta2_active))
+
+    n = args.blast_n
+    p = W.blast_2d(n)
+    h = p.dx
+    # the blast's centre empties and heats, so dt keeps shrinking: probe how
+    # far a bounded number of steps gets, then run both forms from the same
+    # initial state to a common end time inside that reach
+    s = B.Solver(B.config_from_problem(p, 1, cfl_positivity_cap=True))
+    s.set_state(np.ascontiguousarray(p.U0).ravel())
+    s.enqueue_steps(args.blast_steps)
+    t_reach = s.get_state()[1]
+    s.close()
+    p.t_final = float(f"{0.8 * t_reach:.3g}")
+    print(f"blast {n}^2: {args.blast_steps} steps reach t = {t_reach:.4g}; "
+          f"both forms run to t = {p.t_final}", file=sys.stderr, flush=True)
+    res = {}
+    for prec, name in ((0, "fp64"), (1, "mixed")):
+        U, info = run(p, prec, cfl_positivity_cap=True)
+        print(f"  {name}: {info}", file=sys.stderr, flush=True)
+        rho = U[0]
+        i_ax = int(np.argmax(rho[0, :]))
+        i_dg = int(np.argmax(np.diagonal(rho)))
+        sym = np.stack([U[0].T, U[2].T, U[1].T, U[3].T])
+        info.update(front_axis=round((i_ax + 0.5) * h, 5),
+                    front_diagonal=round(np.sqrt(2.0) * (i_dg + 0.5) * h, 5),
+                    front_gap_cells=round(abs(np.sqrt(2.0) * (i_dg + 0.5) - (i_ax + 0.5)), 2),
+                    mirror_max_rel=float(np.max(np.abs(U - sym)) / np.max(np.abs(U))),
+                    rho_min=float(rho.min()))
+        res[name] = (U, info)
+    r64, r32 = res["fp64"][0][0], res["mixed"][0][0]
+    out["blast"] = {"grid": [n, n], "t_final": p.t_final, "cfl": "1/12 (positivity cap)",
+                    "t_reach_probe": t_reach, "probe_steps": args.blast_steps,
+                    "fp64": res["fp64"][1], "mixed": res["mixed"][1],
+                    "rel_l1_rho_mixed_vs_fp64": float(np.abs(r32 - r64).sum() / np.abs(r64).sum())}
+
+    # vortex: refinement sweep up to --vortex-n; the FP64 error falls with
+    # the scheme's order while the FP32 form levels off at its rounding floor
+    sweep = []
+    nv = 128
+    while nv <= args.vortex_n:
+        pv = W.vortex_2d(nv, t_final=1.0)
+        ex = W.vortex_2d(nv, t=1.0).U0[0]
+        vres = {"grid": [nv, nv]}
+        for prec, name in ((0, "fp64"), (1, "mixed")):
+            U, info = run(pv, prec)
+            d = U[0] - ex
+            vres[name] = {"l1_rho": float(np.mean(np.abs(d))), "linf_rho": float(np.max(np.abs(d))),
+                          "steps": info["steps"], "seconds": info["seconds"],
+                          "violations": info["violations"]}
+        vres["l1_ratio_mixed_over_fp64"] = vres["mixed"]["l1_rho"] / vres["fp64"]["l1_rho"]
+        print(f"vortex {nv}^2: {vres}", file=sys.stderr, flush=True)
+        sweep.append(vres)
+        nv *= 2
+    out["vortex"] = {"t_final": 1.0, "cfl": 0.5, "error": "density vs the translated closed form",
+                     "sweep": sweep}
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args, ws):

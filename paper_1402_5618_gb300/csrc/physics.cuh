@@ -39,6 +39,18 @@ __device__ __forceinline__ void zratios(real um2, real um1, real u0, real up1, r
 // are (dmin/tau)^2 q_k = (dmin/d_k)^2 and the constant 1 of eq. (weight)
 // becomes s = (dmin/tau)^2; the normalised weights are unchanged
 // (near a jump of 3e6 the plain q_k reaches 1e52, beyond FP32's range).
+//
+// eps is lifted to the FP32 noise floor of the indicators.  Each FP32
+// average carries a rounding error of up to u max|ubar| (u = 2^-24), so the
+// indicators of a flat stencil are not 0 but up to about 33 (u max|ubar|)^2;
+// eps of eq. (weight), meant to sit above the indicators' zero level and
+// below every real one, becomes eps + 4096 (u max|ubar|)^2 over the stencil
+// (about a hundred times that noise bound).  With the FP64 value alone the
+// weights follow rounding noise wherever the solution is flat to FP32
+// precision, and a grid-scale mode that the nonlinear weights otherwise damp
+// grows from that noise.
+constexpr float FP32_BETA_FLOOR = 4096.0f * 5.9604645e-08f * 5.9604645e-08f;
+
 __device__ __forceinline__ void zratios_scaled(float um2, float um1, float u0, float up1, float up2,
                                                float eps, float &q0, float &q1, float &q2,
                                                float &one) {
@@ -47,6 +59,9 @@ __device__ __forceinline__ void zratios_scaled(float um2, float um1, float u0, f
   float b1 = c13 * sqr(um1 - 2.0f * u0 + up1) + 0.25f * sqr(um1 - up1);
   float b2 = c13 * sqr(u0 - 2.0f * up1 + up2) + 0.25f * sqr(3.0f * u0 - 4.0f * up1 + up2);
   float tau = fabsf(b2 - b0);
+  const float umax = fmaxf(fmaxf(fmaxf(fabsf(um2), fabsf(um1)), fmaxf(fabsf(up1), fabsf(up2))),
+                           fabsf(u0));
+  eps = fmaf(FP32_BETA_FLOOR * umax, umax, eps);
   float d0 = b0 + eps, d1 = b1 + eps, d2 = b2 + eps;
   float dmin = fminf(fminf(d0, d1), d2);
   // branch-free: the numerator is min(tau, dmin); the constant term is 1

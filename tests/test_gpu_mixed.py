@@ -74,10 +74,12 @@ def _run(B, p, prec, t_final=None, max_steps=10**9):
     return U.reshape(p.U0.shape), steps, rc, st
 
 
-@pytest.mark.parametrize("n", [64, 128])
+@pytest.mark.parametrize("n", [64, 128, 512, 768])
 def test_mixed_vortex_error_within_2x_fp64(B, n):
     """Smooth data: L1 density error against the translated closed-form
-    vortex within 2x of the FP64 path's."""
+    vortex within 2x of the FP64 path's, and Linf within 3x.  At 512^2 and
+    above the FP64 error falls below what FP32 resolves where the solution is
+    flat; 768^2 also spans two CTAs per periodic line."""
     p = W.vortex_2d(n, t_final=1.0)
     ex = W.vortex_2d(n, t=1.0).U0
     U64, s64, rc64, _ = _run(B, p, B.PREC_FP64)
@@ -86,6 +88,9 @@ def test_mixed_vortex_error_within_2x_fp64(B, n):
     e64 = np.mean(np.abs(U64[0] - ex[0]))
     e32 = np.mean(np.abs(U32[0] - ex[0]))
     assert e32 <= 2.0 * e64, (e32, e64)
+    i64 = np.max(np.abs(U64[0] - ex[0]))
+    i32 = np.max(np.abs(U32[0] - ex[0]))
+    assert i32 <= 3.0 * i64, (i32, i64)
 
 
 def test_mixed_blast_positivity_and_agreement(B):
@@ -98,6 +103,18 @@ def test_mixed_blast_positivity_and_agreement(B):
     assert rc32 in (0, B.PP_ERR_STEPS)
     rel = np.abs(U32[0] - U64[0]).sum() / np.abs(U64[0]).sum()
     assert rel < 1e-3, rel
+
+
+def test_mixed_blast_mirror_symmetry(B):
+    """The corner blast is symmetric about the diagonal: U(i, j) equals U(j, i)
+    with the momenta swapped.  The mixed form's x sweep and its transposed y
+    sweep run the same arithmetic on mirrored data, so the symmetry holds
+    exactly."""
+    p = W.blast_2d(256, cfl=1 / 12)
+    U, steps, rc, st = _run(B, p, B.PREC_MIXED, t_final=1e9, max_steps=120)
+    assert st.violations == 0 and steps == 120
+    sym = np.stack([U[0].T, U[2].T, U[1].T, U[3].T])
+    assert np.array_equal(U, sym)
 
 
 def test_mixed_1d_riemann_positivity(B):
