@@ -105,6 +105,34 @@ def test_mixed_blast_positivity_and_agreement(B):
     assert rel < 1e-3, rel
 
 
+def test_mixed_full_size_blast_4096_one_step(B):
+    """The benchmark's workload in the benchmark's launch configuration: the
+    4096^2 blast at the positivity CFL, one SSP-RK3 step of the mixed form
+    (x sweep, transposed y sweep, stage combination) against the oracle's
+    FP64 step with the same dt, over the whole grid: each variable within
+    FP32 accuracy of its largest value, and in relative L1 over the blast's
+    neighbourhood (the compact solves couple every cell of a line, so the
+    whole grid moves by tiny amounts)."""
+    p = W.blast_2d(4096)
+    g = _grid(p)
+    s = B.Solver(B.config_from_problem(p, B.PREC_MIXED, cfl_positivity_cap=True))
+    s.set_state(np.ascontiguousarray(p.U0).ravel())
+    dt = s.step()
+    Ug = s.get_state()[0].reshape(p.U0.shape)
+    st = s.stats()
+    s.close()
+    assert st.violations == 0
+    rate = oracle.max_rate(g, p.U0)
+    assert abs(dt - (1.0 / 12.0) / rate) <= 1e-12 * dt
+    Uo = oracle.rk3_step(g, p.U0, dt)
+    for v in range(4):
+        err = np.abs(Ug[v] - Uo[v]).max() / np.abs(Uo[v]).max()
+        assert err <= 1e-5, (v, err)
+        blk = (slice(None), slice(0, 64), slice(0, 64))
+        rel = np.abs(Ug[blk][v] - Uo[blk][v]).sum() / np.abs(Uo[blk][v]).sum()
+        assert rel <= 1e-5, (v, rel)
+
+
 def test_mixed_blast_mirror_symmetry(B):
     """The corner blast is symmetric about the diagonal: U(i, j) equals U(j, i)
     with the momenta swapped.  The mixed form's x sweep and its transposed y
