@@ -184,6 +184,143 @@ __global__ void transpose_planes_kernel(const float *in, float *out, int nx, int
   }
 }
 
+// The same stage combination with 16-byte accesses (nx, ny multiples of 4):
+// thread (tx, ty) of a 32 x 32 tile owns the 4 cells (4 tx .. 4 tx + 3, ty)
+// of the row-major planes, and one float4 of a row of each transposed plane.
+template <int NV>
+__global__ void __launch_bounds__(256, 4)
+    combine_t4_kernel(const float *Ukh, const float *Ukl, const float *U0h, const float *U0l,
+                      const float *Dx, const float *DyT, float *Uoh, float *Uol, float *UT, int nx,
+                      int ny, long long ncell, int stage, float ihx, float ihy, float gg1,
+                      Ctl *ctl) {
+  // D_y tile [v][i][j] in, then (same element, same thread) the new hi part out
+  __shared__ float tile[NV][TT][TT + 1];
+  __shared__ float red_min[8], red_max[8];
+  __shared__ unsigned int red_bad[8];
+  __shared__ unsigned long long red_first[8];
+  if (!ctl->active) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 8 x 32
+  const int i0 = blockIdx.x * TT, j0 = blockIdx.y * TT;
+  // row ty of the transposed tile: i = i0 + ty, j = j0 + 4 tx .. + 3
+  if (i0 + ty < nx && j0 + 4 * tx < ny) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float4 d = *reinterpret_cast<const float4 *>(DyT + v * ncell + (long long)(i0 + ty) * ny + j0 + 4 * tx);
+      tile[v][ty][4 * tx] = d.x;
+      tile[v][ty][4 * tx + 1] = d.y;
+      tile[v][ty][4 * tx + 2] = d.z;
+      tile[v][ty][4 * tx + 3] = d.w;
+    }
+  }
+  __syncthreads();
+  const double dt = ctl->dt;
+  const dfl dtd = {float(dt), float(dt - double(float(dt)))};
+  const dfl third = {0.333333343f, -9.93410776e-09f};
+  const dfl two3 = {0.666666687f, -1.98682155e-08f};
+  float mymin = 3.0e38f, mymax = 0.0f;
+  unsigned int nbad = 0;
+  unsigned long long firstbad = ~0ull;
+  const int j = j0 + ty, ib = i0 + 4 * tx;
+  if (j < ny && ib < nx) {
+    const long long a0 = (long long)j * nx + ib;
+    float Th[NV][4], Tl[NV][4];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const long long a = v * ncell + a0;
+      const float4 dx = *reinterpret_cast<const float4 *>(Dx + a);
+      const float4 uh = *reinterpret_cast<const float4 *>(Ukh + a);
+      const float4 ul = *reinterpret_cast<const float4 *>(Ukl + a);
+      float4 zh = make_float4(0.f, 0.f, 0.f, 0.f), zl = zh;
+      if (stage != 0) {
+        zh = *reinterpret_cast<const float4 *>(U0h + a);
+        zl = *reinterpret_cast<const float4 *>(U0l + a);
+      }
+      const float dxs[4] = {dx.x, dx.y, dx.z, dx.w}, uhs[4] = {uh.x, uh.y, uh.z, uh.w};
+      const float uls[4] = {ul.x, ul.y, ul.z, ul.w}, zhs[4] = {zh.x, zh.y, zh.z, zh.w};
+      const float zls[4] = {zl.x, zl.y, zl.z, zl.w};
+      float oh[4], ol[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float L = dxs[q] + tile[v][4 * tx + q][ty];
+        const dfl s = df_add({uhs[q], uls[q]}, df_mul_f(dtd, L));
+        dfl un;
+        if (stage == 0) {
+          un = s;
+        } else {
+          const dfl u0 = {zhs[q], zls[q]};
+          if (stage == 1) un = df_add(df_mul_f(u0, 0.75f), df_mul_f(s, 0.25f));
+          else un = df_add(df_mul(u0, third), df_mul(s, two3));
+        }
+        oh[q] = un.hi;
+        ol[q] = un.lo;
+        Th[v][q] = un.hi;
+        Tl[v][q] = un.lo;
+        tile[v][4 * tx + q][ty] = un.hi;
+      }
+      *reinterpret_cast<float4 *>(Uoh + a) = make_float4(oh[0], oh[1], oh[2], oh[3]);
+      *reinterpret_cast<float4 *>(Uol + a) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float rho = Th[0][q], mx = Th[1][q], my = Th[2][q], E = Th[NV - 1][q];
+      const dfl rE = df_mul({Th[0][q], Tl[0][q]}, {Th[NV - 1][q], Tl[NV - 1][q]});
+      const dfl m2 = df_add(df_mul({Th[1][q], Tl[1][q]}, {Th[1][q], Tl[1][q]}),
+                            df_mul({Th[2][q], Tl[2][q]}, {Th[2][q], Tl[2][q]}));
+      const dfl gq = df_add(rE, {-0.5f * m2.hi, -0.5f * m2.lo});
+      const bool ok = rho > 0.0f && gq.hi > 0.0f && isfinite(E) && isfinite(mx) && isfinite(my);
+      if (!ok) {
+        ++nbad;
+        firstbad = min(firstbad, (unsigned long long)(a0 + q));
+      } else {
+        mymin = fminf(mymin, rho);
+        const float irho = 1.0f / rho;
+        const float a = sqrtf(gg1 * (gq.hi * irho * irho));
+        const float rate = (fabsf(mx * irho) + a) * ihx + (fabsf(my * irho) + a) * ihy;
+        mymax = fmaxf(mymax, rate);
+      }
+    }
+  }
+  __syncthreads();
+  if (i0 + ty < nx && j0 + 4 * tx < ny) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      *reinterpret_cast<float4 *>(UT + v * ncell + (long long)(i0 + ty) * ny + j0 + 4 * tx) =
+          make_float4(tile[v][ty][4 * tx], tile[v][ty][4 * tx + 1], tile[v][ty][4 * tx + 2],
+                      tile[v][ty][4 * tx + 3]);
+  }
+  // block reduction: warps of 4 rows, then one set of atomics per block
+  const int lin = tx + 8 * ty, wid = lin >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    mymin = fminf(mymin, __shfl_down_sync(0xffffffffu, mymin, d));
+    mymax = fmaxf(mymax, __shfl_down_sync(0xffffffffu, mymax, d));
+    nbad += __shfl_down_sync(0xffffffffu, nbad, d);
+    const unsigned long long fb = __shfl_down_sync(0xffffffffu, firstbad, d);
+    firstbad = fb < firstbad ? fb : firstbad;
+  }
+  if ((lin & 31) == 0) {
+    red_min[wid] = mymin;
+    red_max[wid] = mymax;
+    red_bad[wid] = nbad;
+    red_first[wid] = firstbad;
+  }
+  __syncthreads();
+  if (lin == 0) {
+    for (int y = 1; y < 8; ++y) {
+      mymin = fminf(mymin, red_min[y]);
+      mymax = fmaxf(mymax, red_max[y]);
+      nbad += red_bad[y];
+      firstbad = red_first[y] < firstbad ? red_first[y] : firstbad;
+    }
+    if (mymin < 3.0e38f) atomicMin(&ctl->minrho[stage], dbits((double)mymin));
+    if (stage == 2) atomicMax(&ctl->rate, dbits((double)mymax));
+    if (nbad) {
+      atomicAdd(&ctl->nviol, (unsigned long long)nbad);
+      atomicMin(&ctl->first_bad, firstbad);
+    }
+  }
+}
+
 // Stage combination of the mixed 2-D form on 32 x 32 tiles: L = D_x + D_y
 // (D_y read from its transposed layout), compensated SSP-RK3 update of the
 // hi + lo state, the transposed hi copy of the result for the next y sweep,
@@ -575,6 +712,13 @@ cudaError_t launch_combine_t(const pp_cweno_s *h, const void *Uin, void *Uout, i
   const float *Ukh = hi_of(const_cast<void *>(Uin)), *Ukl = lo_of(h, const_cast<void *>(Uin));
   const float *U0h = hi_of(h->U0), *U0l = lo_of(h, h->U0);
   float *Uoh = hi_of(Uout), *Uol = lo_of(h, Uout);
+  if (h->nx % 4 == 0 && h->ny % 4 == 0) {   // 16-byte rows of every plane
+    combine_t4_kernel<4><<<grid, dim3(8, TT), 0, h->stream>>>(
+        Ukh, Ukl, U0h, U0l, reinterpret_cast<const float *>(h->D), h->DT, Uoh, Uol, h->UT,
+        (int)h->nx, (int)h->ny, h->ncell, stage, (float)(1.0 / h->dx), (float)(1.0 / h->dy),
+        (float)(h->cfg.gamma * (h->cfg.gamma - 1.0)), h->ctl);
+    return cudaGetLastError();
+  }
   combine_t_kernel<4, 8><<<grid, dim3(TT, 8), 0, h->stream>>>(
       Ukh, Ukl, U0h, U0l, reinterpret_cast<const float *>(h->D), h->DT, Uoh, Uol, h->UT, (int)h->nx,
       (int)h->ny, h->ncell, stage, (float)(1.0 / h->dx), (float)(1.0 / h->dy),
