@@ -408,6 +408,7 @@ struct Exch {
   real warp_xn[NV][2][WPV][2];   // x, z after each warp
   Bwd<real> seg_bwd[NV][2];
   double sm[NV][2][6];           // y_f, z_f, y_l, z_l, -a0/b0 (periodic)
+  int nflag;                     // mixed limiter: cells flagged by the FP32 pretest
 };
 
 // Segment planes in shared memory carry one pad word per 128 bytes: segment
@@ -568,6 +569,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       Us[kv * UWP + UH + S::pad(j - 2)] = (i < hi + 2) ? cell_val(kv, i) : real(0);
     }
   }
+  if (tid == 0) ex.nflag = 0;
   if (PER) {
     // stencils of the two "position 0" cells (minus: cell 0, plus: cell n-1)
     // for the Sherman-Morrison row at the far end of each system
@@ -1229,26 +1231,63 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   unsigned int t1 = 0, t2 = 0;
   const real inv12 = real(1) / (real(1) - real(2) * wgl);
   if (args.limiter) {
-    for (int c = tid; c < hi - lo; c += T) {
-      real ub[NV], a[NV], b[NV];
-#pragma unroll
-      for (int kv = 0; kv < NV; ++kv) {
-        ub[kv] = Us[kv * UWP + UH + S::pad(c)];
-        a[kv] = Fm[kv * WP + S::pad(c)];
-        b[kv] = Fp[kv * WP + S::pad(c)];
-      }
-      int f;
-      if constexpr (MIXED) f = limit_cell_mixed<NV>(ub, a, b, wgl, inv12, eps_pos);
-      else f = limit_cell<real, NV>(ub, a, b, wgl, eps_pos, unit_roundoff<real>());
-      if (f) {
+    if constexpr (MIXED) {
+      // FP32 pretest of every cell; the flagged ones (rare) are listed in the
+      // dead weight planes and limited in FP64 in a second pass, so the
+      // per-cell loop carries no FP64 state
+      int *flagged = reinterpret_cast<int *>(Wt);
+      for (int c = tid; c < hi - lo; c += T) {
+        real ub[NV], a[NV], b[NV];
 #pragma unroll
         for (int kv = 0; kv < NV; ++kv) {
-          Fm[kv * WP + S::pad(c)] = a[kv];
-          Fp[kv * WP + S::pad(c)] = b[kv];
+          ub[kv] = Us[kv * UWP + UH + S::pad(c)];
+          a[kv] = Fm[kv * WP + S::pad(c)];
+          b[kv] = Fp[kv * WP + S::pad(c)];
         }
+        if (limit_need_mixed<NV>(ub, a, b, wgl, inv12, eps_pos)) flagged[atomicAdd(&ex.nflag, 1)] = c;
       }
-      t1 += f & 1;
-      t2 += (f >> 1) & 1;
+      __syncthreads();
+      const int nf = ex.nflag;
+      for (int q = tid; q < nf; q += T) {
+        const int c = flagged[q];
+        real ub[NV], a[NV], b[NV];
+#pragma unroll
+        for (int kv = 0; kv < NV; ++kv) {
+          ub[kv] = Us[kv * UWP + UH + S::pad(c)];
+          a[kv] = Fm[kv * WP + S::pad(c)];
+          b[kv] = Fp[kv * WP + S::pad(c)];
+        }
+        const int f = limit_cell_mixed_fp64<NV>(ub, a, b, wgl, eps_pos);
+        if (f) {
+#pragma unroll
+          for (int kv = 0; kv < NV; ++kv) {
+            Fm[kv * WP + S::pad(c)] = a[kv];
+            Fp[kv * WP + S::pad(c)] = b[kv];
+          }
+        }
+        t1 += f & 1;
+        t2 += (f >> 1) & 1;
+      }
+    } else {
+      for (int c = tid; c < hi - lo; c += T) {
+        real ub[NV], a[NV], b[NV];
+#pragma unroll
+        for (int kv = 0; kv < NV; ++kv) {
+          ub[kv] = Us[kv * UWP + UH + S::pad(c)];
+          a[kv] = Fm[kv * WP + S::pad(c)];
+          b[kv] = Fp[kv * WP + S::pad(c)];
+        }
+        const int f = limit_cell<real, NV>(ub, a, b, wgl, eps_pos, unit_roundoff<real>());
+        if (f) {
+#pragma unroll
+          for (int kv = 0; kv < NV; ++kv) {
+            Fm[kv * WP + S::pad(c)] = a[kv];
+            Fp[kv * WP + S::pad(c)] = b[kv];
+          }
+        }
+        t1 += f & 1;
+        t2 += (f >> 1) & 1;
+      }
     }
   }
   // ---------------------------------------------------------------- flux

@@ -330,39 +330,11 @@ __device__ __forceinline__ int limit_cell(const real *ub, real *um, real *up, re
 // allowances; only cells that may need limiting compute the scaling factors
 // theta_1, theta_2 in FP64 (with the FP32 allowance, since the limited faces
 // are stored in FP32).  Returns the limiter flags.
-// the FP64 factors of a cell that may need limiting: rare, so kept out of
-// line (its FP64 registers do not count against the line kernel's hot
-// path); the states travel by value
+// The mixed form's FP32 pretest of a cell: true when the FP64 limiter might
+// change its face values (the caller then runs limit_cell_fp64 on it)
 template <int NV>
-struct LimStates {
-  float b[NV], m[NV], p[NV];
-  int flags;
-};
-
-template <int NV>
-__device__ __noinline__ LimStates<NV> limit_cell_fp64(LimStates<NV> s, float wgl, float eps,
-                                                      float uf) {
-  double b[NV], m[NV], p[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    b[k] = s.b[k];
-    m[k] = s.m[k];
-    p[k] = s.p[k];
-  }
-  s.flags = limit_cell<double, NV>(b, m, p, (double)wgl, (double)eps, (double)uf);
-  if (s.flags) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      s.m[k] = (float)m[k];
-      s.p[k] = (float)p[k];
-    }
-  }
-  return s;
-}
-
-template <int NV>
-__device__ __forceinline__ int limit_cell_mixed(const float *ub, float *um, float *up, float wgl,
-                                                float inv12, float eps) {
+__device__ __forceinline__ bool limit_need_mixed(const float *ub, const float *um, const float *up,
+                                                 float wgl, float inv12, float eps) {
   const float uf = 5.9604645e-08f;
   float w3[NV];   // the interior quadrature point implied by the cell average
 #pragma unroll
@@ -385,22 +357,32 @@ __device__ __forceinline__ int limit_cell_mixed(const float *ub, float *um, floa
       32.0f * uf * ((fabsf(ub[NV - 1]) + emx) * (fabsf(ub[0]) + rmx) + sm);
   need = need | (energy_form<float, NV>(um, eps) < eta2) |
          (energy_form<float, NV>(up, eps) < eta2) | (energy_form<float, NV>(w3, eps) < eta2);
-  if (!need) return 0;
-  LimStates<NV> st;
+  return need;
+}
+
+// The FP64 limiter of a flagged cell of the mixed form, on FP32 face values
+// limited in place (with the FP32 round-off allowance: the limited faces are
+// stored in FP32).  Returns the limiter flags.
+template <int NV>
+__device__ __forceinline__ int limit_cell_mixed_fp64(const float *ub, float *um, float *up,
+                                                     float wgl, float eps) {
+  const double uf = 5.9604645e-08;
+  double b[NV], m[NV], p[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    st.b[k] = ub[k];
-    st.m[k] = um[k];
-    st.p[k] = up[k];
+    b[k] = ub[k];
+    m[k] = um[k];
+    p[k] = up[k];
   }
-  st.flags = 0;
-  st = limit_cell_fp64<NV>(st, wgl, eps, uf);
+  const int f = limit_cell<double, NV>(b, m, p, (double)wgl, (double)eps, uf);
+  if (f) {
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    um[k] = st.m[k];
-    up[k] = st.p[k];
+    for (int k = 0; k < NV; ++k) {
+      um[k] = (float)m[k];
+      up[k] = (float)p[k];
+    }
   }
-  return st.flags;
+  return f;
 }
 
 }  // namespace ppk
