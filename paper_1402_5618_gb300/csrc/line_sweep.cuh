@@ -408,7 +408,6 @@ struct Exch {
   real warp_xn[NV][2][WPV][2];   // x, z after each warp
   Bwd<real> seg_bwd[NV][2];
   double sm[NV][2][6];           // y_f, z_f, y_l, z_l, -a0/b0 (periodic)
-  int nflag;                     // mixed limiter: cells flagged by the FP32 pretest
 };
 
 // Segment planes in shared memory carry one pad word per 128 bytes: segment
@@ -569,7 +568,6 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       Us[kv * UWP + UH + S::pad(j - 2)] = (i < hi + 2) ? cell_val(kv, i) : real(0);
     }
   }
-  if (tid == 0) ex.nflag = 0;
   if (PER) {
     // stencils of the two "position 0" cells (minus: cell 0, plus: cell n-1)
     // for the Sherman-Morrison row at the far end of each system
@@ -1232,11 +1230,13 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   const real inv12 = real(1) / (real(1) - real(2) * wgl);
   if (args.limiter) {
     if constexpr (MIXED) {
-      // FP32 pretest of every cell; the flagged ones (rare) are listed in the
-      // dead weight planes and limited in FP64 in a second pass, so the
-      // per-cell loop carries no FP64 state
-      int *flagged = reinterpret_cast<int *>(Wt);
-      for (int c = tid; c < hi - lo; c += T) {
+      // FP32 pretest of every cell of this thread; the flagged ones (rare)
+      // are limited in FP64 in a second loop, so the pretest loop carries no
+      // FP64 state
+      static_assert(SEG <= 32 * T, "one mask bit per cell of a thread");
+      unsigned int mask = 0;
+#pragma unroll 1
+      for (int q = 0, c = tid; c < hi - lo; ++q, c += T) {
         real ub[NV], a[NV], b[NV];
 #pragma unroll
         for (int kv = 0; kv < NV; ++kv) {
@@ -1244,12 +1244,13 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
           a[kv] = Fm[kv * WP + S::pad(c)];
           b[kv] = Fp[kv * WP + S::pad(c)];
         }
-        if (limit_need_mixed<NV>(ub, a, b, wgl, inv12, eps_pos)) flagged[atomicAdd(&ex.nflag, 1)] = c;
+        if (limit_need_mixed<NV>(ub, a, b, wgl, inv12, eps_pos)) mask |= 1u << q;
       }
-      __syncthreads();
-      const int nf = ex.nflag;
-      for (int q = tid; q < nf; q += T) {
-        const int c = flagged[q];
+#pragma unroll 1
+      while (mask) {
+        const int q = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int c = tid + q * T;
         real ub[NV], a[NV], b[NV];
 #pragma unroll
         for (int kv = 0; kv < NV; ++kv) {
