@@ -1229,66 +1229,49 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   unsigned int t1 = 0, t2 = 0;
   const real inv12 = real(1) / (real(1) - real(2) * wgl);
   if (args.limiter) {
-    if constexpr (MIXED) {
-      // FP32 pretest of every cell of this thread; the flagged ones (rare)
-      // are limited in FP64 in a second loop, so the pretest loop carries no
-      // FP64 state
-      static_assert(SEG <= 32 * T, "one mask bit per cell of a thread");
-      unsigned int mask = 0;
+    // FP32 pretest of every cell of this thread (a superset of the cells
+    // the exact test limits: its thresholds carry twice the FP32 round-off
+    // allowance, which covers the FP32 evaluation and, in the FP64 form, the
+    // rounding of the inputs to FP32); the flagged cells (rare) are limited
+    // exactly in a second loop, so the pretest loop carries no FP64 state
+    static_assert(SEG <= 32 * T, "one mask bit per cell of a thread");
+    unsigned int mask = 0;
+    const float wgl_f = float(wgl), inv12_f = float(inv12), eps_f = float(eps_pos);
 #pragma unroll 1
-      for (int q = 0, c = tid; c < hi - lo; ++q, c += T) {
-        real ub[NV], a[NV], b[NV];
+    for (int q = 0, c = tid; c < hi - lo; ++q, c += T) {
+      float ub[NV], a[NV], b[NV];
 #pragma unroll
-        for (int kv = 0; kv < NV; ++kv) {
-          ub[kv] = Us[kv * UWP + UH + S::pad(c)];
-          a[kv] = Fm[kv * WP + S::pad(c)];
-          b[kv] = Fp[kv * WP + S::pad(c)];
-        }
-        if (limit_need_mixed<NV>(ub, a, b, wgl, inv12, eps_pos)) mask |= 1u << q;
+      for (int kv = 0; kv < NV; ++kv) {
+        ub[kv] = float(Us[kv * UWP + UH + S::pad(c)]);
+        a[kv] = float(Fm[kv * WP + S::pad(c)]);
+        b[kv] = float(Fp[kv * WP + S::pad(c)]);
       }
+      if (limit_need_mixed<NV>(ub, a, b, wgl_f, inv12_f, eps_f)) mask |= 1u << q;
+    }
 #pragma unroll 1
-      while (mask) {
-        const int q = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const int c = tid + q * T;
-        real ub[NV], a[NV], b[NV];
+    while (mask) {
+      const int q = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int c = tid + q * T;
+      real ub[NV], a[NV], b[NV];
+#pragma unroll
+      for (int kv = 0; kv < NV; ++kv) {
+        ub[kv] = Us[kv * UWP + UH + S::pad(c)];
+        a[kv] = Fm[kv * WP + S::pad(c)];
+        b[kv] = Fp[kv * WP + S::pad(c)];
+      }
+      int f;
+      if constexpr (MIXED) f = limit_cell_mixed_fp64<NV>(ub, a, b, wgl, eps_pos);
+      else f = limit_cell<real, NV>(ub, a, b, wgl, eps_pos, unit_roundoff<real>());
+      if (f) {
 #pragma unroll
         for (int kv = 0; kv < NV; ++kv) {
-          ub[kv] = Us[kv * UWP + UH + S::pad(c)];
-          a[kv] = Fm[kv * WP + S::pad(c)];
-          b[kv] = Fp[kv * WP + S::pad(c)];
+          Fm[kv * WP + S::pad(c)] = a[kv];
+          Fp[kv * WP + S::pad(c)] = b[kv];
         }
-        const int f = limit_cell_mixed_fp64<NV>(ub, a, b, wgl, eps_pos);
-        if (f) {
-#pragma unroll
-          for (int kv = 0; kv < NV; ++kv) {
-            Fm[kv * WP + S::pad(c)] = a[kv];
-            Fp[kv * WP + S::pad(c)] = b[kv];
-          }
-        }
-        t1 += f & 1;
-        t2 += (f >> 1) & 1;
       }
-    } else {
-      for (int c = tid; c < hi - lo; c += T) {
-        real ub[NV], a[NV], b[NV];
-#pragma unroll
-        for (int kv = 0; kv < NV; ++kv) {
-          ub[kv] = Us[kv * UWP + UH + S::pad(c)];
-          a[kv] = Fm[kv * WP + S::pad(c)];
-          b[kv] = Fp[kv * WP + S::pad(c)];
-        }
-        const int f = limit_cell<real, NV>(ub, a, b, wgl, eps_pos, unit_roundoff<real>());
-        if (f) {
-#pragma unroll
-          for (int kv = 0; kv < NV; ++kv) {
-            Fm[kv * WP + S::pad(c)] = a[kv];
-            Fp[kv * WP + S::pad(c)] = b[kv];
-          }
-        }
-        t1 += f & 1;
-        t2 += (f >> 1) & 1;
-      }
+      t1 += f & 1;
+      t2 += (f >> 1) & 1;
     }
   }
   // ---------------------------------------------------------------- flux

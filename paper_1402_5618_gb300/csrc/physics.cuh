@@ -330,8 +330,9 @@ __device__ __forceinline__ int limit_cell(const real *ub, real *um, real *up, re
 // allowances; only cells that may need limiting compute the scaling factors
 // theta_1, theta_2 in FP64 (with the FP32 allowance, since the limited faces
 // are stored in FP32).  Returns the limiter flags.
-// The mixed form's FP32 pretest of a cell: true when the FP64 limiter might
-// change its face values (the caller then runs limit_cell_fp64 on it)
+// FP32 pretest of a cell: true when the exact (FP64) limiter might change
+// its face values; the caller then runs the exact limiter on it.  Used by
+// both forms (the FP64 form passes its values rounded to FP32).
 template <int NV>
 __device__ __forceinline__ bool limit_need_mixed(const float *ub, const float *um, const float *up,
                                                  float wgl, float inv12, float eps) {
@@ -357,7 +358,9 @@ __device__ __forceinline__ bool limit_need_mixed(const float *ub, const float *u
       32.0f * uf * ((fabsf(ub[NV - 1]) + emx) * (fabsf(ub[0]) + rmx) + sm);
   need = need | (energy_form<float, NV>(um, eps) < eta2) |
          (energy_form<float, NV>(up, eps) < eta2) | (energy_form<float, NV>(w3, eps) < eta2);
-  return need;
+  // magnitudes beyond FP32's range (or NaN) make the allowance non-finite:
+  // such a cell always goes to the exact test
+  return need | !(eta2 <= 3.0e38f);
 }
 
 // The FP64 limiter of a flagged cell of the mixed form, on FP32 face values
