@@ -76,7 +76,9 @@ typedef struct {
   int bc[4];               /* pp_bc_t of x-lo, x-hi, y-lo, y-hi */
   int precision;           /* pp_prec_t */
   double gl_weight;        /* Gauss-Lobatto end weight omega_hat_1 of the limiter, Sec. 2.4 (1/12) */
-  double eps_weno;         /* epsilon of the WENO-Z weights, eq. (weight) (1e-13) */
+  double eps_weno;         /* epsilon of the WENO-Z weights, eq. (weight) (1e-13); the mixed
+                              form adds 4096 (u max|ubar|)^2 over each 5-cell stencil
+                              (u = 2^-24), the FP32 rounding floor of the indicators */
   double eps_pos;          /* cap of the limiter epsilon, Sec. 2.4 step 1 (1e-13) */
   int cfl_positivity_cap;  /* 1: use min(cfl, gl_weight), the bound of eq. (CFL-CD) */
   int limiter;             /* 1: Zhang-Shu limiter on (default); 0: off */
