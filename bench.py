@@ -270,8 +270,50 @@ def run_native(args, ws, rank, local):
         sv.close()
         acc[prec] = float(np.mean(np.abs(Uv[0] - ex)))
 
+    # batches of uneven problems in one handle each (the batch path of the
+    # C ABI: lines grouped by cluster size, one launch per group and stage)
+    batches = {}
+    if args.batches:
+        # the 1-D set without the problems whose data open an exact vacuum
+        # (u_R - u_L >= 2 (a_L + a_R) / (gamma - 1)): a vacuum cell is outside
+        # G, the problem stops, and its lines would drop out of the timed work
+        def opens_vacuum(q):
+            g = q.gamma
+            ends = []
+            for c in (0, q.nx - 1):
+                rho, m, E = q.U0[:, 0, c] if q.U0.ndim == 3 else q.U0[:, c]
+                u = m / rho
+                pr = (g - 1.0) * (E - 0.5 * rho * u * u)
+                ends.append((u, np.sqrt(g * pr / rho)))
+            (ul, al), (ur, ar) = ends
+            return ur - ul >= 2.0 * (al + ar) / (g - 1.0)
+        rb_all = W.riemann_batch()
+        rb = [q for q in rb_all if not opens_vacuum(q)]
+        for q in rb:   # the first-order positivity CFL 1/2 times the end weight
+            q.cfl = 1.0 / 24.0
+        for name, probs, steps in (("riemann_1d", rb, 20), ("quadrant_2d", W.quadrant_batch(), 6)):
+            U0b = np.concatenate([np.ascontiguousarray(q.U0).ravel() for q in probs])
+            cells = int(sum(q.nx * q.ny for q in probs))
+            row = {"problems": len(probs), "cells": cells}
+            for prec, pname in ((1, "mixed"), (0, "fp64")):
+                sb = B.Solver(None, batch=[B.config_from_problem(q, prec, cfl_positivity_cap=True)
+                                           for q in probs], stream=stream)
+                sb.set_state(U0b)
+                sb.enqueue_steps(3)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                sb.enqueue_steps(steps)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                ms = ev0.elapsed_time(ev1)
+                stb = sb.stats()
+                sb.close()
+                row[pname] = {"value": cells * 3 * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
+                              "ms_per_step": ms / steps, "violations": int(stb.violations)}
+            batches[name] = row
+
     return dict(results=results, ncell=ncell, e2e_s=e2e_s, acc=acc,
-                state_bytes=U0.nbytes)
+                state_bytes=U0.nbytes, batches=batches)
 
 
 def _roofline(r, prec, ncell, hbm_peak, peak_kind):
@@ -359,6 +401,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batches", type=int, default=1, help="also time the batch workloads (0: skip)")
     ap.add_argument("--profile-only", choices=["mixed", "fp64"], default=None,
                     help="only run --steps steps of the blast on an --n^2 grid (for ncu)")
     ap.add_argument("--n", type=int, default=N_GRID)
@@ -426,6 +469,12 @@ def main():
                          "ratio_mixed_over_fp64": out["acc"][1] / out["acc"][0]},
             "positivity_violations": int(rm["violations"] + rd["violations"]),
         }
+        if out["batches"]:
+            line["batches"] = {"note": "seeded batches of uneven problems at the positivity CFL "
+                                       "(1/24 for the 1-D set, 1/12 for the 2-D set): the 4096 1-D "
+                                       "Riemann problems of 256-8192 cells less those opening an "
+                                       "exact vacuum, 256 2-D four-quadrant problems of "
+                                       "128^2-1024^2", **out["batches"]}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -106,7 +106,7 @@ struct SweepArgs {
   // batched launch: line table and problem descriptors (nullptr: one problem)
   const LineRef *lines;
   const ProbDesc *probs;
-  int xdir;           // batched launch: 1 x lines, 0 y lines
+  int xdir;           // batched launch: 1 x lines, 0 y lines, 2 rows of the transposed planes
   long long nvals;    // batched mixed form: values per hi block (lo block follows)
 };
 
@@ -120,10 +120,14 @@ __device__ __forceinline__ void bind_line(SweepArgs &a, long long &line) {
   line = lr.line;
   a.ctl = a.ctl + lr.prob;
   a.ncell = pd.ncell;
-  if (a.xdir) {
+  if (a.xdir == 1) {
     a.n = pd.nx; a.cell_stride = 1; a.line_stride = pd.nx;
     a.bclo = pd.bc[0]; a.bchi = pd.bc[1];
     a.h = pd.dx; a.h_other = NV == 4 ? pd.dy : 0.0; a.ih = pd.idx;
+  } else if (a.xdir == 2) {   // a row of the problem's transposed planes: a y line
+    a.n = pd.ny; a.cell_stride = 1; a.line_stride = pd.ny;
+    a.bclo = pd.bc[2]; a.bchi = pd.bc[3];
+    a.h = pd.dy; a.h_other = pd.dx; a.ih = pd.idy;
   } else {
     a.n = pd.ny; a.cell_stride = pd.nx; a.line_stride = 1;
     a.bclo = pd.bc[2]; a.bchi = pd.bc[3];

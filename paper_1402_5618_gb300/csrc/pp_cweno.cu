@@ -167,12 +167,10 @@ __global__ void batch_reduce_kernel(const void *Uv, const float *lo, const ProbD
 constexpr int TT = 32;   // tile edge
 
 // out[v][i][j] = in[v][j][i] for nv planes of ny x nx
-__global__ void transpose_planes_kernel(const float *in, float *out, int nx, int ny, long long ncell) {
+// one 32 x 32 tile of a plane (nx x ny, row-major) into the transposed plane
+__device__ __forceinline__ void transpose_tile(const float *src, float *dst, int i0, int j0, int nx,
+                                               int ny) {
   __shared__ float tile[TT][TT + 1];
-  const int v = blockIdx.z;
-  const int i0 = blockIdx.x * TT, j0 = blockIdx.y * TT;
-  const float *src = in + v * ncell;
-  float *dst = out + v * ncell;
   for (int r = threadIdx.y; r < TT; r += blockDim.y) {
     int j = j0 + r, i = i0 + threadIdx.x;
     if (j < ny && i < nx) tile[r][threadIdx.x] = src[(long long)j * nx + i];
@@ -182,6 +180,24 @@ __global__ void transpose_planes_kernel(const float *in, float *out, int nx, int
     int i = i0 + r, j = j0 + threadIdx.x;
     if (i < nx && j < ny) dst[(long long)i * ny + j] = tile[threadIdx.x][r];
   }
+}
+
+__global__ void transpose_planes_kernel(const float *in, float *out, int nx, int ny, long long ncell) {
+  const int v = blockIdx.z;
+  transpose_tile(in + v * ncell, out + v * ncell, blockIdx.x * TT, blockIdx.y * TT, nx, ny);
+}
+
+// batched problems: one block per (tile of a problem, variable)
+struct TileRef {
+  int prob, i0, j0, pad;
+};
+
+__global__ void transpose_planes_b_kernel(const float *in, float *out, const TileRef *tiles,
+                                          const ProbDesc *probs) {
+  const TileRef t = tiles[blockIdx.x];
+  const ProbDesc pd = probs[t.prob];
+  const long long o = pd.off + blockIdx.y * pd.ncell;
+  transpose_tile(in + o, out + o, t.i0, t.j0, pd.nx, pd.ny);
 }
 
 // The same stage combination with 16-byte accesses (nx, ny multiples of 4):
@@ -326,18 +342,17 @@ __global__ void __launch_bounds__(256, 4)
 // hi + lo state, the transposed hi copy of the result for the next y sweep,
 // and the grid-wide reductions (min rho, max rate, cells outside G).
 template <int NV, int RY>
-__global__ void __launch_bounds__(TT *RY, 6)
-    combine_t_kernel(const float *Ukh, const float *Ukl, const float *U0h, const float *U0l,
-                     const float *Dx, const float *DyT, float *Uoh, float *Uol, float *UT, int nx,
-                     int ny, long long ncell, int stage, float ihx, float ihy, float gg1,
-                     Ctl *ctl) {
+__device__ __forceinline__ void combine_tile(int i0, int j0, const float *Ukh, const float *Ukl,
+                                             const float *U0h, const float *U0l, const float *Dx,
+                                             const float *DyT, float *Uoh, float *Uol, float *UT,
+                                             int nx, int ny, long long ncell, int stage, float ihx,
+                                             float ihy, float gg1, Ctl *ctl) {
   // D_y tile in, then (same element, same thread) the new hi part out
   __shared__ float tile[NV][TT][TT + 1];
   __shared__ float red_min[RY], red_max[RY];
   __shared__ unsigned int red_bad[RY];
   __shared__ unsigned long long red_first[RY];
   if (!ctl->active) return;
-  const int i0 = blockIdx.x * TT, j0 = blockIdx.y * TT;
   // D_y tile: DyT[v][i][j], read along j
 #pragma unroll
   for (int v = 0; v < NV; ++v)
@@ -441,6 +456,32 @@ __global__ void __launch_bounds__(TT *RY, 6)
   }
 }
 
+template <int NV, int RY>
+__global__ void __launch_bounds__(TT *RY, 6)
+    combine_t_kernel(const float *Ukh, const float *Ukl, const float *U0h, const float *U0l,
+                     const float *Dx, const float *DyT, float *Uoh, float *Uol, float *UT, int nx,
+                     int ny, long long ncell, int stage, float ihx, float ihy, float gg1,
+                     Ctl *ctl) {
+  combine_tile<NV, RY>(blockIdx.x * TT, blockIdx.y * TT, Ukh, Ukl, U0h, U0l, Dx, DyT, Uoh, Uol,
+                       UT, nx, ny, ncell, stage, ihx, ihy, gg1, ctl);
+}
+
+// batched problems: one block per tile of a problem, each problem at its
+// offset in every buffer, with its own grid and control block
+template <int NV, int RY>
+__global__ void __launch_bounds__(TT *RY, 6)
+    combine_tb_kernel(const float *Ukh, const float *Ukl, const float *U0h, const float *U0l,
+                      const float *Dx, const float *DyT, float *Uoh, float *Uol, float *UT,
+                      const TileRef *tiles, const ProbDesc *probs, int stage, float gg1,
+                      Ctl *ctls) {
+  const TileRef t = tiles[blockIdx.x];
+  const ProbDesc pd = probs[t.prob];
+  const long long o = pd.off;
+  combine_tile<NV, RY>(t.i0, t.j0, Ukh + o, Ukl + o, U0h + o, U0l + o, Dx + o, DyT + o, Uoh + o,
+                       Uol + o, UT + o, pd.nx, pd.ny, pd.ncell, stage, (float)pd.idx,
+                       (float)pd.idy, gg1, ctls + t.prob);
+}
+
 // FP64 planes <-> FP32 hi / lo plane pairs (mixed form state)
 __global__ void split_kernel(const double *in, float *hi, float *lo, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -503,6 +544,7 @@ struct LineGroup {
   int R;
   bool periodic;
   bool xdir;
+  bool trans = false;         // y lines as rows of the transposed planes (mixed 2-D batches)
   LineRef *lines = nullptr;   // device
   long long nlines = 0;
 };
@@ -520,6 +562,9 @@ struct pp_cweno_s {
   cudaGraphExec_t graph = nullptr;
   long long launches_per_step = 0;
   int m = 8;                  // rows per thread chunk of the line kernels (autotuned)
+  bool btrans = false;        // mixed 2-D batch: transposed y sweeps and batched combination
+  TileRef *tiles = nullptr;   // device: the 32 x 32 tiles of every problem (btrans)
+  long long ntiles = 0;
   // mixed 2-D single problem: transposed hi planes and transposed y-sweep output
   bool ytrans = false;
   float *UT = nullptr, *DT = nullptr;
@@ -678,8 +723,15 @@ cudaError_t launch_group(const pp_cweno_s *h, const LineGroup &g, int mode, cons
   a.R = g.R;
   a.lines = g.lines;
   a.probs = h->probs;
-  a.xdir = g.xdir ? 1 : 0;
+  a.xdir = g.xdir ? 1 : (g.trans ? 2 : 0);
   a.nvals = nvals(h);
+  if (g.trans) {   // rows of the transposed hi planes in, D_y transposed out
+    a.Uh = h->UT;
+    a.Ul = nullptr;
+    a.U0h = a.U0l = a.Uoh = a.Uol = nullptr;
+    a.Din = nullptr;
+    a.Dout = h->DT;
+  }
   a.vn = g.xdir ? 1 : 2;
   a.vt = h->nv == 4 ? (g.xdir ? 2 : 1) : -1;
   return dispatch(h, mode, g.periodic, a, g.nlines, attrs_only);
@@ -726,7 +778,22 @@ cudaError_t launch_combine_t(const pp_cweno_s *h, const void *Uin, void *Uout, i
   return cudaGetLastError();
 }
 
+cudaError_t launch_combine_b(const pp_cweno_s *h, const void *Uin, void *Uout, int stage) {
+  const float *Ukh = hi_of(const_cast<void *>(Uin)), *Ukl = lo_of(h, const_cast<void *>(Uin));
+  const float *U0h = hi_of(h->U0), *U0l = lo_of(h, h->U0);
+  float *Uoh = hi_of(Uout), *Uol = lo_of(h, Uout);
+  combine_tb_kernel<4, 8><<<(unsigned)h->ntiles, dim3(TT, 8), 0, h->stream>>>(
+      Ukh, Ukl, U0h, U0l, reinterpret_cast<const float *>(h->D), h->DT, Uoh, Uol, h->UT, h->tiles,
+      h->probs, stage, (float)(h->cfg.gamma * (h->cfg.gamma - 1.0)), h->ctl);
+  return cudaGetLastError();
+}
+
 cudaError_t transpose_state_hi(const pp_cweno_s *h) {
+  if (h->btrans) {
+    transpose_planes_b_kernel<<<dim3((unsigned)h->ntiles, (unsigned)h->nv), dim3(TT, 8), 0,
+                                h->stream>>>(hi_of(h->U0), h->UT, h->tiles, h->probs);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((h->nx + TT - 1) / TT), (unsigned)((h->ny + TT - 1) / TT), (unsigned)h->nv);
   transpose_planes_kernel<<<grid, dim3(TT, 8), 0, h->stream>>>(hi_of(h->U0), h->UT, (int)h->nx,
                                                                (int)h->ny, h->ncell);
@@ -777,6 +844,16 @@ cudaError_t enqueue_step(pp_cweno_s *h, cudaEvent_t *ev = nullptr, int *nev = nu
       if (h->nv == 4) e = launch_group(h, g, MODE_XSWEEP, Uin, h->U0, nullptr, h->D, nullptr, s);
       else e = launch_group(h, g, MODE_FINAL, Uin, h->U0, nullptr, nullptr, Uout, s);
       if (e != cudaSuccess) return e;
+    }
+    if (h->btrans) {   // mixed 2-D: transposed y rows, then the batched combination
+      for (const LineGroup &g : h->groups) {
+        if (g.xdir) continue;
+        e = launch_group(h, g, MODE_XSWEEP, Uin, h->U0, nullptr, h->DT, nullptr, s);
+        if (e != cudaSuccess) return e;
+      }
+      e = launch_combine_b(h, Uin, Uout, s);
+      if (e != cudaSuccess) return e;
+      continue;
     }
     for (const LineGroup &g : h->groups) {
       if (g.xdir) continue;
@@ -883,8 +960,9 @@ int finish_create(pp_cweno_s *h) {
   if (e == cudaSuccess) e = cudaMalloc(&h->ctl_scratch, sizeof(Ctl) * h->nprob);
   if (e == cudaSuccess) e = cudaMallocHost(&h->hctl, sizeof(Ctl) * h->nprob);
   h->ytrans = is_mixed(h) && h->nv == 4 && !h->batch;
-  if (e == cudaSuccess && h->ytrans) e = cudaMalloc(&h->UT, sizeof(float) * (size_t)nvals(h));
-  if (e == cudaSuccess && h->ytrans) e = cudaMalloc(&h->DT, sizeof(float) * (size_t)nvals(h));
+  const bool tr = h->ytrans || h->btrans;
+  if (e == cudaSuccess && tr) e = cudaMalloc(&h->UT, sizeof(float) * (size_t)nvals(h));
+  if (e == cudaSuccess && tr) e = cudaMalloc(&h->DT, sizeof(float) * (size_t)nvals(h));
   if (e != cudaSuccess) return PP_ERR_CUDA;
   memset(h->hctl, 0, sizeof(Ctl) * h->nprob);
   // kernel attributes (dynamic shared memory, cluster size) are set here,
@@ -907,7 +985,8 @@ int finish_create(pp_cweno_s *h) {
   if (e != cudaSuccess) return PP_ERR_CUDA;
   if (h->batch) {
     h->launches_per_step = 1;
-    for (int s = 0; s < 3; ++s) h->launches_per_step += (long long)h->groups.size();
+    for (int s = 0; s < 3; ++s)
+      h->launches_per_step += (long long)h->groups.size() + (h->btrans ? 1 : 0);
   } else {
     h->launches_per_step = 1 + 3 * (h->ytrans ? 3 : (h->nv == 4 ? 2 : 1));
   }
@@ -1050,6 +1129,8 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
   h->stream = (cudaStream_t)cuda_stream;
   h->nv = c0.ndim == 2 ? 4 : 3;
   h->nprob = (int)nprob;
+  h->btrans = c0.precision == PP_PREC_MIXED && c0.ndim == 2;
+  std::vector<TileRef> tiles;
   long long off = 0, cells = 0;
   // line groups keyed by (direction, cluster size, periodic)
   std::vector<std::vector<LineRef>> glines;
@@ -1060,6 +1141,7 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
     lg.R = R;
     lg.periodic = per;
     lg.xdir = xdir;
+    lg.trans = !xdir && h->btrans;
     h->groups.push_back(lg);
     glines.emplace_back();
     return h->groups.size() - 1;
@@ -1086,6 +1168,9 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
     if (c.ndim == 2) {
       size_t gy = group_of(false, seg_count(d.ny), c.bc[2] == PP_BC_PERIODIC);
       for (int i = 0; i < d.nx; ++i) glines[gy].push_back({p, i});
+      if (h->btrans)
+        for (int j0 = 0; j0 < d.ny; j0 += TT)
+          for (int i0 = 0; i0 < d.nx; i0 += TT) tiles.push_back({p, i0, j0, 0});
     }
   }
   h->ncell = cells;
@@ -1115,6 +1200,12 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
       e = cudaMemcpy(h->groups[g].lines, slines[g].data(), sizeof(LineRef) * slines[g].size(),
                      cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess && h->btrans) {
+    h->ntiles = (long long)tiles.size();
+    e = cudaMalloc(&h->tiles, sizeof(TileRef) * tiles.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->tiles, tiles.data(), sizeof(TileRef) * tiles.size(), cudaMemcpyHostToDevice);
+  }
   int rc = e == cudaSuccess ? finish_create(h) : PP_ERR_CUDA;
   if (rc) {
     pp_cweno_destroy(h);
@@ -1138,7 +1229,7 @@ int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) 
     }
     split_kernel<<<grid_for(nval), 256, 0, h->stream>>>(src, hi_of(h->U0), lo_of(h, h->U0), nval);
     e = cudaGetLastError();
-    if (e == cudaSuccess && h->ytrans) e = transpose_state_hi(h);
+    if (e == cudaSuccess && (h->ytrans || h->btrans)) e = transpose_state_hi(h);
   } else {
     e = cudaMemcpyAsync(h->U0, U, bytes,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
@@ -1559,6 +1650,7 @@ int pp_cweno_destroy(pp_cweno_t h) {
   cudaFree(h->ctl);
   cudaFree(h->ctl_scratch);
   cudaFree(h->probs);
+  cudaFree(h->tiles);
   cudaFree(h->UT);
   cudaFree(h->DT);
   for (auto &g : h->groups) cudaFree(g.lines);

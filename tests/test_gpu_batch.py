@@ -89,3 +89,26 @@ def test_batch_mixed_runs_and_tracks_fp64(B):
     assert rc64 == 0 and rc32 == 0 and st64.violations == 0 and st32.violations == 0
     for a, b in zip(o32, o64):
         assert _rel(a, b)[0] < 1e-4
+
+
+def test_batch_mixed_2d_transposed_path(B):
+    """Mixed 2-D batch (transposed y rows, batched stage combination) of
+    uneven problems -- partial tiles, sides that are not multiples of 4, a
+    periodic vortex beside transmissive quadrants: no violations, each
+    problem close to the FP64 batch, and to the same problem run alone."""
+    st4 = [(1.0, 0.1, 0.0, 1.0), (0.5, 0.0, 0.2, 0.4), (0.2, -0.1, 0.0, 0.1), (0.8, 0.0, -0.2, 0.6)]
+    probs = [W.quadrant_2d(n, st4, t_final=0.02) for n in (40, 130, 600)]
+    probs.append(W.vortex_2d(96, t_final=0.02))
+    for p in probs:
+        p.cfl = 1.0 / 12.0
+    o64, rc64, s64 = _batch_run(B, probs, B.PREC_FP64, max_steps=12)
+    o32, rc32, s32 = _batch_run(B, probs, B.PREC_MIXED, max_steps=12)
+    assert rc32 in (0, B.PP_ERR_STEPS) and s32.violations == 0 and s64.violations == 0
+    for p, a, b in zip(probs, o32, o64):
+        assert np.all(_rel(a, b) < 1e-5), (p.nx, _rel(a, b))
+        s = B.Solver(B.config_from_problem(p, B.PREC_MIXED))
+        s.set_state(np.ascontiguousarray(p.U0).ravel())
+        s.advance(p.t_final, 12, check=False)
+        one = s.get_state()[0].reshape(p.U0.shape)
+        s.close()
+        assert np.all(_rel(a, one) < 1e-5), (p.nx, _rel(a, one))
