@@ -64,7 +64,7 @@ enum {
   PP_ERR_STEPS = 4,        /* advance stopped at max_steps before t_final */
   PP_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
   PP_ERR_CUDA = 6,         /* a CUDA runtime call failed */
-  PP_ERR_UNSUPPORTED = 7   /* configuration outside what this build supports */
+  PP_ERR_UNSUPPORTED = 7   /* configuration outside what this library supports */
 };
 
 typedef struct {

@@ -1668,7 +1668,7 @@ const char *pp_cweno_strerror(int code) {
     case PP_ERR_STEPS: return "max_steps reached before t_final";
     case PP_ERR_TIMEOUT: return "bounded device wait expired";
     case PP_ERR_CUDA: return "CUDA runtime error";
-    case PP_ERR_UNSUPPORTED: return "configuration not supported by this build";
+    case PP_ERR_UNSUPPORTED: return "configuration not supported by this library";
     default: return "unknown error";
   }
 }
