@@ -143,6 +143,12 @@ int pp_cweno_operator(pp_cweno_t h, const double *U_dev, double *L_dev, double e
 /* Statistics; synchronises.  For a batch, sums and extrema over problems. */
 int pp_cweno_stats(pp_cweno_t h, pp_cweno_stats_t *out);
 
+/* Statistics of problem k of a batch (k = 0 for a single problem): its
+ * steps, time, limiter counts and violations (first_bad_cell indexes the
+ * problem's own cells); max_rate and min_rho are not filled (0).
+ * Synchronises. */
+int pp_cweno_problem_stats(pp_cweno_t h, int64_t k, pp_cweno_stats_t *out);
+
 /* Number of problems in the handle and the cell count of problem k. */
 int pp_cweno_num_problems(pp_cweno_t h, int64_t *nprob);
 int pp_cweno_problem_cells(pp_cweno_t h, int64_t k, int64_t *ncell);

@@ -43,7 +43,8 @@ class Stats(C.Structure):
 EXPORTS = [
     "pp_cweno_config_default", "pp_cweno_create", "pp_cweno_create_batch", "pp_cweno_set_state",
     "pp_cweno_get_state", "pp_cweno_step", "pp_cweno_advance", "pp_cweno_enqueue_steps",
-    "pp_cweno_operator", "pp_cweno_stats", "pp_cweno_num_problems", "pp_cweno_problem_cells",
+    "pp_cweno_operator", "pp_cweno_stats", "pp_cweno_problem_stats", "pp_cweno_num_problems",
+    "pp_cweno_problem_cells",
     "pp_cweno_rows_per_chunk",
     "pp_cweno_launches_per_step", "pp_cweno_profile_step", "pp_cweno_fma_peak",
     "pp_cweno_operator_noalloc", "pp_cweno_destroy", "pp_cweno_strerror",
@@ -82,6 +83,7 @@ def lib(build_if_missing: bool = False):
     L.pp_cweno_enqueue_steps.argtypes = [vp, C.c_int64]
     L.pp_cweno_operator.argtypes = [vp, vp, vp, C.c_double]
     L.pp_cweno_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.pp_cweno_problem_stats.argtypes = [vp, C.c_int64, C.POINTER(Stats)]
     L.pp_cweno_num_problems.argtypes = [vp, i64p]
     L.pp_cweno_problem_cells.argtypes = [vp, C.c_int64, i64p]
     L.pp_cweno_launches_per_step.argtypes = [vp, i64p]
@@ -233,6 +235,12 @@ class Solver:
     def stats(self) -> Stats:
         s = Stats()
         _check(lib().pp_cweno_stats(self.h, C.byref(s)), "stats")
+        return s
+
+    def problem_stats(self, k: int) -> Stats:
+        """steps, time, limiter counts and violations of problem k of a batch"""
+        s = Stats()
+        _check(lib().pp_cweno_problem_stats(self.h, k, C.byref(s)), "problem_stats")
         return s
 
     def profile_step(self) -> list[float]:

@@ -1464,6 +1464,23 @@ int pp_cweno_stats(pp_cweno_t h, pp_cweno_stats_t *out) {
   return PP_OK;
 }
 
+int pp_cweno_problem_stats(pp_cweno_t h, int64_t k, pp_cweno_stats_t *out) {
+  if (!h || !out || k < 0 || k >= h->nprob) return PP_ERR_ARG;
+  int rc = pull_ctl(h);
+  if (rc) return rc;
+  const Ctl *c = h->hctl + k;
+  memset(out, 0, sizeof(*out));
+  out->steps = c->step;
+  out->stages = 3 * c->step;
+  out->theta1_active = (int64_t)c->theta1;
+  out->theta2_active = (int64_t)c->theta2;
+  out->violations = (int64_t)c->nviol;
+  out->first_bad_cell = c->nviol ? (int64_t)c->first_bad : -1;
+  out->t = c->t;
+  out->last_dt = c->last_dt;
+  return PP_OK;
+}
+
 int pp_cweno_num_problems(pp_cweno_t h, int64_t *nprob) {
   if (!h || !nprob) return PP_ERR_ARG;
   *nprob = h->nprob;

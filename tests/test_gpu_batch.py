@@ -112,3 +112,21 @@ def test_batch_mixed_2d_transposed_path(B):
         one = s.get_state()[0].reshape(p.U0.shape)
         s.close()
         assert np.all(_rel(a, one) < 1e-5), (p.nx, _rel(a, one))
+
+
+def test_batch_problem_stats(B):
+    """Per-problem statistics of a batch: each problem's own step count (the
+    oracle's, run alone), time and violations; an index out of range is an
+    argument error."""
+    probs = [W.riemann_1d(n, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), t_final=0.02) for n in (64, 300, 1000)]
+    s = B.Solver(None, batch=[B.config_from_problem(p, B.PREC_FP64) for p in probs])
+    s.set_state(np.concatenate([np.ascontiguousarray(p.U0).ravel() for p in probs]))
+    s.advance(0.02)
+    for k, p in enumerate(probs):
+        st = s.problem_stats(k)
+        Uo, to, so, *_ = oracle.advance(_grid(p), p.U0, p.cfl, 0.02)
+        assert st.steps == so and st.t == 0.02 and st.violations == 0 and st.first_bad_cell == -1
+    with pytest.raises(B.PPError) as e:
+        s.problem_stats(len(probs))
+    assert e.value.code == B.PP_ERR_ARG
+    s.close()

@@ -48,6 +48,8 @@ def _flux_scale(p, U):
     ("smooth_1d_1500", lambda: W.random_smooth_1d(1500, stream=52), 2e-6),
     ("jumps_600x530", lambda: W.random_jumps_2d(600, 530, stream=61), 1e-4),
     ("riemann_1300", lambda: W.riemann_1d(1300, (1.0, 0.75, 1.0), (0.125, -0.3, 0.1), bc=(2, 1)), 1e-4),
+    ("smooth_periodic_8192", lambda: W.random_smooth_1d(8192, stream=56), 2e-6),
+    ("jumps_periodic_1100x600", lambda: W.random_jumps_2d(1100, 600, stream=64, bc=(0, 0, 0, 0)), 1e-4),
 ])
 def test_mixed_operator_close_to_oracle(B, name, make, tol):
     p = make()

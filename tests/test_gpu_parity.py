@@ -76,6 +76,9 @@ OPERATOR_CASES_1D = [
     ("leblanc_1000", lambda: W.leblanc(1000)),
     ("n8_periodic", lambda: W.random_smooth_1d(8, stream=54)),
     ("n8_bounded", lambda: W.random_smooth_1d(8, stream=55, periodic=False)),
+    # the longest line: 16 CTAs in one cluster
+    ("smooth_periodic_8192", lambda: W.random_smooth_1d(8192, stream=56)),
+    ("riemann_bounded_8192", lambda: W.riemann_1d(8192, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1))),
 ]
 
 
@@ -94,6 +97,8 @@ OPERATOR_CASES_2D = [
     ("jumps_periodic_96x40", lambda: W.random_jumps_2d(96, 40, stream=62, bc=(0, 0, 0, 0))),
     ("blast_96", lambda: W.blast_2d(96)),
     ("quadrant_1030", lambda: W.quadrant_batch(1, 1030, 1031, stream=63)[0]),
+    # periodic lines of 3 (x) and 2 (y) CTAs: cross-CTA maps and the cyclic correction
+    ("jumps_periodic_1100x600", lambda: W.random_jumps_2d(1100, 600, stream=64, bc=(0, 0, 0, 0))),
 ]
 
 
@@ -227,6 +232,23 @@ def test_full_size_sampled_operator_4096(B):
 
 
 # ------------------------------------------------------------ API behaviour
+def test_size_limits(B):
+    """Lines of 8 to 8192 cells (one to sixteen CTAs per cluster); outside
+    that range creation fails with a code, nothing is launched."""
+    cfg = B.make_config(ndim=1, nx=8193)
+    with pytest.raises(B.PPError) as e:
+        B.Solver(cfg)
+    assert e.value.code == B.PP_ERR_UNSUPPORTED
+    cfg = B.make_config(ndim=1, nx=7)
+    with pytest.raises(B.PPError) as e:
+        B.Solver(cfg)
+    assert e.value.code == B.PP_ERR_ARG
+    cfg = B.make_config(ndim=2, nx=64, ny=8193)
+    with pytest.raises(B.PPError) as e:
+        B.Solver(cfg)
+    assert e.value.code == B.PP_ERR_UNSUPPORTED
+
+
 def test_set_state_rejects_inadmissible(B):
     p = W.random_smooth_1d(64, stream=3)
     U = p.U0.copy()
