@@ -34,6 +34,7 @@ class Grid(C.Structure):
         ("dx", C.c_double), ("dy", C.c_double), ("gamma", C.c_double),
         ("bc", C.c_int * 4), ("gl_weight", C.c_double), ("eps_weno", C.c_double),
         ("eps_pos", C.c_double), ("limiter", C.c_int), ("linear_weights", C.c_int),
+        ("flux", C.c_int),
     ]
 
 
@@ -74,6 +75,7 @@ def lib():
             L.orc_cyclic.argtypes = [C.c_long, dp, dp, dp, dp, dp, C.c_int]
             L.orc_recon_scalar.argtypes = [C.c_long, dp, C.c_int, C.c_double, C.c_int, dp, dp]
             L.orc_hllc.argtypes = [C.c_int, C.c_double, dp, dp, dp]
+            L.orc_llf.argtypes = [C.c_int, C.c_double, dp, dp, dp]
             L.orc_flux.argtypes = [C.c_int, C.c_double, dp, dp]
             L.orc_hllc_batch.argtypes = [C.c_int, C.c_double, C.c_long, dp, dp, dp]
             L.orc_limit_cell.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, dp, dp, dp]
@@ -112,7 +114,7 @@ def _f64(x) -> np.ndarray:
 def make_grid(ndim: int, nx: int, ny: int = 1, dx: float = 1.0, dy: float = 1.0,
               gamma: float = 1.4, bc=(0, 0, 0, 0), gl_weight: float = 1.0 / 12.0,
               eps_weno: float = 1e-13, eps_pos: float = 1e-13, limiter: bool = True,
-              linear_weights: bool = False) -> Grid:
+              linear_weights: bool = False, flux: int = 0) -> Grid:
     g = Grid()
     g.ndim, g.nx, g.ny = ndim, nx, (ny if ndim == 2 else 1)
     g.dx, g.dy, g.gamma = dx, dy, gamma
@@ -120,6 +122,7 @@ def make_grid(ndim: int, nx: int, ny: int = 1, dx: float = 1.0, dy: float = 1.0,
         g.bc[k] = int(bc[k])
     g.gl_weight, g.eps_weno, g.eps_pos = gl_weight, eps_weno, eps_pos
     g.limiter, g.linear_weights = int(limiter), int(linear_weights)
+    g.flux = int(flux)
     return g
 
 
@@ -169,6 +172,13 @@ def hllc(Ul, Ur, gamma=1.4) -> np.ndarray:
     Ul, Ur = _f64(Ul), _f64(Ur)
     F = np.zeros(len(Ul))
     lib().orc_hllc(len(Ul), gamma, _p(Ul), _p(Ur), _p(F))
+    return F
+
+
+def llf(Ul, Ur, gamma=1.4) -> np.ndarray:
+    Ul, Ur = _f64(Ul), _f64(Ur)
+    F = np.zeros(len(Ul))
+    lib().orc_llf(len(Ul), gamma, _p(Ul), _p(Ur), _p(F))
     return F
 
 

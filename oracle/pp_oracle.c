@@ -29,6 +29,10 @@
  *  - Gauss-Lobatto end weight omega_hat_1 = 1/12 (M = 4 points) by default.
  *  - 2-D: dimension by dimension, L = L_x + L_y, HLLC at face centres with
  *    the tangential momentum carried by the contact.
+ *  - Lax-Friedrichs flux (named in Sec. 3 as a way to control the
+ *    oscillations of the near-vacuum double rarefaction): the local form,
+ *    the dissipation coefficient being the larger |u| + a of the two face
+ *    states; an alternative to HLLC selected per grid.
  */
 #include "pp_oracle.h"
 
@@ -334,6 +338,18 @@ void orc_hllc(int nv, double gamma, const double *Ul, const double *Ur, double *
   }
 }
 
+/* Sec. 3 (double rarefaction remark): the Lax-Friedrichs flux, here its
+ * local form with the largest signal speed |u| + a of the two face states */
+void orc_llf(int nv, double gamma, const double *Ul, const double *Ur, double *F) {
+  double Fl[4], Fr[4];
+  orc_flux(nv, gamma, Ul, Fl);
+  orc_flux(nv, gamma, Ur, Fr);
+  double al = fabs(Ul[1] / Ul[0]) + sqrt(gamma * pressure(nv, gamma, Ul) / Ul[0]);
+  double ar = fabs(Ur[1] / Ur[0]) + sqrt(gamma * pressure(nv, gamma, Ur) / Ur[0]);
+  double alpha = fmax(al, ar);
+  for (int k = 0; k < nv; ++k) F[k] = 0.5 * (Fl[k] + Fr[k]) - 0.5 * alpha * (Ur[k] - Ul[k]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sec. 2.4: the positivity-preserving limiter, steps 1-4.                    */
 /* ------------------------------------------------------------------------ */
@@ -503,7 +519,8 @@ static int line_operator(const orc_grid *g, int nv, long n, const double *line, 
       } else {
         for (int v = 0; v < nv; ++v) { Ul[v] = um[v * n + f - 1]; Ur[v] = up[v * n + f]; }
       }
-      orc_hllc(nv, g->gamma, Ul, Ur, F);
+      if (g->flux) orc_llf(nv, g->gamma, Ul, Ur, F);
+      else orc_hllc(nv, g->gamma, Ul, Ur, F);
       for (int v = 0; v < nv; ++v) fl[v * (n + 1) + f] = F[v];
     }
     /* eq. (1DEulerFV-b) */

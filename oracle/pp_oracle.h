@@ -32,6 +32,7 @@ typedef struct {
   double eps_pos;        /* cap of the limiter epsilon (1e-13), Sec. 2.4 step 1 */
   int    limiter;        /* 1: Zhang-Shu limiter on, 0: off (tests only) */
   int    linear_weights; /* 1: force omega_k = c_k (linear compact scheme, tests) */
+  int    flux;           /* 0: HLLC (Sec. 2.4); 1: local Lax-Friedrichs (Sec. 3 remark) */
 } orc_grid;
 
 typedef struct {
@@ -72,6 +73,10 @@ int orc_recon_scalar(long n, const double *ext, int periodic, double eps_weno,
  * (star-l), (acoustic ws)).  nv = 3: (rho, m, E); nv = 4: (rho, m_n, m_t, E)
  * with the tangential momentum carried by the contact. */
 void orc_hllc(int nv, double gamma, const double *Ul, const double *Ur, double *F);
+/* Local Lax-Friedrichs flux (the alternative Sec. 3 names for the near-vacuum
+ * double rarefaction): F = (F(Ul) + F(Ur))/2 - alpha (Ur - Ul)/2 with alpha
+ * the larger |u| + a of the two states (u normal to the face). */
+void orc_llf(int nv, double gamma, const double *Ul, const double *Ur, double *F);
 /* n faces at once; Ul, Ur, F are [n][nv] (test convenience). */
 void orc_hllc_batch(int nv, double gamma, long n, const double *Ul, const double *Ur, double *F);
 /* Physical flux F(U) in the normal direction. */

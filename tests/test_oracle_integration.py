@@ -212,3 +212,61 @@ def test_riemann_problem_converges_to_exact():
         ex = oracle.riemann_cell_averages(d["WL"], d["WR"], d["x0"], d["x1"], n, d["xd"], d["t"])
         errs.append(p.dx * np.abs(U[0] - ex[0]).sum())
     assert errs[1] < 0.75 * errs[0] and errs[1] < 0.1, errs
+
+
+# ------------------------------------------- Sec. 3 remark: Lax-Friedrichs flux
+def test_llf_density_wave_fifth_order():
+    """With the local Lax-Friedrichs flux at the faces the scheme is still
+    fifth order on the smooth density wave (the face flux is consistent and
+    Lipschitz; the order comes from the reconstruction).  The wave is a pure
+    contact (u = 1, p = 1), which HLLC resolves without dissipation while LLF
+    damps the O(h^5) face jumps with alpha = |u| + a, so LLF's errors are
+    larger than HLLC's but by a bounded factor (2.1 measured)."""
+    l1 = {}
+    for n in (40, 80):
+        p = W.density_wave(n)
+        Ul, *_ = _run(p, flux=1)
+        Uh, *_ = _run(p)
+        ex = W.density_wave_exact(n, 2.0)
+        l1[n] = p.dx * np.abs(Ul[0] - ex).sum()
+        lh = p.dx * np.abs(Uh[0] - ex).sum()
+        assert 1.0 < l1[n] / lh < 3.0, (n, l1[n], lh)
+        assert not np.array_equal(Ul, Uh)
+    assert np.log2(l1[40] / l1[80]) > 4.8, l1
+
+
+@pytest.mark.parametrize("name", ["123", "leblanc"])
+def test_llf_positivity(name):
+    """Positivity under the limiter at CFL omega_1/2 with the Lax-Friedrichs
+    face flux (its first-order scheme is positive up to CFL 1, pinned above,
+    so the limiter theorem's bound holds a fortiori)."""
+    p = POSITIVITY_CASES[name]()
+    U, steps, cnt = _run(p, flux=1)
+    rho, e, pr = _prim(U, p.gamma)
+    assert np.all(rho > 0) and np.all(e > 0)
+    assert np.all(np.isfinite(U))
+
+
+def test_llf_123_central_deviation_not_larger():
+    """Sec. 3, double rarefaction (123) example: the paper attributes the
+    oscillations of velocity and internal energy in the near-vacuum centre
+    to the less dissipative HLLC flux and names the Lax-Friedrichs flux as
+    the way to control them, without showing results.  Measured form of that
+    remark: on the paper's 400 cells, the largest deviation from the exact
+    solution of u and of e over the central quarter of the domain is no
+    larger with LLF than with HLLC (the oracle reconstructs conservative
+    variables, the paper characteristic ones, so the effect is small:
+    about 5% here)."""
+    d = W.PAPER_RIEMANN["123"]
+    p = POSITIVITY_CASES["123"]()
+    ex = oracle.riemann_cell_averages(d["WL"], d["WR"], d["x0"], d["x1"], p.nx, d["xd"], d["t"])
+    uex = ex[1] / ex[0]
+    eex = ex[2] / ex[0] - 0.5 * uex ** 2
+    c = slice(3 * p.nx // 8, 5 * p.nx // 8)
+    dev = {}
+    for flux in (0, 1):
+        U, *_ = _run(p, flux=flux)
+        u = U[1] / U[0]
+        e = U[2] / U[0] - 0.5 * u ** 2
+        dev[flux] = (np.abs(u - uex)[c].max(), np.abs(e - eex)[c].max())
+    assert dev[1][0] <= dev[0][0] and dev[1][1] <= dev[0][1], dev
