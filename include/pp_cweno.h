@@ -56,6 +56,14 @@ typedef enum {
                         the conserved variables in FP64 */
 } pp_prec_t;
 
+/* Numerical flux at the faces. */
+typedef enum {
+  PP_FLUX_HLLC = 0,  /* HLLC, Sec. 2.4 */
+  PP_FLUX_LLF = 1    /* local Lax-Friedrichs: (F(Ul) + F(Ur))/2 - alpha (Ur - Ul)/2 with
+                        alpha = max(|u_l| + a_l, |u_r| + a_r); the more dissipative
+                        alternative Sec. 3 names for near-vacuum rarefactions */
+} pp_flux_t;
+
 enum {
   PP_OK = 0,
   PP_ERR_ARG = 1,          /* bad sizes, gamma <= 1, cfl <= 0, unpaired periodic sides, ... */
@@ -82,6 +90,7 @@ typedef struct {
   double eps_pos;          /* cap of the limiter epsilon, Sec. 2.4 step 1 (1e-13) */
   int cfl_positivity_cap;  /* 1: use min(cfl, gl_weight), the bound of eq. (CFL-CD) */
   int limiter;             /* 1: Zhang-Shu limiter on (default); 0: off */
+  int flux;                /* pp_flux_t: face flux (PP_FLUX_HLLC default) */
 } pp_cweno_config;
 
 typedef struct {
@@ -105,8 +114,9 @@ int pp_cweno_config_default(pp_cweno_config *cfg);
 int pp_cweno_create(const pp_cweno_config *cfg, void *cuda_stream, pp_cweno_t *out);
 
 /* Create one handle for nprob independent problems advanced together (each
- * with its own time step).  All configs must share ndim, gamma, precision
- * and the limiter settings; sizes, domains, boundaries and cfl may differ. */
+ * with its own time step).  All configs must share ndim, gamma, precision,
+ * the limiter settings and the flux; sizes, domains, boundaries and cfl may
+ * differ. */
 int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda_stream,
                           pp_cweno_t *out);
 

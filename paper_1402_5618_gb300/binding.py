@@ -18,6 +18,7 @@ PP_OK, PP_ERR_ARG, PP_ERR_STATE, PP_ERR_NONPHYSICAL, PP_ERR_STEPS, PP_ERR_TIMEOU
     PP_ERR_CUDA, PP_ERR_UNSUPPORTED = range(8)
 PREC_FP64, PREC_MIXED = 0, 1
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+FLUX_HLLC, FLUX_LLF = 0, 1
 
 
 class Config(C.Structure):
@@ -27,6 +28,7 @@ class Config(C.Structure):
         ("gamma", C.c_double), ("cfl", C.c_double), ("bc", C.c_int * 4),
         ("precision", C.c_int), ("gl_weight", C.c_double), ("eps_weno", C.c_double),
         ("eps_pos", C.c_double), ("cfl_positivity_cap", C.c_int), ("limiter", C.c_int),
+        ("flux", C.c_int),
     ]
 
 
@@ -113,7 +115,7 @@ def _check(rc: int, where: str, ok=(PP_OK,)):
 
 def make_config(ndim=1, nx=200, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, cfl=0.5,
                 bc=(0, 0, 0, 0), precision=PREC_FP64, gl_weight=1.0 / 12.0, eps_weno=1e-13,
-                eps_pos=1e-13, cfl_positivity_cap=False, limiter=True) -> Config:
+                eps_pos=1e-13, cfl_positivity_cap=False, limiter=True, flux=FLUX_HLLC) -> Config:
     c = Config()
     lib().pp_cweno_config_default(C.byref(c))
     c.ndim, c.nx, c.ny = ndim, nx, (ny if ndim == 2 else 1)
@@ -124,6 +126,7 @@ def make_config(ndim=1, nx=200, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4,
     c.precision = int(precision)
     c.gl_weight, c.eps_weno, c.eps_pos = gl_weight, eps_weno, eps_pos
     c.cfl_positivity_cap, c.limiter = int(cfl_positivity_cap), int(limiter)
+    c.flux = int(flux)
     return c
 
 

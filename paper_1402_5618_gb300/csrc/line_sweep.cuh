@@ -102,6 +102,7 @@ struct SweepArgs {
   int stage;          // 0, 1, 2
   double eps_fixed;   // > 0: fixed limiter epsilon, no control-block checks (operator evaluation)
   int limiter;
+  int flux;           // 0 HLLC, 1 local Lax-Friedrichs
   Ctl *ctl;
   // batched launch: line table and problem descriptors (nullptr: one problem)
   const LineRef *lines;
@@ -1279,9 +1280,9 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
     }
   }
   // ---------------------------------------------------------------- flux
-  // HLLC at face f (between cells f-1 and f): the left state is U^- of cell
-  // f-1, the right state U^+ of cell f; the two segment-end faces read a
-  // neighbour CTA's value
+  // HLLC (or local Lax-Friedrichs) at face f (between cells f-1 and f): the
+  // left state is U^- of cell f-1, the right state U^+ of cell f; the two
+  // segment-end faces read a neighbour CTA's value
   auto face = [&](int f) {
     real Ul[NV], Ur[NV], F[NV];
     const real *srcL = nullptr;
@@ -1317,7 +1318,8 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       for (int kv = 0; kv < NV; ++kv) Ur[kv] = Ul[kv];
       if (args.bchi == 2) Ur[1] = -Ur[1];
     }
-    hllc<real, NV>(Ul, Ur, gam, F);
+    if (args.flux) llf<real, NV>(Ul, Ur, gam, F);
+    else hllc<real, NV>(Ul, Ur, gam, F);
 #pragma unroll
     for (int kv = 0; kv < NV; ++kv) Fl[kv * (SEG + 2) + (f - lo)] = F[kv];
   };

@@ -234,6 +234,27 @@ __device__ __forceinline__ void hllc(const real *Ul, const real *Ur, real gamma,
   }
 }
 
+// Local Lax-Friedrichs flux, the alternative Sec. 3 names for the
+// near-vacuum double rarefaction: the mean of the two physical fluxes minus
+// alpha/2 times the jump, alpha the larger signal speed |u| + a of the two
+// face states
+template <typename real, int NV>
+__device__ __forceinline__ void llf(const real *Ul, const real *Ur, real gamma, real *F) {
+  real pl = pressure<real, NV>(Ul, gamma), pr = pressure<real, NV>(Ur, gamma);
+  if constexpr (sizeof(real) == 4) {
+    pl = fmaxf(pl, 0.0f);
+    pr = fmaxf(pr, 0.0f);
+  }
+  real al = fabs(Ul[1] / Ul[0]) + sqrt(gamma * pl / Ul[0]);
+  real ar = fabs(Ur[1] / Ur[0]) + sqrt(gamma * pr / Ur[0]);
+  real ha = real(0.5) * fmax(al, ar);
+  real Fl[NV], Fr[NV];
+  phys_flux<real, NV>(Ul, pl, Fl);
+  phys_flux<real, NV>(Ur, pr, Fr);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) F[k] = real(0.5) * (Fl[k] + Fr[k]) - ha * (Ur[k] - Ul[k]);
+}
+
 template <typename real>
 __device__ __forceinline__ constexpr real unit_roundoff() {
   return sizeof(real) == 8 ? real(1.1102230246251565e-16) : real(5.9604645e-08);

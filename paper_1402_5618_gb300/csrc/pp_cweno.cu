@@ -616,6 +616,7 @@ int check_config(const pp_cweno_config *c) {
   if (!(c->gl_weight > 0.0 && c->gl_weight < 0.5)) return PP_ERR_ARG;
   if (!(c->eps_weno > 0.0) || !(c->eps_pos > 0.0)) return PP_ERR_ARG;
   if (c->precision != PP_PREC_FP64 && c->precision != PP_PREC_MIXED) return PP_ERR_ARG;
+  if (c->flux != PP_FLUX_HLLC && c->flux != PP_FLUX_LLF) return PP_ERR_ARG;
   int nb = c->ndim == 2 ? 4 : 2;
   for (int k = 0; k < nb; ++k)
     if (!bc_valid(c->bc[k])) return PP_ERR_ARG;
@@ -637,6 +638,7 @@ void fill_common(const pp_cweno_s *h, SweepArgs &a, int stage, double eps_fixed,
   a.stage = stage;
   a.eps_fixed = eps_fixed;
   a.limiter = h->cfg.limiter;
+  a.flux = h->cfg.flux;
   a.ctl = ctl;
 }
 
@@ -1081,6 +1083,7 @@ int pp_cweno_config_default(pp_cweno_config *cfg) {
   cfg->eps_pos = 1e-13;
   cfg->cfl_positivity_cap = 0;
   cfg->limiter = 1;
+  cfg->flux = PP_FLUX_HLLC;
   return PP_OK;
 }
 
@@ -1119,7 +1122,7 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
     const pp_cweno_config &c = cfgs[p];
     if (c.ndim != c0.ndim || c.gamma != c0.gamma || c.precision != c0.precision ||
         c.gl_weight != c0.gl_weight || c.eps_weno != c0.eps_weno || c.eps_pos != c0.eps_pos ||
-        c.limiter != c0.limiter)
+        c.limiter != c0.limiter || c.flux != c0.flux)
       return PP_ERR_ARG;
   }
   pp_cweno_s *h = new (std::nothrow) pp_cweno_s();

@@ -33,8 +33,9 @@ def test_config_struct_layout_matches_header():
     import subprocess
     import tempfile
     src = '#include "pp_cweno.h"\n#include <stdio.h>\n#include <stddef.h>\n' \
-          'int main(){printf("%zu %zu %zu\\n", sizeof(pp_cweno_config), ' \
-          'sizeof(pp_cweno_stats_t), offsetof(pp_cweno_config, limiter));return 0;}\n'
+          'int main(){printf("%zu %zu %zu %zu\\n", sizeof(pp_cweno_config), ' \
+          'sizeof(pp_cweno_stats_t), offsetof(pp_cweno_config, limiter), ' \
+          'offsetof(pp_cweno_config, flux));return 0;}\n'
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
         open(c, "w").write(src)
@@ -44,6 +45,23 @@ def test_config_struct_layout_matches_header():
     assert int(out[0]) == ctypes.sizeof(binding.Config)
     assert int(out[1]) == ctypes.sizeof(binding.Stats)
     assert int(out[2]) == binding.Config.limiter.offset
+    assert int(out[3]) == binding.Config.flux.offset
+
+
+def test_config_rejects_unknown_flux():
+    """The configuration check runs before any device call: an unknown flux
+    selector is PP_ERR_ARG, for one problem and for a batch whose problems
+    disagree on the flux."""
+    L = binding.lib()
+    h = ctypes.c_void_p()
+    for bad in (-1, 2, 99):
+        c = binding.make_config(flux=bad)
+        assert L.pp_cweno_create(ctypes.byref(c), None, ctypes.byref(h)) == binding.PP_ERR_ARG
+        assert not h.value
+    arr = (binding.Config * 2)(binding.make_config(flux=binding.FLUX_HLLC),
+                               binding.make_config(flux=binding.FLUX_LLF))
+    assert L.pp_cweno_create_batch(arr, 2, None, ctypes.byref(h)) == binding.PP_ERR_ARG
+    assert not h.value
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
