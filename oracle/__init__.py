@@ -34,7 +34,7 @@ class Grid(C.Structure):
         ("dx", C.c_double), ("dy", C.c_double), ("gamma", C.c_double),
         ("bc", C.c_int * 4), ("gl_weight", C.c_double), ("eps_weno", C.c_double),
         ("eps_pos", C.c_double), ("limiter", C.c_int), ("linear_weights", C.c_int),
-        ("flux", C.c_int),
+        ("flux", C.c_int), ("recon", C.c_int),
     ]
 
 
@@ -75,6 +75,11 @@ def lib():
             L.orc_cyclic.argtypes = [C.c_long, dp, dp, dp, dp, dp, C.c_int]
             L.orc_recon_scalar.argtypes = [C.c_long, dp, C.c_int, C.c_double, C.c_int, dp, dp]
             L.orc_hllc.argtypes = [C.c_int, C.c_double, dp, dp, dp]
+            L.orc_roe_eigen.argtypes = [C.c_int, C.c_double, dp, dp, dp, dp]
+            L.orc_block_thomas.argtypes = [C.c_long, C.c_int, dp, dp, dp, dp, C.c_int, dp, C.c_int]
+            L.orc_block_cyclic.argtypes = [C.c_long, C.c_int, dp, dp, dp, dp, dp, C.c_int]
+            L.orc_recon_char.argtypes = [C.c_int, C.c_long, dp, C.c_int, C.c_double, C.c_double,
+                                         C.c_int, dp, dp]
             L.orc_llf.argtypes = [C.c_int, C.c_double, dp, dp, dp]
             L.orc_flux.argtypes = [C.c_int, C.c_double, dp, dp]
             L.orc_hllc_batch.argtypes = [C.c_int, C.c_double, C.c_long, dp, dp, dp]
@@ -114,7 +119,7 @@ def _f64(x) -> np.ndarray:
 def make_grid(ndim: int, nx: int, ny: int = 1, dx: float = 1.0, dy: float = 1.0,
               gamma: float = 1.4, bc=(0, 0, 0, 0), gl_weight: float = 1.0 / 12.0,
               eps_weno: float = 1e-13, eps_pos: float = 1e-13, limiter: bool = True,
-              linear_weights: bool = False, flux: int = 0) -> Grid:
+              linear_weights: bool = False, flux: int = 0, recon: int = 0) -> Grid:
     g = Grid()
     g.ndim, g.nx, g.ny = ndim, nx, (ny if ndim == 2 else 1)
     g.dx, g.dy, g.gamma = dx, dy, gamma
@@ -123,6 +128,7 @@ def make_grid(ndim: int, nx: int, ny: int = 1, dx: float = 1.0, dy: float = 1.0,
     g.gl_weight, g.eps_weno, g.eps_pos = gl_weight, eps_weno, eps_pos
     g.limiter, g.linear_weights = int(limiter), int(linear_weights)
     g.flux = int(flux)
+    g.recon = int(recon)
     return g
 
 
@@ -163,6 +169,50 @@ def recon_scalar(ext, periodic: bool, eps_weno=1e-13, linear=False):
     n = len(ext) - 4
     um, up = np.zeros(n), np.zeros(n)
     rc = lib().orc_recon_scalar(n, _p(ext), int(periodic), eps_weno, int(linear), _p(um), _p(up))
+    if rc:
+        raise ArithmeticError("reconstruction failed")
+    return um, up
+
+
+def roe_eigen(Ua, Ub, gamma=1.4):
+    """(L, R): left / right eigenvector matrices at the Roe average, Sec. 2.3"""
+    Ua, Ub = _f64(Ua), _f64(Ub)
+    nv = len(Ua)
+    Lm, Rm = np.zeros((nv, nv)), np.zeros((nv, nv))
+    lib().orc_roe_eigen(nv, gamma, _p(Ua), _p(Ub), _p(Lm), _p(Rm))
+    return Lm, Rm
+
+
+def block_thomas(A, B, C_, r, reverse=False) -> np.ndarray:
+    """A, B, C_: [n, m, m]; r: [n, m] or [n, m, ncol]"""
+    A, B, C_, r = map(_f64, (A, B, C_, r))
+    n, m = B.shape[0], B.shape[1]
+    ncol = 1 if r.ndim == 2 else r.shape[2]
+    x = np.zeros_like(r)
+    rc = lib().orc_block_thomas(n, m, _p(A), _p(B), _p(C_), _p(r), ncol, _p(x), int(reverse))
+    if rc:
+        raise ArithmeticError("singular pivot block")
+    return x
+
+
+def block_cyclic(A, B, C_, r, reverse=False) -> np.ndarray:
+    A, B, C_, r = map(_f64, (A, B, C_, r))
+    n, m = B.shape[0], B.shape[1]
+    x = np.zeros_like(r)
+    rc = lib().orc_block_cyclic(n, m, _p(A), _p(B), _p(C_), _p(r), _p(x), int(reverse))
+    if rc:
+        raise ArithmeticError("singular cyclic block system")
+    return x
+
+
+def recon_char(ext, periodic: bool, gamma=1.4, eps_weno=1e-13, linear=False):
+    """ext: [nv, n+4] conserved averages with two ghosts per side.  Returns
+    (U^-_{j+1/2}, U^+_{j-1/2}) as [nv, n] arrays."""
+    ext = _f64(ext)
+    nv, n = ext.shape[0], ext.shape[1] - 4
+    um, up = np.zeros((nv, n)), np.zeros((nv, n))
+    rc = lib().orc_recon_char(nv, n, _p(ext), int(periodic), gamma, eps_weno, int(linear),
+                              _p(um), _p(up))
     if rc:
         raise ArithmeticError("reconstruction failed")
     return um, up

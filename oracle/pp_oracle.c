@@ -33,6 +33,14 @@
  *    oscillations of the near-vacuum double rarefaction): the local form,
  *    the dissipation coefficient being the larger |u| + a of the two face
  *    states; an alternative to HLLC selected per grid.
+ *  - characteristic-wise reconstruction (Sec. 2.3), selected per grid: the
+ *    eigenvectors of a row come from the Roe average of the two cells
+ *    adjacent to the row's face (cells j, j+1 for U^-_{j+1/2}; cells k-1, k
+ *    for U^+_{k-1/2}); the weights of field k use that face's l^(k) on all
+ *    five cells of the stencil; bounded lines close the first and last
+ *    unknown with WENO5-Z on the same characteristic variables; the cyclic
+ *    block system is solved with a Woodbury correction; 2-D lines use the
+ *    4 x 4 eigensystem with the shear field (0, 0, 1, v).
  */
 #include "pp_oracle.h"
 
@@ -351,6 +359,268 @@ void orc_llf(int nv, double gamma, const double *Ul, const double *Ur, double *F
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 2.3: characteristic-wise compact-WENO reconstruction of a line.      */
+/* ------------------------------------------------------------------------ */
+/* Solve M X = Y in place for m x m matrix M (row-major) and ncol columns of
+ * Y ([m][ncol], overwritten with X): Gaussian elimination with partial
+ * pivoting.  Returns -1 on a zero pivot. */
+static int dense_solve(int m, double *M, int ncol, double *Y) {
+  for (int k = 0; k < m; ++k) {
+    int p = k;
+    for (int i = k + 1; i < m; ++i)
+      if (fabs(M[i * m + k]) > fabs(M[p * m + k])) p = i;
+    if (M[p * m + k] == 0.0) return -1;
+    if (p != k) {
+      for (int c = 0; c < m; ++c) { double t = M[k * m + c]; M[k * m + c] = M[p * m + c]; M[p * m + c] = t; }
+      for (int c = 0; c < ncol; ++c) { double t = Y[k * ncol + c]; Y[k * ncol + c] = Y[p * ncol + c]; Y[p * ncol + c] = t; }
+    }
+    for (int i = k + 1; i < m; ++i) {
+      double f = M[i * m + k] / M[k * m + k];
+      for (int c = k; c < m; ++c) M[i * m + c] -= f * M[k * m + c];
+      for (int c = 0; c < ncol; ++c) Y[i * ncol + c] -= f * Y[k * ncol + c];
+    }
+  }
+  for (int k = m - 1; k >= 0; --k)
+    for (int c = 0; c < ncol; ++c) {
+      double s = Y[k * ncol + c];
+      for (int j = k + 1; j < m; ++j) s -= M[k * m + j] * Y[j * ncol + c];
+      Y[k * ncol + c] = s / M[k * m + k];
+    }
+  return 0;
+}
+
+/* Sec. 2.3: Roe average of two conserved states and the left / right
+ * eigenvectors of the flux Jacobian there (eqs. (eigen), (reigenv),
+ * (leigenv)); nv = 4 adds the tangential velocity v: eigenvalues u - a, u,
+ * u, u + a with the shear eigenvector (0, 0, 1, v). */
+void orc_roe_eigen(int nv, double gamma, const double *Ua, const double *Ub, double *Lm, double *Rm) {
+  double sa = sqrt(Ua[0]), sb = sqrt(Ub[0]);
+  double pa = pressure(nv, gamma, Ua), pb = pressure(nv, gamma, Ub);
+  double u = (Ua[1] / sa + Ub[1] / sb) / (sa + sb);
+  double v = nv == 4 ? (Ua[2] / sa + Ub[2] / sb) / (sa + sb) : 0.0;
+  double H = ((Ua[nv - 1] + pa) / sa + (Ub[nv - 1] + pb) / sb) / (sa + sb);
+  double q2 = u * u + v * v;
+  double a = sqrt((gamma - 1.0) * (H - 0.5 * q2));
+  double c1 = (gamma - 1.0) / (a * a), c2 = 0.5 * q2 * c1;
+  if (nv == 3) {
+    double R[9] = {1.0, 1.0, 1.0,
+                   u - a, u, u + a,
+                   H - u * a, 0.5 * u * u, H + u * a};
+    double L[9] = {0.5 * (c2 + u / a), 0.5 * (-c1 * u - 1.0 / a), 0.5 * c1,
+                   1.0 - c2, c1 * u, -c1,
+                   0.5 * (c2 - u / a), 0.5 * (-c1 * u + 1.0 / a), 0.5 * c1};
+    memcpy(Rm, R, sizeof R);
+    memcpy(Lm, L, sizeof L);
+  } else {
+    double R[16] = {1.0, 1.0, 0.0, 1.0,
+                    u - a, u, 0.0, u + a,
+                    v, v, 1.0, v,
+                    H - u * a, 0.5 * q2, v, H + u * a};
+    double L[16] = {0.5 * (c2 + u / a), 0.5 * (-c1 * u - 1.0 / a), -0.5 * c1 * v, 0.5 * c1,
+                    1.0 - c2, c1 * u, c1 * v, -c1,
+                    -v, 0.0, 1.0, 0.0,
+                    0.5 * (c2 - u / a), 0.5 * (-c1 * u + 1.0 / a), -0.5 * c1 * v, 0.5 * c1};
+    memcpy(Rm, R, sizeof R);
+    memcpy(Lm, L, sizeof L);
+  }
+}
+
+/* Block tridiagonal system with m x m blocks and ncol right-hand sides:
+ *   A[i] x[i-1] + B[i] x[i] + C[i] x[i+1] = r[i],  i = 0..n-1
+ * A, B, C are [n][m][m] (A[0], C[n-1] ignored), r and x [n][m][ncol].
+ * Block Thomas elimination; reverse = 1 eliminates from i = n-1 downward. */
+int orc_block_thomas(long n, int m, const double *A, const double *B, const double *C,
+                     const double *r, int ncol, double *x, int reverse) {
+  const long mm = (long)m * m, mc = (long)m * ncol;
+  double *Y = (double *)malloc(sizeof(double) * (size_t)(n * mm));   /* Bp^{-1} (next block) */
+  double *g = (double *)malloc(sizeof(double) * (size_t)(n * mc));
+  double Bp[16], T[16 * 5];
+  if (!Y || !g) { free(Y); free(g); return -1; }
+  int rc = 0;
+  for (long s = 0; s < n && rc == 0; ++s) {
+    long i = reverse ? n - 1 - s : s;         /* row being eliminated */
+    long ip = reverse ? i + 1 : i - 1;        /* previously eliminated neighbour */
+    const double *lo = reverse ? C + i * mm : A + i * mm;   /* couples the previous row */
+    const double *hi = reverse ? A + i * mm : C + i * mm;   /* couples the next row */
+    /* Bp = B_i - lo Y_prev, rhs = r_i - lo g_prev */
+    for (int a = 0; a < m; ++a) {
+      for (int b = 0; b < m; ++b) {
+        double t = B[i * mm + a * m + b];
+        if (s > 0) for (int k = 0; k < m; ++k) t -= lo[a * m + k] * Y[ip * mm + k * m + b];
+        Bp[a * m + b] = t;
+      }
+    }
+    /* T = [hi | rhs] with m + ncol columns, solved against Bp */
+    int w = m + ncol;
+    for (int a = 0; a < m; ++a) {
+      for (int b = 0; b < m; ++b) T[a * w + b] = hi[a * m + b];
+      for (int c = 0; c < ncol; ++c) {
+        double t = r[i * mc + a * ncol + c];
+        if (s > 0) for (int k = 0; k < m; ++k) t -= lo[a * m + k] * g[ip * mc + k * ncol + c];
+        T[a * w + m + c] = t;
+      }
+    }
+    rc = dense_solve(m, Bp, w, T);
+    for (int a = 0; a < m; ++a) {
+      for (int b = 0; b < m; ++b) Y[i * mm + a * m + b] = T[a * w + b];
+      for (int c = 0; c < ncol; ++c) g[i * mc + a * ncol + c] = T[a * w + m + c];
+    }
+  }
+  /* back substitution: x_i = g_i - Y_i x_next */
+  for (long s = n - 1; s >= 0 && rc == 0; --s) {
+    long i = reverse ? n - 1 - s : s;
+    long in = reverse ? i - 1 : i + 1;
+    for (int a = 0; a < m; ++a)
+      for (int c = 0; c < ncol; ++c) {
+        double t = g[i * mc + a * ncol + c];
+        if (s < n - 1) for (int k = 0; k < m; ++k) t -= Y[i * mm + a * m + k] * x[in * mc + k * ncol + c];
+        x[i * mc + a * ncol + c] = t;
+      }
+  }
+  free(Y); free(g);
+  return rc;
+}
+
+/* Cyclic block tridiagonal system (A[0] couples x[n-1], C[n-1] couples
+ * x[0]), one right-hand side: Woodbury correction of a block Thomas solve.
+ * With G = -B[0], T = T' + U V^T where U = (G, 0, .., 0, C[n-1]) and
+ * V^T = (I, 0, .., 0, G^{-1} A[0]); T' has B'[0] = B[0] - G and
+ * B'[n-1] = B[n-1] - C[n-1] G^{-1} A[0] and no corners.  Then
+ * x = y - Z (I + V^T Z)^{-1} V^T y with T' y = r, T' Z = U. */
+int orc_block_cyclic(long n, int m, const double *A, const double *B, const double *C,
+                     const double *r, double *x, int reverse) {
+  const long mm = (long)m * m;
+  double *Bm = (double *)malloc(sizeof(double) * (size_t)(n * mm));
+  double *Um = (double *)calloc((size_t)(n * mm), sizeof(double));
+  double *Z = (double *)malloc(sizeof(double) * (size_t)(n * mm));
+  double *y = (double *)malloc(sizeof(double) * (size_t)(n * m));
+  if (!Bm || !Um || !Z || !y) { free(Bm); free(Um); free(Z); free(y); return -1; }
+  double G[16], GiA[16], Gc[16];
+  for (int k = 0; k < mm; ++k) { G[k] = -B[k]; Gc[k] = G[k]; GiA[k] = A[k]; }
+  int rc = dense_solve(m, Gc, m, GiA);     /* GiA = G^{-1} A[0] */
+  memcpy(Bm, B, sizeof(double) * (size_t)(n * mm));
+  for (int k = 0; k < mm; ++k) Bm[k] = B[k] - G[k];
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) {
+      double t = 0.0;
+      for (int k = 0; k < m; ++k) t += C[(n - 1) * mm + a * m + k] * GiA[k * m + b];
+      Bm[(n - 1) * mm + a * m + b] -= t;
+    }
+  for (int k = 0; k < mm; ++k) { Um[k] = G[k]; Um[(n - 1) * mm + k] = C[(n - 1) * mm + k]; }
+  if (rc == 0) rc = orc_block_thomas(n, m, A, Bm, C, r, 1, y, reverse);
+  if (rc == 0) rc = orc_block_thomas(n, m, A, Bm, C, Um, m, Z, reverse);
+  if (rc == 0) {
+    /* S = I + V^T Z (m x m), t = V^T y */
+    double S[16], t[4];
+    for (int a = 0; a < m; ++a) {
+      for (int b = 0; b < m; ++b) {
+        double s = (a == b ? 1.0 : 0.0) + Z[a * m + b];
+        for (int k = 0; k < m; ++k) s += GiA[a * m + k] * Z[(n - 1) * mm + k * m + b];
+        S[a * m + b] = s;
+      }
+      double s = y[a];
+      for (int k = 0; k < m; ++k) s += GiA[a * m + k] * y[(n - 1) * m + k];
+      t[a] = s;
+    }
+    rc = dense_solve(m, S, 1, t);
+    for (long i = 0; i < n && rc == 0; ++i)
+      for (int a = 0; a < m; ++a) {
+        double s = y[i * m + a];
+        for (int k = 0; k < m; ++k) s -= Z[i * mm + a * m + k] * t[k];
+        x[i * m + a] = s;
+      }
+  }
+  free(Bm); free(Um); free(Z); free(y);
+  return rc;
+}
+
+/* The characteristic-wise reconstruction of Sec. 2.3, steps 1-4, on one line
+ * of nv conserved variables.  ext is [nv][n+4] with two ghost cells per
+ * side; um, up are [nv][n] like the component-wise form.
+ * Minus system: unknown j is U~_{j+1/2}; its row is the scalar row of
+ * eq. (CWENO-FV) for every characteristic field k, multiplied by the left
+ * eigenvector l^(k) at the Roe average of cells j and j+1 (eq. (cha-1)),
+ * the weights coming from the characteristic variables l^(k) ubar_i of the
+ * five cells j-2..j+2; eq. (1DEuler-FVC) is the resulting block system.
+ * Plus system: unknown k is U~^+_{k-1/2} at the Roe average of cells k-1
+ * and k, with the mirrored row and indicators of the component-wise form.
+ * Bounded lines close the first and last unknown with the explicit WENO5-Z
+ * value of each characteristic variable (same face eigenvectors). */
+int orc_recon_char(int nv, long n, const double *ext, int periodic, double gamma,
+                   double eps_weno, int linear, double *um, double *up) {
+  if (n < 3) return -1;
+  const long s = n + 4, mm = (long)nv * nv;
+  double *A = (double *)calloc((size_t)(n * mm), sizeof(double));
+  double *B = (double *)calloc((size_t)(n * mm), sizeof(double));
+  double *C = (double *)calloc((size_t)(n * mm), sizeof(double));
+  double *r = (double *)calloc((size_t)(n * nv), sizeof(double));
+  double *x = (double *)malloc(sizeof(double) * (size_t)(n * nv));
+  if (!A || !B || !C || !r || !x) { free(A); free(B); free(C); free(r); free(x); return -1; }
+  int rc = 0;
+  for (int side = 0; side < 2 && rc == 0; ++side) {
+    for (long j = 0; j < n; ++j) {
+      /* step 1: eigenvectors at the row's face (j+1/2 minus, j-1/2 plus) */
+      double Ua[4], Ub[4], Lm[16], Rm[16];
+      long ca = side == 0 ? j : j - 1;
+      for (int v = 0; v < nv; ++v) { Ua[v] = ext[v * s + ca + 2]; Ub[v] = ext[v * s + ca + 3]; }
+      orc_roe_eigen(nv, gamma, Ua, Ub, Lm, Rm);
+      /* characteristic variables of the five cells j-2..j+2 */
+      double w5[4][5];
+      for (int k = 0; k < nv; ++k)
+        for (int q = 0; q < 5; ++q) {
+          double t = 0.0;
+          for (int v = 0; v < nv; ++v) t += Lm[k * nv + v] * ext[v * s + j + q];
+          w5[k][q] = t;
+        }
+      int closure = !periodic && (j == 0 || j == n - 1);
+      for (int k = 0; k < nv; ++k) {
+        const double *lk = Lm + k * nv;
+        if (closure) {
+          double val = side == 0 ? weno5z_minus(w5[k], eps_weno, linear)
+                                 : weno5z_plus(w5[k], eps_weno, linear);
+          for (int v = 0; v < nv; ++v) B[j * mm + k * nv + v] = lk[v];
+          r[j * nv + k] = val;
+          continue;
+        }
+        /* step 2: weights of field k (mirrored indicators on the plus side) */
+        double beta[3], bw[3], w[3];
+        orc_smoothness(w5[k], beta);
+        if (side == 0) { bw[0] = beta[0]; bw[1] = beta[1]; bw[2] = beta[2]; }
+        else { bw[0] = beta[2]; bw[1] = beta[1]; bw[2] = beta[0]; }
+        if (linear) { w[0] = C_COMPACT[0]; w[1] = C_COMPACT[1]; w[2] = C_COMPACT[2]; }
+        else orc_wenoz_weights(bw, C_COMPACT, eps_weno, w);
+        /* step 3: the scalar row's coefficients */
+        double a, b, c, dm, dc, dp;   /* on x_{j-1}, x_j, x_{j+1}; on ubar_{j-1}, ubar_j, ubar_{j+1} */
+        if (side == 0) {
+          a = (2.0 * w[0] + w[1]) / 3.0; b = (w[0] + 2.0 * (w[1] + w[2])) / 3.0; c = w[2] / 3.0;
+          dm = w[0] / 6.0; dc = (5.0 * (w[0] + w[1]) + w[2]) / 6.0; dp = (w[1] + 5.0 * w[2]) / 6.0;
+        } else {
+          a = w[2] / 3.0; b = (w[0] + 2.0 * (w[1] + w[2])) / 3.0; c = (2.0 * w[0] + w[1]) / 3.0;
+          dm = (w[1] + 5.0 * w[2]) / 6.0; dc = (5.0 * (w[0] + w[1]) + w[2]) / 6.0; dp = w[0] / 6.0;
+        }
+        /* step 4: block row = coefficient x l^(k) */
+        for (int v = 0; v < nv; ++v) {
+          A[j * mm + k * nv + v] = a * lk[v];
+          B[j * mm + k * nv + v] = b * lk[v];
+          C[j * mm + k * nv + v] = c * lk[v];
+        }
+        r[j * nv + k] = dm * w5[k][1] + dc * w5[k][2] + dp * w5[k][3];
+      }
+    }
+    rc = periodic ? orc_block_cyclic(n, nv, A, B, C, r, x, side)
+                  : orc_block_thomas(n, nv, A, B, C, r, 1, x, side);
+    double *out = side == 0 ? um : up;
+    for (long j = 0; j < n; ++j)
+      for (int v = 0; v < nv; ++v) out[v * n + j] = x[j * nv + v];
+    memset(A, 0, sizeof(double) * (size_t)(n * mm));
+    memset(B, 0, sizeof(double) * (size_t)(n * mm));
+    memset(C, 0, sizeof(double) * (size_t)(n * mm));
+  }
+  free(A); free(B); free(C); free(r); free(x);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 2.4: the positivity-preserving limiter, steps 1-4.                    */
 /* ------------------------------------------------------------------------ */
 
@@ -489,10 +759,15 @@ static int line_operator(const orc_grid *g, int nv, long n, const double *line, 
   if (rc == 0) {
     for (int v = 0; v < nv; ++v) memcpy(ext + v * s + 2, line + v * n, sizeof(double) * (size_t)n);
     ghost(nv, n, ext, bclo, bchi);
-    /* component-wise reconstruction of the conserved variables */
-    for (int v = 0; v < nv && rc == 0; ++v) {
-      rc = orc_recon_scalar(n, ext + v * s, periodic, g->eps_weno, g->linear_weights, tm, tp);
-      for (long j = 0; j < n; ++j) { um[v * n + j] = tm[j]; up[v * n + j] = tp[j]; }
+    if (g->recon) {
+      /* characteristic-wise reconstruction, Sec. 2.3 */
+      rc = orc_recon_char(nv, n, ext, periodic, g->gamma, g->eps_weno, g->linear_weights, um, up);
+    } else {
+      /* component-wise reconstruction of the conserved variables */
+      for (int v = 0; v < nv && rc == 0; ++v) {
+        rc = orc_recon_scalar(n, ext + v * s, periodic, g->eps_weno, g->linear_weights, tm, tp);
+        for (long j = 0; j < n; ++j) { um[v * n + j] = tm[j]; up[v * n + j] = tp[j]; }
+      }
     }
   }
   if (rc == 0 && g->limiter) {

@@ -33,6 +33,7 @@ typedef struct {
   int    limiter;        /* 1: Zhang-Shu limiter on, 0: off (tests only) */
   int    linear_weights; /* 1: force omega_k = c_k (linear compact scheme, tests) */
   int    flux;           /* 0: HLLC (Sec. 2.4); 1: local Lax-Friedrichs (Sec. 3 remark) */
+  int    recon;          /* 0: component-wise (conserved variables); 1: characteristic-wise (Sec. 2.3) */
 } orc_grid;
 
 typedef struct {
@@ -68,6 +69,27 @@ int orc_cyclic(long n, const double *sub, const double *diag, const double *sup,
  * up[j] = u^+_{j-1/2} (left face of cell j, from cell j).  Returns 0 or -1. */
 int orc_recon_scalar(long n, const double *ext, int periodic, double eps_weno,
                      int linear_weights, double *um, double *up);
+
+/* ---- characteristic-wise pieces (Sec. 2.3) ---- */
+/* Left (Lm) and right (Rm) eigenvector matrices, row-major nv x nv, of the
+ * flux Jacobian at the Roe average of the conserved states Ua and Ub; rows
+ * of Lm are l^(k), columns of Rm are r^(k), ordered u - a, u, (u), u + a. */
+void orc_roe_eigen(int nv, double gamma, const double *Ua, const double *Ub, double *Lm, double *Rm);
+/* Block tridiagonal system with m x m blocks (m <= 4) and ncol <= 4
+ * right-hand sides: A[i] x[i-1] + B[i] x[i] + C[i] x[i+1] = r[i]; A, B, C
+ * [n][m][m], r and x [n][m][ncol]; block Thomas elimination (reverse = 1
+ * from i = n-1 downward).  Returns 0, or -1 on a singular pivot block. */
+int orc_block_thomas(long n, int m, const double *A, const double *B, const double *C,
+                     const double *r, int ncol, double *x, int reverse);
+/* Cyclic block tridiagonal system (A[0] couples x[n-1], C[n-1] couples
+ * x[0]), one right-hand side; Woodbury correction of block Thomas solves. */
+int orc_block_cyclic(long n, int m, const double *A, const double *B, const double *C,
+                     const double *r, double *x, int reverse);
+/* Characteristic-wise compact-WENO reconstruction of one line of nv conserved
+ * variables: ext [nv][n+4] with two ghost cells per side, um / up [nv][n]
+ * as in orc_recon_scalar. */
+int orc_recon_char(int nv, long n, const double *ext, int periodic, double gamma,
+                   double eps_weno, int linear_weights, double *um, double *up);
 
 /* HLLC flux with Batten wave speeds (Sec. 2.4, eqs. (HLLC), (contact-v),
  * (star-l), (acoustic ws)).  nv = 3: (rho, m, E); nv = 4: (rho, m_n, m_t, E)
