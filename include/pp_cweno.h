@@ -64,6 +64,19 @@ typedef enum {
                         alternative Sec. 3 names for near-vacuum rarefactions */
 } pp_flux_t;
 
+/* Variables the compact-WENO reconstruction works on. */
+typedef enum {
+  PP_RECON_COMPONENT = 0,      /* each conserved variable on its own: one scalar
+                                  tridiagonal system per variable and side (Sec. 2.2) */
+  PP_RECON_CHARACTERISTIC = 1  /* characteristic variables of the Roe average at each
+                                  face: one block tridiagonal system per side, blocks
+                                  diag(a, b, c) L (Sec. 2.3, eq. (1DEuler-FVC)).
+                                  FP64 single problems only (PP_ERR_UNSUPPORTED
+                                  otherwise); needs 2 x (n (nv^2 + nv) + nv^2) x
+                                  lines doubles of scratch per sweep direction
+                                  (periodic: nv^2 + nv (nv+1) per row) */
+} pp_recon_t;
+
 enum {
   PP_OK = 0,
   PP_ERR_ARG = 1,          /* bad sizes, gamma <= 1, cfl <= 0, unpaired periodic sides, ... */
@@ -91,6 +104,7 @@ typedef struct {
   int cfl_positivity_cap;  /* 1: use min(cfl, gl_weight), the bound of eq. (CFL-CD) */
   int limiter;             /* 1: Zhang-Shu limiter on (default); 0: off */
   int flux;                /* pp_flux_t: face flux (PP_FLUX_HLLC default) */
+  int recon;               /* pp_recon_t: reconstructed variables (PP_RECON_COMPONENT default) */
 } pp_cweno_config;
 
 typedef struct {
@@ -115,8 +129,9 @@ int pp_cweno_create(const pp_cweno_config *cfg, void *cuda_stream, pp_cweno_t *o
 
 /* Create one handle for nprob independent problems advanced together (each
  * with its own time step).  All configs must share ndim, gamma, precision,
- * the limiter settings and the flux; sizes, domains, boundaries and cfl may
- * differ. */
+ * the limiter settings and the flux, and use the component-wise
+ * reconstruction (PP_ERR_UNSUPPORTED otherwise); sizes, domains, boundaries
+ * and cfl may differ. */
 int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda_stream,
                           pp_cweno_t *out);
 

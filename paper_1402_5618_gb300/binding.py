@@ -19,6 +19,7 @@ PP_OK, PP_ERR_ARG, PP_ERR_STATE, PP_ERR_NONPHYSICAL, PP_ERR_STEPS, PP_ERR_TIMEOU
 PREC_FP64, PREC_MIXED = 0, 1
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
 FLUX_HLLC, FLUX_LLF = 0, 1
+RECON_COMPONENT, RECON_CHARACTERISTIC = 0, 1
 
 
 class Config(C.Structure):
@@ -28,7 +29,7 @@ class Config(C.Structure):
         ("gamma", C.c_double), ("cfl", C.c_double), ("bc", C.c_int * 4),
         ("precision", C.c_int), ("gl_weight", C.c_double), ("eps_weno", C.c_double),
         ("eps_pos", C.c_double), ("cfl_positivity_cap", C.c_int), ("limiter", C.c_int),
-        ("flux", C.c_int),
+        ("flux", C.c_int), ("recon", C.c_int),
     ]
 
 
@@ -115,7 +116,8 @@ def _check(rc: int, where: str, ok=(PP_OK,)):
 
 def make_config(ndim=1, nx=200, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, cfl=0.5,
                 bc=(0, 0, 0, 0), precision=PREC_FP64, gl_weight=1.0 / 12.0, eps_weno=1e-13,
-                eps_pos=1e-13, cfl_positivity_cap=False, limiter=True, flux=FLUX_HLLC) -> Config:
+                eps_pos=1e-13, cfl_positivity_cap=False, limiter=True, flux=FLUX_HLLC,
+                recon=RECON_COMPONENT) -> Config:
     c = Config()
     lib().pp_cweno_config_default(C.byref(c))
     c.ndim, c.nx, c.ny = ndim, nx, (ny if ndim == 2 else 1)
@@ -127,6 +129,7 @@ def make_config(ndim=1, nx=200, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4,
     c.gl_weight, c.eps_weno, c.eps_pos = gl_weight, eps_weno, eps_pos
     c.cfl_positivity_cap, c.limiter = int(cfl_positivity_cap), int(limiter)
     c.flux = int(flux)
+    c.recon = int(recon)
     return c
 
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libppcweno.so")
 SOURCES = ["pp_cweno.cu", "sweep_f64_m8.cu", "sweep_f64_m16.cu", "sweep_f32_m8.cu",
-           "sweep_f32_m16.cu"]
+           "sweep_f32_m16.cu", "char_recon.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include")]

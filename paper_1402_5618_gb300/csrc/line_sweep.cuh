@@ -103,6 +103,9 @@ struct SweepArgs {
   double eps_fixed;   // > 0: fixed limiter epsilon, no control-block checks (operator evaluation)
   int limiter;
   int flux;           // 0 HLLC, 1 local Lax-Friedrichs
+  // FP64 form: face values U^-, U^+ computed by another kernel (FP64
+  // planes in the state's layout); nullptr: the kernel reconstructs them
+  const double *Fm_pre, *Fp_pre;
   Ctl *ctl;
   // batched launch: line table and problem descriptors (nullptr: one problem)
   const LineRef *lines;
@@ -584,646 +587,658 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   }
   __syncthreads();
 
-  // ---------------------------------------------------------------- rows
-  const real *uv = Us + v * UWP + UH;         // u of segment cell c at uv[pad(c)], c in [-2, SEG+2)
-  real *wt = Wt + v * 4 * WP;                 // wt[q*WP + pad(c)]: w0-, w2-, w0+, w2+
-  const int s0 = lo + k * M;                  // first cell of this thread's chunk
-  const int len = max(0, min(M, hi - s0));
-  const int cb = S::pad(k * M);               // padded offset of the chunk's first cell
-  const bool bounded = !PER;
-  auto u_at = [&](int i) -> real { return uv[S::pad(i - lo)]; };
-
-  // the chunk's cells with a two-cell halo, from shared memory into registers
-  auto load_window = [&](real *win) {
-    win[0] = uv[S::pad(k * M - 2)];
-    win[1] = uv[S::pad(k * M - 1)];
-#pragma unroll
-    for (int q = 0; q < M; ++q) win[q + 2] = uv[cb + q];
-    win[M + 2] = uv[S::pad(k * M + M)];
-    win[M + 3] = uv[S::pad(k * M + M + 1)];
-  };
-
-  // a, b of the unmodified position-0 row of side 0 (cell 0) or 1 (cell n-1),
-  // needed by the Sherman-Morrison row at the far end of a periodic system
-  auto far_row = [&](int side, real &a0, real &b0) {
-    const real *y = Rm + (v * 2 + side) * 6 + 2;
-    real q0, q1, q2, one, w0, w1, w2;
-    zratios_any(y[-2], y[-1], y[0], y[1], y[2], eps_w, q0, q1, q2, one);
-    if (side == 0) zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
-    else zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, w0, w1, w2, one);
-    Row<real> r = compact_row02(w0, w2, real(0), real(0), real(0));
-    a0 = r.a;
-    b0 = r.b;
-  };
-
-  // row of the periodic end cell i (0 or n-1), side 0 (minus) or 1 (plus),
-  // from the stored weights; zr = the Sherman-Morrison right-hand side entry
-  auto per_row = [&](int i, int side, real &zr) -> Row<real> {
-    const real *o = wt + 2 * side * WP + S::pad(i - lo);
-    const real xm = u_at(i - 1), x0 = u_at(i), xp = u_at(i + 1);
-    Row<real> r = side == 0 ? compact_row02(o[0], o[WP], xm, x0, xp)
-                            : compact_row02(o[0], o[WP], xp, x0, xm);
-    const int first = side == 0 ? 0 : n - 1, last = side == 0 ? n - 1 : 0;
-    zr = real(0);
-    if (i == first) {          // T = A - u v^T with g = -b at position 0
-      zr = -r.b;
-      r.b = r.b + r.b;
-      r.a = real(0);
-    } else if (i == last) {    // corner removed, b reduced by c a0 / g
-      real a0, b0;
-      far_row(side, a0, b0);
-      zr = r.c;
-      r.b = r.b + r.c * a0 / b0;
-      r.c = real(0);
-    }
-    return r;
-  };
-
-  // ------------------------------------------- weights + chunk maps (F1)
-  // weights are stored for the elimination pass (F5); the rows come from the
-  // register window.  The bounded closure cells store their explicit
-  // WENO5-Z face values in the w0 slots instead (rows 0 x + 1 x + 0 x = f).
-  Fwd<real> fm = fwd_identity<real>(), fp = fwd_identity<real>();
-  {
-    real win[M + 4];
-    load_window(win);
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-      if (j < len) {
-        const int i = s0 + j;
-        real zm = real(0), zp = real(0);
-        Row<real> rm, rp;
-        if (bounded && (i == 0 || i == n - 1)) {
-          real fmv = weno5z_face(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w);
-          real fpv = weno5z_face(win[j + 4], win[j + 3], win[j + 2], win[j + 1], win[j], eps_w);
-          wt[cb + j] = fmv;
-          wt[2 * WP + cb + j] = fpv;
-          rm.a = real(0); rm.b = real(1); rm.c = real(0); rm.r = fmv;
-          rp.a = real(0); rp.b = real(1); rp.c = real(0); rp.r = fpv;
-        } else {
-          real q0, q1, q2, one, w0, w1, w2, v0, v1, v2;
-          zratios_any(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w, q0, q1, q2, one);
-          if constexpr (MIXED) {
-            zweights_pair(q0, q1, q2, one, w0, w2, v0, v2);
-            (void)w1; (void)v1;
-          } else {
-            zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
-            zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, v0, v1, v2, one);
-          }
-          wt[cb + j] = w0;
-          wt[WP + cb + j] = w2;
-          wt[2 * WP + cb + j] = v0;
-          wt[3 * WP + cb + j] = v2;
-          if (PER && (i == 0 || i == n - 1)) {
-            rm = per_row(i, 0, zm);
-            rp = per_row(i, 1, zp);
-          } else {
-            rm = compact_row02(w0, w2, win[j + 1], win[j + 2], win[j + 3]);
-            rp = compact_row02(v0, v2, win[j + 3], win[j + 2], win[j + 1]);
-          }
-        }
-        fwd_push_left<real, PER>(fm, rm, zm);
-        fwd_push_right<real, PER>(fp, rp, zp);
-      }
-    }
-  }
-  fwd_normalise(fm);
-  fwd_normalise(fp);
-
-  // ------------------------------------------- warp inclusive scans (F2)
-  // minus maps accumulate from the lower lanes, plus maps from the higher
-  if constexpr (MIXED) {
-    Fwd2 f2 = fwd2_pack(fm, fp);
-    const float2 one2 = p_set(1.0f), zero2 = p_set(0.0f);
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const bool am = lane >= d, ap = lane + d < 32;
-      Fwd2 o;
-      // every lane executes both shuffles; the select comes after
-#define PPK_SH2(fld, idv)                                                    \
-  {                                                                          \
-    const float tm_ = __shfl_up_sync(0xffffffffu, f2.fld.x, d);              \
-    const float tp_ = __shfl_down_sync(0xffffffffu, f2.fld.y, d);            \
-    o.fld.x = am ? tm_ : idv.x;                                              \
-    o.fld.y = ap ? tp_ : idv.y;                                              \
-  }
-      PPK_SH2(g00, one2); PPK_SH2(g01, zero2); PPK_SH2(g10, zero2); PPK_SH2(g11, one2);
-      PPK_SH2(dP, zero2); PPK_SH2(dQ, zero2); PPK_SH2(mu, one2);
-      if (PER) { PPK_SH2(zP, zero2); PPK_SH2(zQ, zero2); } else { o.zP = zero2; o.zQ = zero2; }
-#undef PPK_SH2
-      f2 = fwd2_compose<PER>(f2, o);   // with the identity where a lane has no partner
-      fwd2_normalise(f2);
-    }
-    fwd2_unpack(f2, fm, fp);
-  } else {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      Fwd<real> o = fwd_shfl<real, PER, true>(fm, d);
-      if (lane >= d) { fm = fwd_compose<real, PER>(fm, o); fwd_normalise(fm); }
-      Fwd<real> q = fwd_shfl<real, PER, false>(fp, d);
-      if (lane + d < 32) { fp = fwd_compose<real, PER>(fp, q); fwd_normalise(fp); }
-    }
-  }
-  if (lane == 31) ex.warp_fwd[v][0][w] = fm;
-  if (lane == 0) ex.warp_fwd[v][1][w] = fp;
-  __syncthreads();
-
-  // ------------------------------------------- CTA segment maps (F3)
-  if (tid < 2 * NV) {
-    int vv = tid >> 1, sd = tid & 1;
-    Fwd<real> sg = fwd_identity<real>();
-    for (int ww = 0; ww < WPV; ++ww) {
-      int wi = sd == 0 ? ww : WPV - 1 - ww;
-      sg = fwd_compose<real, PER>(ex.warp_fwd[vv][sd][wi], sg);
-      fwd_normalise(sg);
-    }
-    ex.seg_fwd[vv][sd] = sg;
-  }
-  cluster.sync();
-
-  // ------------------------------------------- incoming states (F4)
-  // The segment maps of the CTAs ahead of this one on each side (minus: the
-  // lower ranks, applied in rank order; plus: the higher ranks, from the
-  // last one down) applied to the zero state that enters a line end.
-  // Mixed form (latency bound): composed by a tree over 16 lanes, lane q
-  // holding rank q's map (the identity where rank q is not ahead), so the
-  // remote reads happen at once.  FP64 form (bound by the FP64 pipe): one
-  // thread per side and variable applies them in turn, the fewest FP64
-  // operations.
-  real cin = real(0), din = real(0), zin = real(0);
-  int fvv = -1, fsd = 0;
-  if constexpr (MIXED) {
-    if (tid < 2 * NV * 16) {   // whole warps: T >= 2 NV 16 for M <= 16
-      const int grp = tid >> 4, q = tid & 15;
-      const int vv = grp >> 1, sd = grp & 1;
-      Fwd<real> mq = fwd_identity<real>();
-      if (q < R && (sd == 0 ? q < rank : q > rank)) {
-        Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
-        mq = rx->seg_fwd[vv][sd];
-      }
-#pragma unroll
-      for (int d = 1; d < 16; d <<= 1) {
-        Fwd<real> o = fwd_shfl<real, PER, false>(mq, d, 16);   // ranks q + d ...
-        if ((q & (2 * d - 1)) == 0) {
-          mq = sd == 0 ? fwd_compose<real, PER>(o, mq) : fwd_compose<real, PER>(mq, o);
-          fwd_normalise(mq);
-        }
-      }
-      if (q == 0) {
-        fwd_apply<real, PER>(mq, cin, din, zin);
-        fvv = vv;
-        fsd = sd;
-      }
+  // face values computed outside (the characteristic-wise reconstruction,
+  // FP64 form): U^- and U^+ of the segment's cells in the state's layout
+  const bool pre = !MIXED && args.Fm_pre != nullptr;
+  if (pre) {
+    for (int idx = tid; idx < NV * (hi - lo); idx += T) {
+      const int kv = idx / (hi - lo), c = idx - kv * (hi - lo);
+      const long long o = gvar(kv, NV, args.vn, args.vt) * args.ncell + lbase + (long long)(lo + c) * cs;
+      Fm[kv * WP + S::pad(c)] = real(args.Fm_pre[o]);
+      Fp[kv * WP + S::pad(c)] = real(args.Fp_pre[o]);
     }
   } else {
-    if (tid < 2 * NV) {
-      const int vv = tid >> 1, sd = tid & 1;
-      if (sd == 0) {
-        for (int q = 0; q < rank; ++q) {
-          Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
-          fwd_apply<real, PER>(rx->seg_fwd[vv][0], cin, din, zin);
-        }
-      } else {
-        for (int q = R - 1; q > rank; --q) {
-          Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
-          fwd_apply<real, PER>(rx->seg_fwd[vv][1], cin, din, zin);
-        }
-      }
-      fvv = vv;
-      fsd = sd;
-    }
-  }
-  if (fvv >= 0) {   // the state entering each warp of this segment
-    for (int ww = 0; ww < WPV; ++ww) {
-      int wi = fsd == 0 ? ww : WPV - 1 - ww;
-      ex.warp_in[fvv][fsd][wi][0] = cin;
-      ex.warp_in[fvv][fsd][wi][1] = din;
-      ex.warp_in[fvv][fsd][wi][2] = zin;
-      fwd_apply<real, PER>(ex.warp_fwd[fvv][fsd][wi], cin, din, zin);
-    }
-  }
-  __syncthreads();
+    // ---------------------------------------------------------------- rows
+    const real *uv = Us + v * UWP + UH;         // u of segment cell c at uv[pad(c)], c in [-2, SEG+2)
+    real *wt = Wt + v * 4 * WP;                 // wt[q*WP + pad(c)]: w0-, w2-, w0+, w2+
+    const int s0 = lo + k * M;                  // first cell of this thread's chunk
+    const int len = max(0, min(M, hi - s0));
+    const int cb = S::pad(k * M);               // padded offset of the chunk's first cell
+    const bool bounded = !PER;
+    auto u_at = [&](int i) -> real { return uv[S::pad(i - lo)]; };
 
-  // the state after each lane's chunk (its inclusive map applied to the
-  // warp's incoming state), handed to the next lane in elimination order
-  real cpm, dpm, zpm, cpp, dpp, zpp;
-  {
-    const real cw = ex.warp_in[v][0][w][0], dw = ex.warp_in[v][0][w][1], zw = ex.warp_in[v][0][w][2];
-    real c = cw, d = dw, z = zw;
-    fwd_apply<real, PER>(fm, c, d, z);
-    cpm = shfl_up_r(c, 1);
-    dpm = shfl_up_r(d, 1);
-    zpm = PER ? shfl_up_r(z, 1) : real(0);
-    if (lane == 0) { cpm = cw; dpm = dw; zpm = zw; }
-  }
-  {
-    const real cw = ex.warp_in[v][1][w][0], dw = ex.warp_in[v][1][w][1], zw = ex.warp_in[v][1][w][2];
-    real c = cw, d = dw, z = zw;
-    fwd_apply<real, PER>(fp, c, d, z);
-    cpp = shfl_down_r(c, 1);
-    dpp = shfl_down_r(d, 1);
-    zpp = PER ? shfl_down_r(z, 1) : real(0);
-    if (lane == 31) { cpp = cw; dpp = dw; zpp = zw; }
-  }
-
-  // ------------------------------------------- chunk elimination (F5)
-  // Thomas elimination of the chunk from the incoming state, and the chunk's
-  // back-substitution map x_first = A + B x_after accumulated in the same
-  // pass: A = sum_j (prod_{l<j} -c'_l) d'_j, B = prod_l -c'_l.  The minus
-  // system runs over the chunk's cells left to right, the plus system right
-  // to left.  c', d' of a cell overwrite its two weights (read just before by
-  // the same thread); z' stays in registers (periodic lines).
-  // Mixed form: the recurrence runs on the projective state (P, Q, D, Z),
-  // c' = P/Q, d' = D/Q, z' = Z/Q, mapped linearly by a row (P <- c Q,
-  // Q <- b Q - a P, D <- r Q - a D), so consecutive rows depend on each other
-  // through two multiply-adds and the reciprocals 1/Q are off that chain
-  // (over one chunk Q changes by at most M factors b - a c': no rescaling).
-  // FP64 form: the plain recurrence with one division per row, the fewest
-  // FP64 operations.
-  real zmv[PER ? M : 1], zpv[PER ? M : 1];
-  Bwd<real> bm, bp;
-  // a full chunk without a line-end cell: every row is a plain compact row
-  const bool plain = len == M && s0 > 0 && s0 + M < n;
-  bool done5 = false;
-  if constexpr (MIXED) {
-    if (plain) {   // both systems together in paired FP32, no guards
-      float win[M + 4];
-      load_window(win);
-      float *om = wt + cb, *op = wt + 2 * WP + cb;
-      float2 P = make_float2(cpm, cpp), Q = p_set(1.0f), D = make_float2(dpm, dpp);
-      float2 Z = make_float2(zpm, zpp);
-      float2 pi = p_set(1.0f), A = p_set(0.0f), Az = p_set(0.0f);
-#pragma unroll
-      for (int jj = 0; jj < M; ++jj) {
-        const int jm = jj, jp = M - 1 - jj;    // minus left to right, plus right to left
-        float2 a, b, c, r;
-        row2(make_float2(om[jm], op[jp]), make_float2(om[WP + jm], op[WP + jp]),
-             make_float2(win[jm + 1], win[jp + 3]), make_float2(win[jm + 2], win[jp + 2]),
-             make_float2(win[jm + 3], win[jp + 1]), a, b, c, r);
-        const float2 na = p_neg(a);
-        const float2 nq = p_fma(na, P, p_mul(b, Q));
-        D = p_fma(na, D, p_mul(r, Q));
-        if (PER) Z = p_mul(na, Z);            // zero right-hand side away from the ends
-        P = p_mul(c, Q);
-        Q = nq;
-        const float2 iq = make_float2(1.0f / Q.x, 1.0f / Q.y);
-        const float2 co = p_mul(P, iq), dd = p_mul(D, iq);
-        om[jm] = co.x;
-        om[WP + jm] = dd.x;
-        op[jp] = co.y;
-        op[WP + jp] = dd.y;
-        A = p_fma(pi, dd, A);
-        if (PER) {
-          const float2 zz = p_mul(Z, iq);
-          zmv[jm] = zz.x;
-          zpv[jp] = zz.y;
-          Az = p_fma(pi, zz, Az);
-        }
-        pi = p_mul(pi, p_neg(co));
-      }
-      bm.A = A.x; bm.Az = Az.x; bm.B = pi.x;
-      bp.A = A.y; bp.Az = Az.y; bp.B = pi.y;
-      done5 = true;
-    }
-  }
-  if (!done5) {
-    real win[M + 4];
-    load_window(win);
-    // projective state (mixed) or (c', -, d', z') (FP64) of each side
-    real Pm = cpm, Qm = real(1), Dm = dpm, Zm = zpm;
-    real Pp = cpp, Qp = real(1), Dp = dpp, Zp = zpp;
-    real pim = real(1), Am = real(0), Azm = real(0);
-    real pip = real(1), Ap = real(0), Azp = real(0);
-    auto elim = [&](const Row<real> &r, real zr, real &P, real &Qs, real &D, real &Z,
-                    real &co, real &dout, real &zo) {
-      if constexpr (MIXED) {
-        real nq = r.b * Qs - r.a * P;
-        D = r.r * Qs - r.a * D;
-        if (PER) Z = zr * Qs - r.a * Z;
-        P = r.c * Qs;
-        Qs = nq;
-        real iq = real(1) / Qs;
-        co = P * iq;
-        dout = D * iq;
-        zo = PER ? Z * iq : real(0);
-      } else {
-        real ip = real(1) / (r.b - r.a * P);
-        D = (r.r - r.a * D) * ip;
-        if (PER) Z = (zr - r.a * Z) * ip;
-        P = r.c * ip;
-        co = P;
-        dout = D;
-        zo = Z;
-      }
+    // the chunk's cells with a two-cell halo, from shared memory into registers
+    auto load_window = [&](real *win) {
+      win[0] = uv[S::pad(k * M - 2)];
+      win[1] = uv[S::pad(k * M - 1)];
+  #pragma unroll
+      for (int q = 0; q < M; ++q) win[q + 2] = uv[cb + q];
+      win[M + 2] = uv[S::pad(k * M + M)];
+      win[M + 3] = uv[S::pad(k * M + M + 1)];
     };
-#pragma unroll
-    for (int jj = 0; jj < M; ++jj) {
-      {   // minus: cell s0 + jj
-        const int j = jj;
+
+    // a, b of the unmodified position-0 row of side 0 (cell 0) or 1 (cell n-1),
+    // needed by the Sherman-Morrison row at the far end of a periodic system
+    auto far_row = [&](int side, real &a0, real &b0) {
+      const real *y = Rm + (v * 2 + side) * 6 + 2;
+      real q0, q1, q2, one, w0, w1, w2;
+      zratios_any(y[-2], y[-1], y[0], y[1], y[2], eps_w, q0, q1, q2, one);
+      if (side == 0) zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
+      else zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, w0, w1, w2, one);
+      Row<real> r = compact_row02(w0, w2, real(0), real(0), real(0));
+      a0 = r.a;
+      b0 = r.b;
+    };
+
+    // row of the periodic end cell i (0 or n-1), side 0 (minus) or 1 (plus),
+    // from the stored weights; zr = the Sherman-Morrison right-hand side entry
+    auto per_row = [&](int i, int side, real &zr) -> Row<real> {
+      const real *o = wt + 2 * side * WP + S::pad(i - lo);
+      const real xm = u_at(i - 1), x0 = u_at(i), xp = u_at(i + 1);
+      Row<real> r = side == 0 ? compact_row02(o[0], o[WP], xm, x0, xp)
+                              : compact_row02(o[0], o[WP], xp, x0, xm);
+      const int first = side == 0 ? 0 : n - 1, last = side == 0 ? n - 1 : 0;
+      zr = real(0);
+      if (i == first) {          // T = A - u v^T with g = -b at position 0
+        zr = -r.b;
+        r.b = r.b + r.b;
+        r.a = real(0);
+      } else if (i == last) {    // corner removed, b reduced by c a0 / g
+        real a0, b0;
+        far_row(side, a0, b0);
+        zr = r.c;
+        r.b = r.b + r.c * a0 / b0;
+        r.c = real(0);
+      }
+      return r;
+    };
+
+    // ------------------------------------------- weights + chunk maps (F1)
+    // weights are stored for the elimination pass (F5); the rows come from the
+    // register window.  The bounded closure cells store their explicit
+    // WENO5-Z face values in the w0 slots instead (rows 0 x + 1 x + 0 x = f).
+    Fwd<real> fm = fwd_identity<real>(), fp = fwd_identity<real>();
+    {
+      real win[M + 4];
+      load_window(win);
+  #pragma unroll
+      for (int j = 0; j < M; ++j) {
         if (j < len) {
           const int i = s0 + j;
-          real *o = wt + cb + j;
-          Row<real> r;
-          real zr = real(0);
+          real zm = real(0), zp = real(0);
+          Row<real> rm, rp;
           if (bounded && (i == 0 || i == n - 1)) {
-            r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
-          } else if (PER && (i == 0 || i == n - 1)) {
-            r = per_row(i, 0, zr);
+            real fmv = weno5z_face(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w);
+            real fpv = weno5z_face(win[j + 4], win[j + 3], win[j + 2], win[j + 1], win[j], eps_w);
+            wt[cb + j] = fmv;
+            wt[2 * WP + cb + j] = fpv;
+            rm.a = real(0); rm.b = real(1); rm.c = real(0); rm.r = fmv;
+            rp.a = real(0); rp.b = real(1); rp.c = real(0); rp.r = fpv;
           } else {
-            r = compact_row02(o[0], o[WP], win[j + 1], win[j + 2], win[j + 3]);
+            real q0, q1, q2, one, w0, w1, w2, v0, v1, v2;
+            zratios_any(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w, q0, q1, q2, one);
+            if constexpr (MIXED) {
+              zweights_pair(q0, q1, q2, one, w0, w2, v0, v2);
+              (void)w1; (void)v1;
+            } else {
+              zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
+              zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, v0, v1, v2, one);
+            }
+            wt[cb + j] = w0;
+            wt[WP + cb + j] = w2;
+            wt[2 * WP + cb + j] = v0;
+            wt[3 * WP + cb + j] = v2;
+            if (PER && (i == 0 || i == n - 1)) {
+              rm = per_row(i, 0, zm);
+              rp = per_row(i, 1, zp);
+            } else {
+              rm = compact_row02(w0, w2, win[j + 1], win[j + 2], win[j + 3]);
+              rp = compact_row02(v0, v2, win[j + 3], win[j + 2], win[j + 1]);
+            }
           }
-          real co, dd, zz;
-          elim(r, zr, Pm, Qm, Dm, Zm, co, dd, zz);
-          o[0] = co;
-          o[WP] = dd;
-          if (PER) zmv[j] = zz;
-          Am += pim * dd;
-          if (PER) Azm += pim * zz;
-          pim *= -co;
-        }
-      }
-      {   // plus: cell s0 + M - 1 - jj
-        const int j = M - 1 - jj;
-        if (j < len) {
-          const int i = s0 + j;
-          real *o = wt + 2 * WP + cb + j;
-          Row<real> r;
-          real zr = real(0);
-          if (bounded && (i == 0 || i == n - 1)) {
-            r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
-          } else if (PER && (i == 0 || i == n - 1)) {
-            r = per_row(i, 1, zr);
-          } else {
-            r = compact_row02(o[0], o[WP], win[j + 3], win[j + 2], win[j + 1]);
-          }
-          real co, dd, zz;
-          elim(r, zr, Pp, Qp, Dp, Zp, co, dd, zz);
-          o[0] = co;
-          o[WP] = dd;
-          if (PER) zpv[j] = zz;
-          Ap += pip * dd;
-          if (PER) Azp += pip * zz;
-          pip *= -co;
+          fwd_push_left<real, PER>(fm, rm, zm);
+          fwd_push_right<real, PER>(fp, rp, zp);
         }
       }
     }
-    bm.A = Am; bm.Az = Azm; bm.B = pim;
-    bp.A = Ap; bp.Az = Azp; bp.B = pip;
-  }
+    fwd_normalise(fm);
+    fwd_normalise(fp);
 
-  // ------------------------------------------- backward scans (F6)
-  // minus back maps accumulate from the higher lanes (its back substitution
-  // runs right to left), plus maps from the lower lanes
-  Bwd<real> bm_in = bm, bp_in = bp;
-  if constexpr (MIXED) {
-    Bwd2 b2;
-    b2.A = make_float2(bm.A, bp.A);
-    b2.B = make_float2(bm.B, bp.B);
-    b2.Az = make_float2(bm.Az, bp.Az);
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const bool am = lane + d < 32, ap = lane >= d;
-      Bwd2 o;
-      {
-        float tm = __shfl_down_sync(0xffffffffu, b2.A.x, d), tp = __shfl_up_sync(0xffffffffu, b2.A.y, d);
-        o.A = make_float2(am ? tm : 0.0f, ap ? tp : 0.0f);
-      }
-      {
-        float tm = __shfl_down_sync(0xffffffffu, b2.B.x, d), tp = __shfl_up_sync(0xffffffffu, b2.B.y, d);
-        o.B = make_float2(am ? tm : 1.0f, ap ? tp : 1.0f);
-      }
-      if (PER) {
-        float tm = __shfl_down_sync(0xffffffffu, b2.Az.x, d), tp = __shfl_up_sync(0xffffffffu, b2.Az.y, d);
-        o.Az = make_float2(am ? tm : 0.0f, ap ? tp : 0.0f);
-      } else {
-        o.Az = p_set(0.0f);
-      }
-      b2 = bwd2_compose(b2, o);   // with the identity where a lane has no partner
-    }
-    bm_in.A = b2.A.x; bm_in.B = b2.B.x; bm_in.Az = b2.Az.x;
-    bp_in.A = b2.A.y; bp_in.B = b2.B.y; bp_in.Az = b2.Az.y;
-  } else {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      Bwd<real> o;
-      o.A = shfl_down_r(bm_in.A, d); o.B = shfl_down_r(bm_in.B, d);
-      o.Az = PER ? shfl_down_r(bm_in.Az, d) : real(0);
-      if (lane + d < 32) bm_in = bwd_compose(bm_in, o);
-      Bwd<real> q;
-      q.A = shfl_up_r(bp_in.A, d); q.B = shfl_up_r(bp_in.B, d);
-      q.Az = PER ? shfl_up_r(bp_in.Az, d) : real(0);
-      if (lane >= d) bp_in = bwd_compose(bp_in, q);
-    }
-  }
-  if (lane == 0) ex.warp_bwd[v][0][w] = bm_in;
-  if (lane == 31) ex.warp_bwd[v][1][w] = bp_in;
-  __syncthreads();
-
-  // ------------------------------------------- segment back maps (F7)
-  if (tid < 2 * NV) {
-    int vv = tid >> 1, sd = tid & 1;
-    Bwd<real> sg;
-    sg.A = real(0); sg.B = real(1); sg.Az = real(0);
-    // minus: first cell of the segment = warp 0 o warp 1 o ...; plus: the
-    // last warp's map is applied first
-    for (int ww = WPV - 1; ww >= 0; --ww) {
-      int wi = sd == 0 ? ww : WPV - 1 - ww;
-      sg = bwd_compose(ex.warp_bwd[vv][sd][wi], sg);
-    }
-    ex.seg_bwd[vv][sd] = sg;
-  }
-  cluster.sync();
-  // back substitution entering this segment from the far side: the back maps
-  // of the CTAs behind it in that order (minus: the higher ranks, the last
-  // acting first; plus: the lower ranks, rank 0 acting first); x = 0 after
-  // the line end.  Mixed form: a tree over 16 lanes as in F4; FP64 form: one
-  // thread per side and variable.
-  {
-    real xb = real(0), zb = real(0);
-    int bvv = -1, bsd = 0;
+    // ------------------------------------------- warp inclusive scans (F2)
+    // minus maps accumulate from the lower lanes, plus maps from the higher
     if constexpr (MIXED) {
-      if (tid < 2 * NV * 16) {
+      Fwd2 f2 = fwd2_pack(fm, fp);
+      const float2 one2 = p_set(1.0f), zero2 = p_set(0.0f);
+  #pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const bool am = lane >= d, ap = lane + d < 32;
+        Fwd2 o;
+        // every lane executes both shuffles; the select comes after
+  #define PPK_SH2(fld, idv)                                                    \
+    {                                                                          \
+      const float tm_ = __shfl_up_sync(0xffffffffu, f2.fld.x, d);              \
+      const float tp_ = __shfl_down_sync(0xffffffffu, f2.fld.y, d);            \
+      o.fld.x = am ? tm_ : idv.x;                                              \
+      o.fld.y = ap ? tp_ : idv.y;                                              \
+    }
+        PPK_SH2(g00, one2); PPK_SH2(g01, zero2); PPK_SH2(g10, zero2); PPK_SH2(g11, one2);
+        PPK_SH2(dP, zero2); PPK_SH2(dQ, zero2); PPK_SH2(mu, one2);
+        if (PER) { PPK_SH2(zP, zero2); PPK_SH2(zQ, zero2); } else { o.zP = zero2; o.zQ = zero2; }
+  #undef PPK_SH2
+        f2 = fwd2_compose<PER>(f2, o);   // with the identity where a lane has no partner
+        fwd2_normalise(f2);
+      }
+      fwd2_unpack(f2, fm, fp);
+    } else {
+  #pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        Fwd<real> o = fwd_shfl<real, PER, true>(fm, d);
+        if (lane >= d) { fm = fwd_compose<real, PER>(fm, o); fwd_normalise(fm); }
+        Fwd<real> q = fwd_shfl<real, PER, false>(fp, d);
+        if (lane + d < 32) { fp = fwd_compose<real, PER>(fp, q); fwd_normalise(fp); }
+      }
+    }
+    if (lane == 31) ex.warp_fwd[v][0][w] = fm;
+    if (lane == 0) ex.warp_fwd[v][1][w] = fp;
+    __syncthreads();
+
+    // ------------------------------------------- CTA segment maps (F3)
+    if (tid < 2 * NV) {
+      int vv = tid >> 1, sd = tid & 1;
+      Fwd<real> sg = fwd_identity<real>();
+      for (int ww = 0; ww < WPV; ++ww) {
+        int wi = sd == 0 ? ww : WPV - 1 - ww;
+        sg = fwd_compose<real, PER>(ex.warp_fwd[vv][sd][wi], sg);
+        fwd_normalise(sg);
+      }
+      ex.seg_fwd[vv][sd] = sg;
+    }
+    cluster.sync();
+
+    // ------------------------------------------- incoming states (F4)
+    // The segment maps of the CTAs ahead of this one on each side (minus: the
+    // lower ranks, applied in rank order; plus: the higher ranks, from the
+    // last one down) applied to the zero state that enters a line end.
+    // Mixed form (latency bound): composed by a tree over 16 lanes, lane q
+    // holding rank q's map (the identity where rank q is not ahead), so the
+    // remote reads happen at once.  FP64 form (bound by the FP64 pipe): one
+    // thread per side and variable applies them in turn, the fewest FP64
+    // operations.
+    real cin = real(0), din = real(0), zin = real(0);
+    int fvv = -1, fsd = 0;
+    if constexpr (MIXED) {
+      if (tid < 2 * NV * 16) {   // whole warps: T >= 2 NV 16 for M <= 16
         const int grp = tid >> 4, q = tid & 15;
         const int vv = grp >> 1, sd = grp & 1;
-        Bwd<real> bq;
-        bq.A = real(0); bq.B = real(1); bq.Az = real(0);
-        if (q < R && (sd == 0 ? q > rank : q < rank)) {
+        Fwd<real> mq = fwd_identity<real>();
+        if (q < R && (sd == 0 ? q < rank : q > rank)) {
           Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
-          bq = rx->seg_bwd[vv][sd];
+          mq = rx->seg_fwd[vv][sd];
         }
-#pragma unroll
+  #pragma unroll
         for (int d = 1; d < 16; d <<= 1) {
-          Bwd<real> o;
-          o.A = shfl_down_r(bq.A, d, 16);
-          o.B = shfl_down_r(bq.B, d, 16);
-          o.Az = PER ? shfl_down_r(bq.Az, d, 16) : real(0);
-          if ((q & (2 * d - 1)) == 0) bq = sd == 0 ? bwd_compose(bq, o) : bwd_compose(o, bq);
+          Fwd<real> o = fwd_shfl<real, PER, false>(mq, d, 16);   // ranks q + d ...
+          if ((q & (2 * d - 1)) == 0) {
+            mq = sd == 0 ? fwd_compose<real, PER>(o, mq) : fwd_compose<real, PER>(mq, o);
+            fwd_normalise(mq);
+          }
         }
         if (q == 0) {
-          xb = bq.A;
-          zb = bq.Az;
-          bvv = vv;
-          bsd = sd;
+          fwd_apply<real, PER>(mq, cin, din, zin);
+          fvv = vv;
+          fsd = sd;
         }
       }
     } else {
       if (tid < 2 * NV) {
         const int vv = tid >> 1, sd = tid & 1;
         if (sd == 0) {
-          for (int q = R - 1; q > rank; --q) {
-            Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
-            Bwd<real> b = rx->seg_bwd[vv][0];
-            xb = b.A + b.B * xb;
-            zb = b.Az + b.B * zb;
-          }
-        } else {
           for (int q = 0; q < rank; ++q) {
             Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
-            Bwd<real> b = rx->seg_bwd[vv][1];
-            xb = b.A + b.B * xb;
-            zb = b.Az + b.B * zb;
+            fwd_apply<real, PER>(rx->seg_fwd[vv][0], cin, din, zin);
+          }
+        } else {
+          for (int q = R - 1; q > rank; --q) {
+            Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
+            fwd_apply<real, PER>(rx->seg_fwd[vv][1], cin, din, zin);
           }
         }
-        bvv = vv;
-        bsd = sd;
+        fvv = vv;
+        fsd = sd;
       }
     }
-    if (bvv >= 0) {
+    if (fvv >= 0) {   // the state entering each warp of this segment
       for (int ww = 0; ww < WPV; ++ww) {
-        int wi = bsd == 0 ? WPV - 1 - ww : ww;
-        ex.warp_xn[bvv][bsd][wi][0] = xb;
-        ex.warp_xn[bvv][bsd][wi][1] = zb;
-        Bwd<real> b = ex.warp_bwd[bvv][bsd][wi];
-        xb = b.A + b.B * xb;
-        zb = b.Az + b.B * zb;
+        int wi = fsd == 0 ? ww : WPV - 1 - ww;
+        ex.warp_in[fvv][fsd][wi][0] = cin;
+        ex.warp_in[fvv][fsd][wi][1] = din;
+        ex.warp_in[fvv][fsd][wi][2] = zin;
+        fwd_apply<real, PER>(ex.warp_fwd[fvv][fsd][wi], cin, din, zin);
       }
     }
-  }
-  __syncthreads();
+    __syncthreads();
 
-  // ------------------------------------------- back substitution (F8)
-  // minus from the chunk's last cell down, plus from its first cell up; c', d'
-  // come from the weight slots, the solution goes to Fm / Fp.  The value
-  // entering a chunk is the value leaving the neighbouring lane's chunk (its
-  // inclusive back map applied to the warp's entering value).
-  real xm, zm_, xp, zp_;
-  {
-    const real xn = ex.warp_xn[v][0][w][0], zn = ex.warp_xn[v][0][w][1];
-    const real xo = bm_in.A + bm_in.B * xn, zo = bm_in.Az + bm_in.B * zn;
-    xm = shfl_down_r(xo, 1);
-    zm_ = PER ? shfl_down_r(zo, 1) : real(0);
-    if (lane == 31) { xm = xn; zm_ = zn; }
-  }
-  {
-    const real xn = ex.warp_xn[v][1][w][0], zn = ex.warp_xn[v][1][w][1];
-    const real xo = bp_in.A + bp_in.B * xn, zo = bp_in.Az + bp_in.B * zn;
-    xp = shfl_up_r(xo, 1);
-    zp_ = PER ? shfl_up_r(zo, 1) : real(0);
-    if (lane == 0) { xp = xn; zp_ = zn; }
-  }
-  real zmo[PER ? M : 1], zpo[PER ? M : 1];
-  bool done8 = false;
-  if constexpr (MIXED) {
-    if (plain) {   // both systems together, no guards
-      const float *om = wt + cb, *op = wt + 2 * WP + cb;
-      float *dm = Fm + v * WP + cb, *dp = Fp + v * WP + cb;
-      float2 x2 = make_float2(xm, xp), z2 = make_float2(zm_, zp_);
-#pragma unroll
+    // the state after each lane's chunk (its inclusive map applied to the
+    // warp's incoming state), handed to the next lane in elimination order
+    real cpm, dpm, zpm, cpp, dpp, zpp;
+    {
+      const real cw = ex.warp_in[v][0][w][0], dw = ex.warp_in[v][0][w][1], zw = ex.warp_in[v][0][w][2];
+      real c = cw, d = dw, z = zw;
+      fwd_apply<real, PER>(fm, c, d, z);
+      cpm = shfl_up_r(c, 1);
+      dpm = shfl_up_r(d, 1);
+      zpm = PER ? shfl_up_r(z, 1) : real(0);
+      if (lane == 0) { cpm = cw; dpm = dw; zpm = zw; }
+    }
+    {
+      const real cw = ex.warp_in[v][1][w][0], dw = ex.warp_in[v][1][w][1], zw = ex.warp_in[v][1][w][2];
+      real c = cw, d = dw, z = zw;
+      fwd_apply<real, PER>(fp, c, d, z);
+      cpp = shfl_down_r(c, 1);
+      dpp = shfl_down_r(d, 1);
+      zpp = PER ? shfl_down_r(z, 1) : real(0);
+      if (lane == 31) { cpp = cw; dpp = dw; zpp = zw; }
+    }
+
+    // ------------------------------------------- chunk elimination (F5)
+    // Thomas elimination of the chunk from the incoming state, and the chunk's
+    // back-substitution map x_first = A + B x_after accumulated in the same
+    // pass: A = sum_j (prod_{l<j} -c'_l) d'_j, B = prod_l -c'_l.  The minus
+    // system runs over the chunk's cells left to right, the plus system right
+    // to left.  c', d' of a cell overwrite its two weights (read just before by
+    // the same thread); z' stays in registers (periodic lines).
+    // Mixed form: the recurrence runs on the projective state (P, Q, D, Z),
+    // c' = P/Q, d' = D/Q, z' = Z/Q, mapped linearly by a row (P <- c Q,
+    // Q <- b Q - a P, D <- r Q - a D), so consecutive rows depend on each other
+    // through two multiply-adds and the reciprocals 1/Q are off that chain
+    // (over one chunk Q changes by at most M factors b - a c': no rescaling).
+    // FP64 form: the plain recurrence with one division per row, the fewest
+    // FP64 operations.
+    real zmv[PER ? M : 1], zpv[PER ? M : 1];
+    Bwd<real> bm, bp;
+    // a full chunk without a line-end cell: every row is a plain compact row
+    const bool plain = len == M && s0 > 0 && s0 + M < n;
+    bool done5 = false;
+    if constexpr (MIXED) {
+      if (plain) {   // both systems together in paired FP32, no guards
+        float win[M + 4];
+        load_window(win);
+        float *om = wt + cb, *op = wt + 2 * WP + cb;
+        float2 P = make_float2(cpm, cpp), Q = p_set(1.0f), D = make_float2(dpm, dpp);
+        float2 Z = make_float2(zpm, zpp);
+        float2 pi = p_set(1.0f), A = p_set(0.0f), Az = p_set(0.0f);
+  #pragma unroll
+        for (int jj = 0; jj < M; ++jj) {
+          const int jm = jj, jp = M - 1 - jj;    // minus left to right, plus right to left
+          float2 a, b, c, r;
+          row2(make_float2(om[jm], op[jp]), make_float2(om[WP + jm], op[WP + jp]),
+               make_float2(win[jm + 1], win[jp + 3]), make_float2(win[jm + 2], win[jp + 2]),
+               make_float2(win[jm + 3], win[jp + 1]), a, b, c, r);
+          const float2 na = p_neg(a);
+          const float2 nq = p_fma(na, P, p_mul(b, Q));
+          D = p_fma(na, D, p_mul(r, Q));
+          if (PER) Z = p_mul(na, Z);            // zero right-hand side away from the ends
+          P = p_mul(c, Q);
+          Q = nq;
+          const float2 iq = make_float2(1.0f / Q.x, 1.0f / Q.y);
+          const float2 co = p_mul(P, iq), dd = p_mul(D, iq);
+          om[jm] = co.x;
+          om[WP + jm] = dd.x;
+          op[jp] = co.y;
+          op[WP + jp] = dd.y;
+          A = p_fma(pi, dd, A);
+          if (PER) {
+            const float2 zz = p_mul(Z, iq);
+            zmv[jm] = zz.x;
+            zpv[jp] = zz.y;
+            Az = p_fma(pi, zz, Az);
+          }
+          pi = p_mul(pi, p_neg(co));
+        }
+        bm.A = A.x; bm.Az = Az.x; bm.B = pi.x;
+        bp.A = A.y; bp.Az = Az.y; bp.B = pi.y;
+        done5 = true;
+      }
+    }
+    if (!done5) {
+      real win[M + 4];
+      load_window(win);
+      // projective state (mixed) or (c', -, d', z') (FP64) of each side
+      real Pm = cpm, Qm = real(1), Dm = dpm, Zm = zpm;
+      real Pp = cpp, Qp = real(1), Dp = dpp, Zp = zpp;
+      real pim = real(1), Am = real(0), Azm = real(0);
+      real pip = real(1), Ap = real(0), Azp = real(0);
+      auto elim = [&](const Row<real> &r, real zr, real &P, real &Qs, real &D, real &Z,
+                      real &co, real &dout, real &zo) {
+        if constexpr (MIXED) {
+          real nq = r.b * Qs - r.a * P;
+          D = r.r * Qs - r.a * D;
+          if (PER) Z = zr * Qs - r.a * Z;
+          P = r.c * Qs;
+          Qs = nq;
+          real iq = real(1) / Qs;
+          co = P * iq;
+          dout = D * iq;
+          zo = PER ? Z * iq : real(0);
+        } else {
+          real ip = real(1) / (r.b - r.a * P);
+          D = (r.r - r.a * D) * ip;
+          if (PER) Z = (zr - r.a * Z) * ip;
+          P = r.c * ip;
+          co = P;
+          dout = D;
+          zo = Z;
+        }
+      };
+  #pragma unroll
       for (int jj = 0; jj < M; ++jj) {
-        const int jm = M - 1 - jj, jp = jj;
-        const float2 nc = make_float2(-om[jm], -op[jp]);
-        x2 = p_fma(nc, x2, make_float2(om[WP + jm], op[WP + jp]));
-        dm[jm] = x2.x;
-        dp[jp] = x2.y;
+        {   // minus: cell s0 + jj
+          const int j = jj;
+          if (j < len) {
+            const int i = s0 + j;
+            real *o = wt + cb + j;
+            Row<real> r;
+            real zr = real(0);
+            if (bounded && (i == 0 || i == n - 1)) {
+              r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
+            } else if (PER && (i == 0 || i == n - 1)) {
+              r = per_row(i, 0, zr);
+            } else {
+              r = compact_row02(o[0], o[WP], win[j + 1], win[j + 2], win[j + 3]);
+            }
+            real co, dd, zz;
+            elim(r, zr, Pm, Qm, Dm, Zm, co, dd, zz);
+            o[0] = co;
+            o[WP] = dd;
+            if (PER) zmv[j] = zz;
+            Am += pim * dd;
+            if (PER) Azm += pim * zz;
+            pim *= -co;
+          }
+        }
+        {   // plus: cell s0 + M - 1 - jj
+          const int j = M - 1 - jj;
+          if (j < len) {
+            const int i = s0 + j;
+            real *o = wt + 2 * WP + cb + j;
+            Row<real> r;
+            real zr = real(0);
+            if (bounded && (i == 0 || i == n - 1)) {
+              r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
+            } else if (PER && (i == 0 || i == n - 1)) {
+              r = per_row(i, 1, zr);
+            } else {
+              r = compact_row02(o[0], o[WP], win[j + 3], win[j + 2], win[j + 1]);
+            }
+            real co, dd, zz;
+            elim(r, zr, Pp, Qp, Dp, Zp, co, dd, zz);
+            o[0] = co;
+            o[WP] = dd;
+            if (PER) zpv[j] = zz;
+            Ap += pip * dd;
+            if (PER) Azp += pip * zz;
+            pip *= -co;
+          }
+        }
+      }
+      bm.A = Am; bm.Az = Azm; bm.B = pim;
+      bp.A = Ap; bp.Az = Azp; bp.B = pip;
+    }
+
+    // ------------------------------------------- backward scans (F6)
+    // minus back maps accumulate from the higher lanes (its back substitution
+    // runs right to left), plus maps from the lower lanes
+    Bwd<real> bm_in = bm, bp_in = bp;
+    if constexpr (MIXED) {
+      Bwd2 b2;
+      b2.A = make_float2(bm.A, bp.A);
+      b2.B = make_float2(bm.B, bp.B);
+      b2.Az = make_float2(bm.Az, bp.Az);
+  #pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const bool am = lane + d < 32, ap = lane >= d;
+        Bwd2 o;
+        {
+          float tm = __shfl_down_sync(0xffffffffu, b2.A.x, d), tp = __shfl_up_sync(0xffffffffu, b2.A.y, d);
+          o.A = make_float2(am ? tm : 0.0f, ap ? tp : 0.0f);
+        }
+        {
+          float tm = __shfl_down_sync(0xffffffffu, b2.B.x, d), tp = __shfl_up_sync(0xffffffffu, b2.B.y, d);
+          o.B = make_float2(am ? tm : 1.0f, ap ? tp : 1.0f);
+        }
         if (PER) {
-          z2 = p_fma(nc, z2, make_float2(zmv[jm], zpv[jp]));
-          zmo[jm] = z2.x;
-          zpo[jp] = z2.y;
+          float tm = __shfl_down_sync(0xffffffffu, b2.Az.x, d), tp = __shfl_up_sync(0xffffffffu, b2.Az.y, d);
+          o.Az = make_float2(am ? tm : 0.0f, ap ? tp : 0.0f);
+        } else {
+          o.Az = p_set(0.0f);
         }
+        b2 = bwd2_compose(b2, o);   // with the identity where a lane has no partner
       }
-      done8 = true;
-    }
-  }
-  if (!done8) {
-    {
-      const real *o = wt + cb;
-      real *dst = Fm + v * WP + cb;
-      real x = xm, z = zm_;
-#pragma unroll
-      for (int jj = 0; jj < M; ++jj) {
-        const int j = M - 1 - jj;
-        if (j < len) {
-          const real c = o[j];
-          x = o[WP + j] - c * x;
-          dst[j] = x;
-          if (PER) {
-            z = zmv[j] - c * z;
-            zmo[j] = z;
-          }
-        }
+      bm_in.A = b2.A.x; bm_in.B = b2.B.x; bm_in.Az = b2.Az.x;
+      bp_in.A = b2.A.y; bp_in.B = b2.B.y; bp_in.Az = b2.Az.y;
+    } else {
+  #pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        Bwd<real> o;
+        o.A = shfl_down_r(bm_in.A, d); o.B = shfl_down_r(bm_in.B, d);
+        o.Az = PER ? shfl_down_r(bm_in.Az, d) : real(0);
+        if (lane + d < 32) bm_in = bwd_compose(bm_in, o);
+        Bwd<real> q;
+        q.A = shfl_up_r(bp_in.A, d); q.B = shfl_up_r(bp_in.B, d);
+        q.Az = PER ? shfl_up_r(bp_in.Az, d) : real(0);
+        if (lane >= d) bp_in = bwd_compose(bp_in, q);
       }
     }
-    {
-      const real *o = wt + 2 * WP + cb;
-      real *dst = Fp + v * WP + cb;
-      real x = xp, z = zp_;
-#pragma unroll
-      for (int j = 0; j < M; ++j) {
-        if (j < len) {
-          const real c = o[j];
-          x = o[WP + j] - c * x;
-          dst[j] = x;
-          if (PER) {
-            z = zpv[j] - c * z;
-            zpo[j] = z;
-          }
-        }
-      }
-    }
-  }
+    if (lane == 0) ex.warp_bwd[v][0][w] = bm_in;
+    if (lane == 31) ex.warp_bwd[v][1][w] = bp_in;
+    __syncthreads();
 
-  if (PER) {
-    // Sherman-Morrison correction x = y - (v.y)/(1 + v.z) z, with
-    // v = e_first + (corner_first / g) e_last and corner_first / g = -a0/b0
-    // of the unmodified position-0 row; the scalars in FP64.  zmo, zpo are
-    // indexed by the chunk's cells.
-    real zm_last = real(0), zp_last = real(0);
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-      if (j == len - 1) { zm_last = zmo[j]; zp_last = zpo[j]; }
-    }
-    if (len > 0 && s0 == 0) {              // cell 0: minus first, plus last
-      real a0, b0;
-      far_row(0, a0, b0);
-      ex.sm[v][0][4] = -(double)a0 / (double)b0;
-      ex.sm[v][0][0] = Fm[v * WP + 0];
-      ex.sm[v][0][1] = zmo[0];
-      ex.sm[v][1][2] = Fp[v * WP + 0];
-      ex.sm[v][1][3] = zpo[0];
-    }
-    if (len > 0 && s0 + len == n) {        // cell n-1: plus first, minus last
-      real a0, b0;
-      far_row(1, a0, b0);
-      ex.sm[v][1][4] = -(double)a0 / (double)b0;
-      ex.sm[v][1][0] = Fp[v * WP + S::pad(n - 1 - lo)];
-      ex.sm[v][1][1] = zp_last;
-      ex.sm[v][0][2] = Fm[v * WP + S::pad(n - 1 - lo)];
-      ex.sm[v][0][3] = zm_last;
+    // ------------------------------------------- segment back maps (F7)
+    if (tid < 2 * NV) {
+      int vv = tid >> 1, sd = tid & 1;
+      Bwd<real> sg;
+      sg.A = real(0); sg.B = real(1); sg.Az = real(0);
+      // minus: first cell of the segment = warp 0 o warp 1 o ...; plus: the
+      // last warp's map is applied first
+      for (int ww = WPV - 1; ww >= 0; --ww) {
+        int wi = sd == 0 ? ww : WPV - 1 - ww;
+        sg = bwd_compose(ex.warp_bwd[vv][sd][wi], sg);
+      }
+      ex.seg_bwd[vv][sd] = sg;
     }
     cluster.sync();
+    // back substitution entering this segment from the far side: the back maps
+    // of the CTAs behind it in that order (minus: the higher ranks, the last
+    // acting first; plus: the lower ranks, rank 0 acting first); x = 0 after
+    // the line end.  Mixed form: a tree over 16 lanes as in F4; FP64 form: one
+    // thread per side and variable.
     {
-      Exch<real, NV, WPV> *r0 = cluster.map_shared_rank(&ex, 0);
-      Exch<real, NV, WPV> *rl = cluster.map_shared_rank(&ex, R - 1);
-      double facm = (r0->sm[v][0][0] + r0->sm[v][0][4] * rl->sm[v][0][2]) /
-                    (1.0 + r0->sm[v][0][1] + r0->sm[v][0][4] * rl->sm[v][0][3]);
-      double facp = (rl->sm[v][1][0] + rl->sm[v][1][4] * r0->sm[v][1][2]) /
-                    (1.0 + rl->sm[v][1][1] + rl->sm[v][1][4] * r0->sm[v][1][3]);
-      real fm_ = real(facm), fp_ = real(facp);
-#pragma unroll
+      real xb = real(0), zb = real(0);
+      int bvv = -1, bsd = 0;
+      if constexpr (MIXED) {
+        if (tid < 2 * NV * 16) {
+          const int grp = tid >> 4, q = tid & 15;
+          const int vv = grp >> 1, sd = grp & 1;
+          Bwd<real> bq;
+          bq.A = real(0); bq.B = real(1); bq.Az = real(0);
+          if (q < R && (sd == 0 ? q > rank : q < rank)) {
+            Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
+            bq = rx->seg_bwd[vv][sd];
+          }
+  #pragma unroll
+          for (int d = 1; d < 16; d <<= 1) {
+            Bwd<real> o;
+            o.A = shfl_down_r(bq.A, d, 16);
+            o.B = shfl_down_r(bq.B, d, 16);
+            o.Az = PER ? shfl_down_r(bq.Az, d, 16) : real(0);
+            if ((q & (2 * d - 1)) == 0) bq = sd == 0 ? bwd_compose(bq, o) : bwd_compose(o, bq);
+          }
+          if (q == 0) {
+            xb = bq.A;
+            zb = bq.Az;
+            bvv = vv;
+            bsd = sd;
+          }
+        }
+      } else {
+        if (tid < 2 * NV) {
+          const int vv = tid >> 1, sd = tid & 1;
+          if (sd == 0) {
+            for (int q = R - 1; q > rank; --q) {
+              Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
+              Bwd<real> b = rx->seg_bwd[vv][0];
+              xb = b.A + b.B * xb;
+              zb = b.Az + b.B * zb;
+            }
+          } else {
+            for (int q = 0; q < rank; ++q) {
+              Exch<real, NV, WPV> *rx = cluster.map_shared_rank(&ex, q);
+              Bwd<real> b = rx->seg_bwd[vv][1];
+              xb = b.A + b.B * xb;
+              zb = b.Az + b.B * zb;
+            }
+          }
+          bvv = vv;
+          bsd = sd;
+        }
+      }
+      if (bvv >= 0) {
+        for (int ww = 0; ww < WPV; ++ww) {
+          int wi = bsd == 0 ? WPV - 1 - ww : ww;
+          ex.warp_xn[bvv][bsd][wi][0] = xb;
+          ex.warp_xn[bvv][bsd][wi][1] = zb;
+          Bwd<real> b = ex.warp_bwd[bvv][bsd][wi];
+          xb = b.A + b.B * xb;
+          zb = b.Az + b.B * zb;
+        }
+      }
+    }
+    __syncthreads();
+
+    // ------------------------------------------- back substitution (F8)
+    // minus from the chunk's last cell down, plus from its first cell up; c', d'
+    // come from the weight slots, the solution goes to Fm / Fp.  The value
+    // entering a chunk is the value leaving the neighbouring lane's chunk (its
+    // inclusive back map applied to the warp's entering value).
+    real xm, zm_, xp, zp_;
+    {
+      const real xn = ex.warp_xn[v][0][w][0], zn = ex.warp_xn[v][0][w][1];
+      const real xo = bm_in.A + bm_in.B * xn, zo = bm_in.Az + bm_in.B * zn;
+      xm = shfl_down_r(xo, 1);
+      zm_ = PER ? shfl_down_r(zo, 1) : real(0);
+      if (lane == 31) { xm = xn; zm_ = zn; }
+    }
+    {
+      const real xn = ex.warp_xn[v][1][w][0], zn = ex.warp_xn[v][1][w][1];
+      const real xo = bp_in.A + bp_in.B * xn, zo = bp_in.Az + bp_in.B * zn;
+      xp = shfl_up_r(xo, 1);
+      zp_ = PER ? shfl_up_r(zo, 1) : real(0);
+      if (lane == 0) { xp = xn; zp_ = zn; }
+    }
+    real zmo[PER ? M : 1], zpo[PER ? M : 1];
+    bool done8 = false;
+    if constexpr (MIXED) {
+      if (plain) {   // both systems together, no guards
+        const float *om = wt + cb, *op = wt + 2 * WP + cb;
+        float *dm = Fm + v * WP + cb, *dp = Fp + v * WP + cb;
+        float2 x2 = make_float2(xm, xp), z2 = make_float2(zm_, zp_);
+  #pragma unroll
+        for (int jj = 0; jj < M; ++jj) {
+          const int jm = M - 1 - jj, jp = jj;
+          const float2 nc = make_float2(-om[jm], -op[jp]);
+          x2 = p_fma(nc, x2, make_float2(om[WP + jm], op[WP + jp]));
+          dm[jm] = x2.x;
+          dp[jp] = x2.y;
+          if (PER) {
+            z2 = p_fma(nc, z2, make_float2(zmv[jm], zpv[jp]));
+            zmo[jm] = z2.x;
+            zpo[jp] = z2.y;
+          }
+        }
+        done8 = true;
+      }
+    }
+    if (!done8) {
+      {
+        const real *o = wt + cb;
+        real *dst = Fm + v * WP + cb;
+        real x = xm, z = zm_;
+  #pragma unroll
+        for (int jj = 0; jj < M; ++jj) {
+          const int j = M - 1 - jj;
+          if (j < len) {
+            const real c = o[j];
+            x = o[WP + j] - c * x;
+            dst[j] = x;
+            if (PER) {
+              z = zmv[j] - c * z;
+              zmo[j] = z;
+            }
+          }
+        }
+      }
+      {
+        const real *o = wt + 2 * WP + cb;
+        real *dst = Fp + v * WP + cb;
+        real x = xp, z = zp_;
+  #pragma unroll
+        for (int j = 0; j < M; ++j) {
+          if (j < len) {
+            const real c = o[j];
+            x = o[WP + j] - c * x;
+            dst[j] = x;
+            if (PER) {
+              z = zpv[j] - c * z;
+              zpo[j] = z;
+            }
+          }
+        }
+      }
+    }
+
+    if (PER) {
+      // Sherman-Morrison correction x = y - (v.y)/(1 + v.z) z, with
+      // v = e_first + (corner_first / g) e_last and corner_first / g = -a0/b0
+      // of the unmodified position-0 row; the scalars in FP64.  zmo, zpo are
+      // indexed by the chunk's cells.
+      real zm_last = real(0), zp_last = real(0);
+  #pragma unroll
       for (int j = 0; j < M; ++j) {
-        if (j < len) {
-          Fm[v * WP + cb + j] -= fm_ * zmo[j];
-          Fp[v * WP + cb + j] -= fp_ * zpo[j];
+        if (j == len - 1) { zm_last = zmo[j]; zp_last = zpo[j]; }
+      }
+      if (len > 0 && s0 == 0) {              // cell 0: minus first, plus last
+        real a0, b0;
+        far_row(0, a0, b0);
+        ex.sm[v][0][4] = -(double)a0 / (double)b0;
+        ex.sm[v][0][0] = Fm[v * WP + 0];
+        ex.sm[v][0][1] = zmo[0];
+        ex.sm[v][1][2] = Fp[v * WP + 0];
+        ex.sm[v][1][3] = zpo[0];
+      }
+      if (len > 0 && s0 + len == n) {        // cell n-1: plus first, minus last
+        real a0, b0;
+        far_row(1, a0, b0);
+        ex.sm[v][1][4] = -(double)a0 / (double)b0;
+        ex.sm[v][1][0] = Fp[v * WP + S::pad(n - 1 - lo)];
+        ex.sm[v][1][1] = zp_last;
+        ex.sm[v][0][2] = Fm[v * WP + S::pad(n - 1 - lo)];
+        ex.sm[v][0][3] = zm_last;
+      }
+      cluster.sync();
+      {
+        Exch<real, NV, WPV> *r0 = cluster.map_shared_rank(&ex, 0);
+        Exch<real, NV, WPV> *rl = cluster.map_shared_rank(&ex, R - 1);
+        double facm = (r0->sm[v][0][0] + r0->sm[v][0][4] * rl->sm[v][0][2]) /
+                      (1.0 + r0->sm[v][0][1] + r0->sm[v][0][4] * rl->sm[v][0][3]);
+        double facp = (rl->sm[v][1][0] + rl->sm[v][1][4] * r0->sm[v][1][2]) /
+                      (1.0 + rl->sm[v][1][1] + rl->sm[v][1][4] * r0->sm[v][1][3]);
+        real fm_ = real(facm), fp_ = real(facp);
+  #pragma unroll
+        for (int j = 0; j < M; ++j) {
+          if (j < len) {
+            Fm[v * WP + cb + j] -= fm_ * zmo[j];
+            Fp[v * WP + cb + j] -= fp_ * zpo[j];
+          }
         }
       }
     }

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/pp_cweno.h"
+#include "char_recon.cuh"
 #include "dfloat.cuh"
 #include "sweeps.cuh"
 
@@ -569,6 +570,9 @@ struct pp_cweno_s {
   bool ytrans = false;
   float *UT = nullptr, *DT = nullptr;
   bool tuned = false;
+  // characteristic-wise reconstruction (FP64 single problem): U^- and U^+
+  // planes of the current sweep direction and the block solver's scratch
+  double *UMP = nullptr, *cscr = nullptr;
   // batch
   bool batch = false;
   int nprob = 1;
@@ -617,6 +621,9 @@ int check_config(const pp_cweno_config *c) {
   if (!(c->eps_weno > 0.0) || !(c->eps_pos > 0.0)) return PP_ERR_ARG;
   if (c->precision != PP_PREC_FP64 && c->precision != PP_PREC_MIXED) return PP_ERR_ARG;
   if (c->flux != PP_FLUX_HLLC && c->flux != PP_FLUX_LLF) return PP_ERR_ARG;
+  if (c->recon != PP_RECON_COMPONENT && c->recon != PP_RECON_CHARACTERISTIC) return PP_ERR_ARG;
+  // the characteristic-wise form is built for FP64 single problems
+  if (c->recon == PP_RECON_CHARACTERISTIC && c->precision != PP_PREC_FP64) return PP_ERR_UNSUPPORTED;
   int nb = c->ndim == 2 ? 4 : 2;
   for (int k = 0; k < nb; ++k)
     if (!bc_valid(c->bc[k])) return PP_ERR_ARG;
@@ -640,6 +647,10 @@ void fill_common(const pp_cweno_s *h, SweepArgs &a, int stage, double eps_fixed,
   a.limiter = h->cfg.limiter;
   a.flux = h->cfg.flux;
   a.ctl = ctl;
+  if (h->cfg.recon == PP_RECON_CHARACTERISTIC) {
+    a.Fm_pre = h->UMP;
+    a.Fp_pre = h->UMP + (size_t)nvals(h);
+  }
 }
 
 void fill_state(const pp_cweno_s *h, SweepArgs &a, const void *Uin, const void *U0, void *Uout) {
@@ -709,6 +720,28 @@ cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const void *Uin, co
     a.h_other = h->dx;
   }
   a.R = seg_count(a.n);
+  if (h->cfg.recon == PP_RECON_CHARACTERISTIC && !attrs_only) {
+    // the face values of this direction first (Sec. 2.3), then the line
+    // kernel limits them and forms the fluxes and the update
+    CharArgs c;
+    c.U = a.U;
+    c.Um = h->UMP;
+    c.Up = h->UMP + (size_t)nvals(h);
+    c.scr = h->cscr;
+    c.ncell = h->ncell;
+    c.nlines = nlines;
+    c.cell_stride = a.cell_stride;
+    c.line_stride = a.line_stride;
+    c.n = a.n;
+    c.vn = a.vn;
+    c.vt = a.vt;
+    c.bclo = a.bclo;
+    c.bchi = a.bchi;
+    c.gamma = h->cfg.gamma;
+    c.eps_weno = h->cfg.eps_weno;
+    cudaError_t e = launch_char_recon(c, h->nv, a.bclo == PP_BC_PERIODIC, h->stream);
+    if (e != cudaSuccess) return e;
+  }
   return dispatch(h, mode, a.bclo == PP_BC_PERIODIC, a, nlines, attrs_only);
 }
 
@@ -965,6 +998,12 @@ int finish_create(pp_cweno_s *h) {
   const bool tr = h->ytrans || h->btrans;
   if (e == cudaSuccess && tr) e = cudaMalloc(&h->UT, sizeof(float) * (size_t)nvals(h));
   if (e == cudaSuccess && tr) e = cudaMalloc(&h->DT, sizeof(float) * (size_t)nvals(h));
+  if (e == cudaSuccess && h->cfg.recon == PP_RECON_CHARACTERISTIC) {
+    e = cudaMalloc(&h->UMP, 2 * bytes);
+    long long sx = char_scratch_doubles(h->nv, h->cfg.bc[0] == PP_BC_PERIODIC, h->nx, h->ny);
+    long long sy = h->nv == 4 ? char_scratch_doubles(h->nv, h->cfg.bc[2] == PP_BC_PERIODIC, h->ny, h->nx) : 0;
+    if (e == cudaSuccess) e = cudaMalloc(&h->cscr, sizeof(double) * (size_t)std::max(sx, sy));
+  }
   if (e != cudaSuccess) return PP_ERR_CUDA;
   memset(h->hctl, 0, sizeof(Ctl) * h->nprob);
   // kernel attributes (dynamic shared memory, cluster size) are set here,
@@ -990,7 +1029,9 @@ int finish_create(pp_cweno_s *h) {
     for (int s = 0; s < 3; ++s)
       h->launches_per_step += (long long)h->groups.size() + (h->btrans ? 1 : 0);
   } else {
-    h->launches_per_step = 1 + 3 * (h->ytrans ? 3 : (h->nv == 4 ? 2 : 1));
+    const int sweeps = h->nv == 4 ? 2 : 1;
+    const int per_sweep = h->cfg.recon == PP_RECON_CHARACTERISTIC ? 2 : 1;
+    h->launches_per_step = 1 + 3 * (h->ytrans ? 3 : sweeps * per_sweep);
   }
   return PP_OK;
 }
@@ -1084,6 +1125,7 @@ int pp_cweno_config_default(pp_cweno_config *cfg) {
   cfg->cfl_positivity_cap = 0;
   cfg->limiter = 1;
   cfg->flux = PP_FLUX_HLLC;
+  cfg->recon = PP_RECON_COMPONENT;
   return PP_OK;
 }
 
@@ -1122,8 +1164,9 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
     const pp_cweno_config &c = cfgs[p];
     if (c.ndim != c0.ndim || c.gamma != c0.gamma || c.precision != c0.precision ||
         c.gl_weight != c0.gl_weight || c.eps_weno != c0.eps_weno || c.eps_pos != c0.eps_pos ||
-        c.limiter != c0.limiter || c.flux != c0.flux)
+        c.limiter != c0.limiter || c.flux != c0.flux || c.recon != c0.recon)
       return PP_ERR_ARG;
+    if (c.recon != PP_RECON_COMPONENT) return PP_ERR_UNSUPPORTED;
   }
   pp_cweno_s *h = new (std::nothrow) pp_cweno_s();
   if (!h) return PP_ERR_CUDA;
@@ -1589,6 +1632,7 @@ int pp_cweno_operator_noalloc(const pp_cweno_config *cfg, const double *U_dev, d
   int rc = check_config(cfg);
   if (rc) return rc;
   if (cfg->precision != PP_PREC_FP64) return PP_ERR_UNSUPPORTED;
+  if (cfg->recon != PP_RECON_COMPONENT) return PP_ERR_UNSUPPORTED;   // needs the handle's scratch
   const int nv = cfg->ndim == 2 ? 4 : 3;
   const long long nx = cfg->nx, ny = cfg->ndim == 2 ? cfg->ny : 1;
   const size_t dbytes = cfg->ndim == 2 ? sizeof(double) * (size_t)nv * (size_t)(nx * ny) : 0;
@@ -1673,6 +1717,8 @@ int pp_cweno_destroy(pp_cweno_t h) {
   cudaFree(h->tiles);
   cudaFree(h->UT);
   cudaFree(h->DT);
+  cudaFree(h->UMP);
+  cudaFree(h->cscr);
   for (auto &g : h->groups) cudaFree(g.lines);
   if (h->hctl) cudaFreeHost(h->hctl);
   delete h;

@@ -33,9 +33,9 @@ def test_config_struct_layout_matches_header():
     import subprocess
     import tempfile
     src = '#include "pp_cweno.h"\n#include <stdio.h>\n#include <stddef.h>\n' \
-          'int main(){printf("%zu %zu %zu %zu\\n", sizeof(pp_cweno_config), ' \
+          'int main(){printf("%zu %zu %zu %zu %zu\\n", sizeof(pp_cweno_config), ' \
           'sizeof(pp_cweno_stats_t), offsetof(pp_cweno_config, limiter), ' \
-          'offsetof(pp_cweno_config, flux));return 0;}\n'
+          'offsetof(pp_cweno_config, flux), offsetof(pp_cweno_config, recon));return 0;}\n'
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
         open(c, "w").write(src)
@@ -46,6 +46,7 @@ def test_config_struct_layout_matches_header():
     assert int(out[1]) == ctypes.sizeof(binding.Stats)
     assert int(out[2]) == binding.Config.limiter.offset
     assert int(out[3]) == binding.Config.flux.offset
+    assert int(out[4]) == binding.Config.recon.offset
 
 
 def test_config_rejects_unknown_flux():
@@ -69,3 +70,21 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(RuntimeError):
         binding.lib()
+
+
+def test_characteristic_form_limits():
+    """The characteristic-wise form is FP64 and single-problem: an unknown
+    selector is PP_ERR_ARG, the mixed form and batches PP_ERR_UNSUPPORTED,
+    all decided before any device call."""
+    L = binding.lib()
+    h = ctypes.c_void_p()
+    c = binding.make_config(recon=2)
+    assert L.pp_cweno_create(ctypes.byref(c), None, ctypes.byref(h)) == binding.PP_ERR_ARG
+    c = binding.make_config(precision=binding.PREC_MIXED, recon=binding.RECON_CHARACTERISTIC)
+    assert L.pp_cweno_create(ctypes.byref(c), None, ctypes.byref(h)) == binding.PP_ERR_UNSUPPORTED
+    c = binding.make_config(recon=binding.RECON_CHARACTERISTIC)
+    arr = (binding.Config * 2)(c, c)
+    assert L.pp_cweno_create_batch(arr, 2, None, ctypes.byref(h)) == binding.PP_ERR_UNSUPPORTED
+    assert not h.value
+    assert L.pp_cweno_operator_noalloc(ctypes.byref(c), ctypes.c_void_p(8), ctypes.c_void_p(8),
+                                       ctypes.c_double(0.0), None) == binding.PP_ERR_UNSUPPORTED
