@@ -70,11 +70,14 @@ typedef enum {
                                   tridiagonal system per variable and side (Sec. 2.2) */
   PP_RECON_CHARACTERISTIC = 1  /* characteristic variables of the Roe average at each
                                   face: one block tridiagonal system per side, blocks
-                                  diag(a, b, c) L (Sec. 2.3, eq. (1DEuler-FVC)).
-                                  FP64 single problems only (PP_ERR_UNSUPPORTED
-                                  otherwise); needs 2 x (n (nv^2 + nv) + nv^2) x
-                                  lines doubles of scratch per sweep direction
-                                  (periodic: nv^2 + nv (nv+1) per row) */
+                                  diag(a, b, c) L (Sec. 2.3, eq. (1DEuler-FVC)),
+                                  in the line arithmetic of either precision.
+                                  Single problems only (PP_ERR_UNSUPPORTED for
+                                  batches and pp_cweno_operator_noalloc); needs
+                                  2 (n (nv^2 + nv) + nv^2) values per line of
+                                  scratch per sweep direction (periodic: nv^2 +
+                                  nv (nv+1) per row; FP64, or FP32 for the mixed
+                                  form) */
 } pp_recon_t;
 
 enum {

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libppcweno.so")
 SOURCES = ["pp_cweno.cu", "sweep_f64_m8.cu", "sweep_f64_m16.cu", "sweep_f32_m8.cu",
-           "sweep_f32_m16.cu", "char_recon.cu"]
+           "sweep_f32_m16.cu", "char_recon_f64.cu", "char_recon_f32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include")]
@@ -25,7 +25,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
 # the FP32 form uses approximate division / square root and flushes
 # denormals; the error-free transformations of the compensated sums use
 # explicitly rounded intrinsics, so they are unaffected
-FILE_FLAGS = {"sweep_f32_m8.cu": ["--use_fast_math"], "sweep_f32_m16.cu": ["--use_fast_math"]}
+FILE_FLAGS = {"sweep_f32_m8.cu": ["--use_fast_math"], "sweep_f32_m16.cu": ["--use_fast_math"],
+              "char_recon_f32.cu": ["--use_fast_math"]}
 
 
 def _nvcc() -> str:

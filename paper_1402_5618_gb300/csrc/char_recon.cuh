@@ -25,9 +25,10 @@
 namespace ppk {
 
 struct CharArgs {
-  const double *U;          // stage input: FP64 planes [nv][ncell]
-  double *Um, *Up;          // out: U^-_{i+1/2}, U^+_{i-1/2} of every cell, same layout
-  double *scr;              // scratch, char_scratch_doubles() doubles
+  const void *U;            // stage input: planes [nv][ncell] of the line's arithmetic
+                            // (FP64, or the FP32 hi parts of the mixed form)
+  void *Um, *Up;            // out: U^-_{i+1/2}, U^+_{i-1/2} of every cell, same layout and type
+  void *scr;                // scratch, char_scratch_values() values of the same type
   long long ncell;          // cells per variable plane
   long long nlines;
   long long cell_stride, line_stride;
@@ -37,18 +38,21 @@ struct CharArgs {
   double gamma, eps_weno;
 };
 
-// doubles of one row of the scratch: the multiplier block Y (nv x nv) and
+// values of one row of the scratch: the multiplier block Y (nv x nv) and
 // the right-hand-side columns g (nv x (1 + nv) on periodic lines)
-inline long long char_row_doubles(int nv, bool periodic) {
+inline long long char_row_values(int nv, bool periodic) {
   return (long long)nv * nv + (long long)nv * (periodic ? nv + 1 : 1);
 }
 
 // scratch for lines of n cells: both sides, n rows each plus one block per
 // line-side for the Woodbury coupling matrix
-inline long long char_scratch_doubles(int nv, bool periodic, long long n, long long nlines) {
-  return 2 * (n * char_row_doubles(nv, periodic) + (long long)nv * nv) * nlines;
+inline long long char_scratch_values(int nv, bool periodic, long long n, long long nlines) {
+  return 2 * (n * char_row_values(nv, periodic) + (long long)nv * nv) * nlines;
 }
 
-cudaError_t launch_char_recon(const CharArgs &a, int nv, bool periodic, cudaStream_t st);
+// one launch per precision, each in its own translation unit (the FP32 one
+// is compiled with the mixed form's fast division and square root)
+cudaError_t launch_char_recon_f64(const CharArgs &a, int nv, bool periodic, cudaStream_t st);
+cudaError_t launch_char_recon_f32(const CharArgs &a, int nv, bool periodic, cudaStream_t st);
 
 }  // namespace ppk

@@ -1,59 +1,64 @@
-// char_recon.cu -- kernel of the characteristic-wise reconstruction
-// (Sec. 2.3); the layout and the walk are described in char_recon.cuh.
+// char_recon_kernel.cuh -- kernel of the characteristic-wise reconstruction
+// (Sec. 2.3) in the arithmetic of the line: real = double is the plain
+// form; real = float the mixed form, reading the FP32 hi parts of the state.
+// The layout and the walk are described in char_recon.cuh.
+#pragma once
+
 #include "char_recon.cuh"
 #include "physics.cuh"
 
 namespace ppk {
-namespace {
+namespace chr {
 
 // Sec. 2.3: rows l^(k) of L, the left eigenvectors of the flux Jacobian at
 // the Roe average of Ua and Ub (eqs. (eigen), (leigenv)), ordered by the
 // eigenvalues u - a, u, (u,) u + a; in 2-D the third row is the shear field
 // (-v, 0, 1, 0) and v enters the acoustic rows through |u|^2 and -c1 v / 2.
-template <int NV>
-__device__ __forceinline__ void roe_left(const double *Ua, const double *Ub, double gamma,
-                                         double (&L)[NV][NV]) {
-  const double sa = sqrt(Ua[0]), sb = sqrt(Ub[0]);
-  const double isab = 1.0 / (sa + sb);
-  const double pa = pressure<double, NV>(Ua, gamma), pb = pressure<double, NV>(Ub, gamma);
-  const double u = (Ua[1] / sa + Ub[1] / sb) * isab;
-  const double v = NV == 4 ? (Ua[2] / sa + Ub[2] / sb) * isab : 0.0;
-  const double H = ((Ua[NV - 1] + pa) / sa + (Ub[NV - 1] + pb) / sb) * isab;
-  const double q2 = u * u + v * v;
-  const double a2 = (gamma - 1.0) * (H - 0.5 * q2);
-  const double ia = 1.0 / sqrt(a2);
-  const double c1 = (gamma - 1.0) / a2, c2 = 0.5 * q2 * c1;
-  L[0][0] = 0.5 * (c2 + u * ia);
-  L[0][1] = -0.5 * (c1 * u + ia);
-  L[0][NV - 1] = 0.5 * c1;
-  L[1][0] = 1.0 - c2;
+template <typename real, int NV>
+__device__ __forceinline__ void roe_left(const real *Ua, const real *Ub, real gamma,
+                                         real (&L)[NV][NV]) {
+  const real one = real(1), half = real(0.5);
+  const real sa = sqrt(Ua[0]), sb = sqrt(Ub[0]);
+  const real isab = one / (sa + sb);
+  const real pa = pressure<real, NV>(Ua, gamma), pb = pressure<real, NV>(Ub, gamma);
+  const real u = (Ua[1] / sa + Ub[1] / sb) * isab;
+  const real v = NV == 4 ? (Ua[2] / sa + Ub[2] / sb) * isab : real(0);
+  const real H = ((Ua[NV - 1] + pa) / sa + (Ub[NV - 1] + pb) / sb) * isab;
+  const real q2 = u * u + v * v;
+  const real a2 = (gamma - one) * (H - half * q2);
+  const real ia = one / sqrt(a2);
+  const real c1 = (gamma - one) / a2, c2 = half * q2 * c1;
+  L[0][0] = half * (c2 + u * ia);
+  L[0][1] = -half * (c1 * u + ia);
+  L[0][NV - 1] = half * c1;
+  L[1][0] = one - c2;
   L[1][1] = c1 * u;
   L[1][NV - 1] = -c1;
-  L[NV - 1][0] = 0.5 * (c2 - u * ia);
-  L[NV - 1][1] = 0.5 * (ia - c1 * u);
-  L[NV - 1][NV - 1] = 0.5 * c1;
+  L[NV - 1][0] = half * (c2 - u * ia);
+  L[NV - 1][1] = half * (ia - c1 * u);
+  L[NV - 1][NV - 1] = half * c1;
   if constexpr (NV == 4) {
-    L[0][2] = -0.5 * c1 * v;
+    L[0][2] = -half * c1 * v;
     L[1][2] = c1 * v;
-    L[3][2] = -0.5 * c1 * v;
+    L[3][2] = -half * c1 * v;
     L[2][0] = -v;
-    L[2][1] = 0.0;
-    L[2][2] = 1.0;
-    L[2][3] = 0.0;
+    L[2][1] = real(0);
+    L[2][2] = one;
+    L[2][3] = real(0);
   }
 }
 
 // X <- M^{-1} X for an NV x NV block M and NCOL columns: Gaussian
 // elimination with partial pivoting, all indices fixed at compile time
-template <int NV, int NCOL>
-__device__ __forceinline__ void gauss_solve(double (&M)[NV][NV], double (&X)[NV][NCOL]) {
+template <typename real, int NV, int NCOL>
+__device__ __forceinline__ void gauss_solve(real (&M)[NV][NV], real (&X)[NV][NCOL]) {
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
-    double best = fabs(M[c][c]);
+    real best = fabs(M[c][c]);
     int piv = c;
 #pragma unroll
     for (int r = c + 1; r < NV; ++r) {
-      const double m = fabs(M[r][c]);
+      const real m = fabs(M[r][c]);
       if (m > best) { best = m; piv = r; }
     }
 #pragma unroll
@@ -61,21 +66,21 @@ __device__ __forceinline__ void gauss_solve(double (&M)[NV][NV], double (&X)[NV]
       const bool sw = piv == r;
 #pragma unroll
       for (int j = c; j < NV; ++j) {
-        const double t = M[c][j];
+        const real t = M[c][j];
         M[c][j] = sw ? M[r][j] : t;
         M[r][j] = sw ? t : M[r][j];
       }
 #pragma unroll
       for (int j = 0; j < NCOL; ++j) {
-        const double t = X[c][j];
+        const real t = X[c][j];
         X[c][j] = sw ? X[r][j] : t;
         X[r][j] = sw ? t : X[r][j];
       }
     }
-    const double inv = 1.0 / M[c][c];
+    const real inv = real(1) / M[c][c];
 #pragma unroll
     for (int r = c + 1; r < NV; ++r) {
-      const double f = M[r][c] * inv;
+      const real f = M[r][c] * inv;
 #pragma unroll
       for (int j = c + 1; j < NV; ++j) M[r][j] -= f * M[c][j];
 #pragma unroll
@@ -84,14 +89,44 @@ __device__ __forceinline__ void gauss_solve(double (&M)[NV][NV], double (&X)[NV]
   }
 #pragma unroll
   for (int c = NV - 1; c >= 0; --c) {
-    const double inv = 1.0 / M[c][c];
+    const real inv = real(1) / M[c][c];
 #pragma unroll
     for (int j = 0; j < NCOL; ++j) {
-      double s = X[c][j];
+      real s = X[c][j];
 #pragma unroll
       for (int q = c + 1; q < NV; ++q) s -= M[c][q] * X[q][j];
       X[c][j] = s * inv;
     }
+  }
+}
+
+// WENO-Z ratios of one characteristic field over its five-cell stencil v.
+// FP32: the scaled ratios with eps lifted to the rounding floor of the
+// indicators, 4096 (u s)^2 with s = mag, the largest sum_m |l_m| |ubar_m|
+// over the stencil: the size of the terms the characteristic variable is
+// summed from, which bounds its rounding error even where the sum cancels
+// (the same floor as the component-wise mixed form, taken on those terms).
+template <typename real>
+__device__ __forceinline__ void char_ratios(const real (&v)[5], real mag, real eps, real &q0,
+                                            real &q1, real &q2, real &one) {
+  if constexpr (sizeof(real) == 4) {
+    const float c13 = 13.0f / 12.0f;
+    const float b0 = c13 * sqr(v[0] - 2.0f * v[1] + v[2]) + 0.25f * sqr(v[0] - 4.0f * v[1] + 3.0f * v[2]);
+    const float b1 = c13 * sqr(v[1] - 2.0f * v[2] + v[3]) + 0.25f * sqr(v[1] - v[3]);
+    const float b2 = c13 * sqr(v[2] - 2.0f * v[3] + v[4]) + 0.25f * sqr(3.0f * v[2] - 4.0f * v[3] + v[4]);
+    const float tau = fabsf(b2 - b0);
+    const float e = fmaf(FP32_BETA_FLOOR * mag, mag, eps);
+    const float d0 = b0 + e, d1 = b1 + e, d2 = b2 + e;
+    const float dmin = fminf(fminf(d0, d1), d2);
+    const float r = fminf(tau, dmin);
+    const float sc = dmin / tau;
+    one = tau <= dmin ? 1.0f : sc * sc;
+    q0 = sqr(r / d0);
+    q1 = sqr(r / d1);
+    q2 = sqr(r / d2);
+  } else {
+    zratios<real>(v[0], v[1], v[2], v[3], v[4], eps, q0, q1, q2);
+    one = real(1);
   }
 }
 
@@ -104,10 +139,11 @@ __device__ __forceinline__ void gauss_solve(double (&M)[NV][NV], double (&X)[NV]
 // B_{n-1} - C_{n-1} G^{-1} A_0 at the last, U = (G, 0, .., 0, C_{n-1}),
 // V^T = (I, 0, .., 0, G^{-1} A_0); the NV columns of U ride along as extra
 // right-hand sides and x = y - Z (I + V^T Z)^{-1} V^T y at the end.
-template <int NV, bool PER>
+template <typename real, int NV, bool PER>
 __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
+  constexpr bool F32 = sizeof(real) == 4;
   constexpr int NC = PER ? NV + 1 : 1;       // right-hand-side columns
-  constexpr int ROW = NV * NV + NV * NC;     // scratch doubles per row: Y, g
+  constexpr int ROW = NV * NV + NV * NC;     // scratch values per row: Y, g
   const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= a.nlines) return;
   const int side = blockIdx.y;
@@ -115,15 +151,17 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
   const int dir = side == 0 ? 1 : -1;
   const long long NL = a.nlines;
   const long long lbase = line * a.line_stride;
-  double *scr = a.scr + (long long)side * ((long long)n * ROW + NV * NV) * NL + line;
-  auto slot = [&](int p, int e) -> double & { return scr[((long long)p * ROW + e) * NL]; };
-  auto wslot = [&](int e) -> double & { return scr[((long long)n * ROW + e) * NL]; };
+  const real *U = reinterpret_cast<const real *>(a.U);
+  real *scr = reinterpret_cast<real *>(a.scr) + (long long)side * ((long long)n * ROW + NV * NV) * NL + line;
+  auto slot = [&](int p, int e) -> real & { return scr[((long long)p * ROW + e) * NL]; };
+  auto wslot = [&](int e) -> real & { return scr[((long long)n * ROW + e) * NL]; };
+  const real gam = real(a.gamma), eps = real(a.eps_weno);
   int gv[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) gv[k] = k == 0 ? 0 : (k == NV - 1 ? NV - 1 : (k == 1 ? a.vn : a.vt));
 
   // line variables of line cell i (ghost cells by the boundary condition)
-  auto cell = [&](int i, double(&out)[NV]) {
+  auto cell = [&](int i, real(&out)[NV]) {
     bool neg = false;
     if (i < 0 || i >= n) {
       if (PER) {
@@ -138,18 +176,18 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
         }
       }
     }
-    const double *src = a.U + lbase + (long long)i * a.cell_stride;
+    const real *src = U + lbase + (long long)i * a.cell_stride;
 #pragma unroll
     for (int k = 0; k < NV; ++k) out[k] = src[gv[k] * a.ncell];
     if (neg) out[1] = -out[1];
   };
   auto cidx = [&](int p) { return side == 0 ? p : n - 1 - p; };
 
-  double win[5][NV];   // walk offsets -2 .. +2 of the current position
+  real win[5][NV];   // walk offsets -2 .. +2 of the current position
 #pragma unroll
   for (int q = 0; q < 4; ++q) cell(cidx(0) + (q - 2) * dir, win[q + 1]);
 
-  double Yp[NV][NV], gp[NV][NC];   // the previous position's multipliers
+  real Yp[NV][NV], gp[NV][NC];   // the previous position's multipliers
 #pragma unroll 1
   for (int p = 0; p < n; ++p) {
 #pragma unroll
@@ -159,35 +197,42 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
     cell(cidx(p) + 2 * dir, win[4]);
 
     // step 1: eigenvectors at the unknown's face (this cell and the next)
-    double L[NV][NV];
-    roe_left<NV>(win[2], win[3], a.gamma, L);
-    // characteristic variables of the five cells
-    double cv[NV][5];
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        double t = 0.0;
-#pragma unroll
-        for (int m = 0; m < NV; ++m) t += L[k][m] * win[q][m];
-        cv[k][q] = t;
-      }
-    // steps 2-3: per-field weights and scalar row (a on the previous
-    // unknown, b on this one, c on the next); closure rows 0 x + 1 x + 0 x
+    real L[NV][NV];
+    roe_left<real, NV>(win[2], win[3], gam, L);
+    // steps 2-3: characteristic variables of the five cells, per-field
+    // weights and scalar row (a on the previous unknown, b on this one, c on
+    // the next); closure rows 0 x + 1 x + 0 x = explicit WENO5-Z value
     const bool closure = !PER && (p == 0 || p == n - 1);
-    double ca[NV], cb[NV], cc[NV], cr[NV];
+    real ca[NV], cb[NV], cc[NV], cr[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
+      real cv[5];
+      real mag = real(0);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        real t = real(0), s = real(0);
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+          t += L[k][m] * win[q][m];
+          if (F32) s += fabs(L[k][m]) * fabs(win[q][m]);
+        }
+        cv[q] = t;
+        if (F32) mag = fmax(mag, s);
+      }
+      real q0, q1, q2, w0, w1, w2, one;
+      char_ratios<real>(cv, mag, eps, q0, q1, q2, one);
       if (closure) {
-        ca[k] = 0.0;
-        cb[k] = 1.0;
-        cc[k] = 0.0;
-        cr[k] = weno5z_face<double>(cv[k][0], cv[k][1], cv[k][2], cv[k][3], cv[k][4], a.eps_weno);
+        zweights<real>(real(0.1), real(0.6), real(0.3), q0, q1, q2, w0, w1, w2, one);
+        const real p0 = real(2) * cv[0] - real(7) * cv[1] + real(11) * cv[2];
+        const real p1 = -cv[1] + real(5) * cv[2] + real(2) * cv[3];
+        const real p2 = real(2) * cv[2] + real(5) * cv[3] - cv[4];
+        ca[k] = real(0);
+        cb[k] = real(1);
+        cc[k] = real(0);
+        cr[k] = (w0 * p0 + w1 * p1 + w2 * p2) * real(1.0 / 6.0);
       } else {
-        double q0, q1, q2, w0, w1, w2;
-        zratios<double>(cv[k][0], cv[k][1], cv[k][2], cv[k][3], cv[k][4], a.eps_weno, q0, q1, q2);
-        zweights<double>(0.2, 0.5, 0.3, q0, q1, q2, w0, w1, w2);
-        const Row<double> r = compact_row<double>(w0, w1, w2, cv[k][1], cv[k][2], cv[k][3]);
+        zweights<real>(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
+        const Row<real> r = compact_row<real>(w0, w1, w2, cv[1], cv[2], cv[3]);
         ca[k] = r.a;
         cb[k] = r.b;
         cc[k] = r.c;
@@ -196,7 +241,7 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
     }
     // step 4: block row diag(ca, cb, cc) L, eliminated against the previous
     // position: Bp = B - A Y_prev, X = [C | r - A g_prev]
-    double Bp[NV][NV], X[NV][NV + NC];
+    real Bp[NV][NV], X[NV][NV + NC];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
 #pragma unroll
@@ -206,13 +251,13 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
       }
       X[k][NV] = cr[k];
 #pragma unroll
-      for (int j = 1; j < NC; ++j) X[k][NV + j] = 0.0;
+      for (int j = 1; j < NC; ++j) X[k][NV + j] = real(0);
     }
     if constexpr (PER) {
       if (p == 0) {
         // G = -B_0: B'_0 = B_0 - G = 2 B_0, Woodbury columns U_0 = G, and
         // G^{-1} A_0 for the last position and the final correction
-        double Gm[NV][NV], GiA[NV][NV];
+        real Gm[NV][NV], GiA[NV][NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
 #pragma unroll
@@ -222,7 +267,7 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
             X[k][NV + 1 + j] = Gm[k][j];
             Bp[k][j] = Bp[k][j] + Bp[k][j];
           }
-        gauss_solve<NV, NV>(Gm, GiA);
+        gauss_solve<real, NV, NV>(Gm, GiA);
 #pragma unroll
         for (int k = 0; k < NV; ++k)
 #pragma unroll
@@ -234,14 +279,14 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
       for (int k = 0; k < NV; ++k) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-          double t = 0.0;
+          real t = real(0);
 #pragma unroll
           for (int m = 0; m < NV; ++m) t += L[k][m] * Yp[m][j];
           Bp[k][j] -= ca[k] * t;
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          double t = 0.0;
+          real t = real(0);
 #pragma unroll
           for (int m = 0; m < NV; ++m) t += L[k][m] * gp[m][c];
           X[k][NV + c] -= ca[k] * t;
@@ -252,7 +297,7 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
       if (p == n - 1) {
         // B'_{n-1} = B_{n-1} - C_{n-1} G^{-1} A_0; the coupling to x_0 moves
         // into the Woodbury columns (U_{n-1} = C_{n-1})
-        double GiA[NV][NV];
+        real GiA[NV][NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
 #pragma unroll
@@ -261,7 +306,7 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
         for (int k = 0; k < NV; ++k)
 #pragma unroll
           for (int j = 0; j < NV; ++j) {
-            double t = 0.0;
+            real t = real(0);
 #pragma unroll
             for (int m = 0; m < NV; ++m) t += X[k][m] * GiA[m][j];
             Bp[k][j] -= t;
@@ -271,11 +316,11 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
 #pragma unroll
           for (int j = 0; j < NV; ++j) {
             X[k][NV + 1 + j] += X[k][j];
-            X[k][j] = 0.0;
+            X[k][j] = real(0);
           }
       }
     }
-    gauss_solve<NV, NV + NC>(Bp, X);
+    gauss_solve<real, NV, NV + NC>(Bp, X);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
 #pragma unroll
@@ -292,8 +337,8 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
   }
 
   // back substitution x_p = g_p - Y_p x_{p+1}
-  double *out = side == 0 ? a.Um : a.Up;
-  double x[NV][NC];
+  real *out = reinterpret_cast<real *>(side == 0 ? a.Um : a.Up);
+  real x[NV][NC];
 #pragma unroll
   for (int k = 0; k < NV; ++k)
 #pragma unroll
@@ -301,7 +346,7 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
 #pragma unroll 1
   for (int p = n - 1; p >= 0; --p) {
     if (p < n - 1) {
-      double Y[NV][NV], xn[NV][NC];
+      real Y[NV][NV], xn[NV][NC];
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
 #pragma unroll
@@ -313,7 +358,7 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
       for (int k = 0; k < NV; ++k)
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          double s = slot(p, NV * NV + k * NC + c);
+          real s = slot(p, NV * NV + k * NC + c);
 #pragma unroll
           for (int j = 0; j < NV; ++j) s -= Y[k][j] * xn[j][c];
           x[k][c] = s;
@@ -325,7 +370,7 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) slot(p, NV * NV + k * NC + c) = x[k][c];
     } else {
-      double *dst = out + lbase + (long long)cidx(p) * a.cell_stride;
+      real *dst = out + lbase + (long long)cidx(p) * a.cell_stride;
 #pragma unroll
       for (int k = 0; k < NV; ++k) dst[gv[k] * a.ncell] = x[k][0];
     }
@@ -333,7 +378,7 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
   if constexpr (PER) {
     // S = I + Z_0 + G^{-1} A_0 Z_{n-1}, t = y_0 + G^{-1} A_0 y_{n-1};
     // x_p = y_p - Z_p S^{-1} t
-    double S[NV][NV], t[NV][1], GiA[NV][NV];
+    real S[NV][NV], t[NV][1], GiA[NV][NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
 #pragma unroll
@@ -342,23 +387,23 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
     for (int k = 0; k < NV; ++k) {
 #pragma unroll
       for (int j = 0; j < NV; ++j) {
-        double s = (k == j ? 1.0 : 0.0) + slot(0, NV * NV + k * NC + 1 + j);
+        real s = (k == j ? real(1) : real(0)) + slot(0, NV * NV + k * NC + 1 + j);
 #pragma unroll
         for (int m = 0; m < NV; ++m) s += GiA[k][m] * slot(n - 1, NV * NV + m * NC + 1 + j);
         S[k][j] = s;
       }
-      double s = slot(0, NV * NV + k * NC);
+      real s = slot(0, NV * NV + k * NC);
 #pragma unroll
       for (int m = 0; m < NV; ++m) s += GiA[k][m] * slot(n - 1, NV * NV + m * NC);
       t[k][0] = s;
     }
-    gauss_solve<NV, 1>(S, t);
+    gauss_solve<real, NV, 1>(S, t);
 #pragma unroll 1
     for (int p = 0; p < n; ++p) {
-      double *dst = out + lbase + (long long)cidx(p) * a.cell_stride;
+      real *dst = out + lbase + (long long)cidx(p) * a.cell_stride;
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
-        double s = slot(p, NV * NV + k * NC);
+        real s = slot(p, NV * NV + k * NC);
 #pragma unroll
         for (int j = 0; j < NV; ++j) s -= slot(p, NV * NV + k * NC + 1 + j) * t[j][0];
         dst[gv[k] * a.ncell] = s;
@@ -367,18 +412,18 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
   }
 }
 
-}  // namespace
-
-cudaError_t launch_char_recon(const CharArgs &a, int nv, bool periodic, cudaStream_t st) {
+template <typename real>
+cudaError_t launch_char_recon_t(const CharArgs &a, int nv, bool periodic, cudaStream_t st) {
   const dim3 grid((unsigned)((a.nlines + 31) / 32), 2, 1);
   if (nv == 3) {
-    if (periodic) char_recon_kernel<3, true><<<grid, 32, 0, st>>>(a);
-    else char_recon_kernel<3, false><<<grid, 32, 0, st>>>(a);
+    if (periodic) char_recon_kernel<real, 3, true><<<grid, 32, 0, st>>>(a);
+    else char_recon_kernel<real, 3, false><<<grid, 32, 0, st>>>(a);
   } else {
-    if (periodic) char_recon_kernel<4, true><<<grid, 32, 0, st>>>(a);
-    else char_recon_kernel<4, false><<<grid, 32, 0, st>>>(a);
+    if (periodic) char_recon_kernel<real, 4, true><<<grid, 32, 0, st>>>(a);
+    else char_recon_kernel<real, 4, false><<<grid, 32, 0, st>>>(a);
   }
   return cudaGetLastError();
 }
 
+}  // namespace chr
 }  // namespace ppk

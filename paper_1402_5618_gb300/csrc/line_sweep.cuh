@@ -103,9 +103,9 @@ struct SweepArgs {
   double eps_fixed;   // > 0: fixed limiter epsilon, no control-block checks (operator evaluation)
   int limiter;
   int flux;           // 0 HLLC, 1 local Lax-Friedrichs
-  // FP64 form: face values U^-, U^+ computed by another kernel (FP64
-  // planes in the state's layout); nullptr: the kernel reconstructs them
-  const double *Fm_pre, *Fp_pre;
+  // face values U^-, U^+ computed by another kernel (planes of the line's
+  // arithmetic in the state's layout); nullptr: the kernel reconstructs them
+  const void *Fm_pre, *Fp_pre;
   Ctl *ctl;
   // batched launch: line table and problem descriptors (nullptr: one problem)
   const LineRef *lines;
@@ -464,7 +464,9 @@ __device__ __forceinline__ double bits_double(unsigned long long b) {
 #ifndef PPK_MIXED_CTAS_M8
 #define PPK_MIXED_CTAS_M8 3
 #endif
-template <typename real, int NV, int M, bool PER, int MODE>
+// PRE: the face values come from another kernel (args.Fm_pre / Fp_pre) and
+// the reconstruction phases are compiled out.
+template <typename real, int NV, int M, bool PER, int MODE, bool PRE>
 __global__ void __launch_bounds__(NV * (SEGC / M),
                                   sizeof(real) == 4 ? (M == 8 ? PPK_MIXED_CTAS_M8 : 2) : 1)
     line_sweep(SweepArgs args_in) {
@@ -587,15 +589,16 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   }
   __syncthreads();
 
-  // face values computed outside (the characteristic-wise reconstruction,
-  // FP64 form): U^- and U^+ of the segment's cells in the state's layout
-  const bool pre = !MIXED && args.Fm_pre != nullptr;
-  if (pre) {
+  // face values computed outside (the characteristic-wise reconstruction):
+  // U^- and U^+ of the segment's cells in the state's layout
+  if constexpr (PRE) {
+    const real *pm = reinterpret_cast<const real *>(args.Fm_pre);
+    const real *pp = reinterpret_cast<const real *>(args.Fp_pre);
     for (int idx = tid; idx < NV * (hi - lo); idx += T) {
       const int kv = idx / (hi - lo), c = idx - kv * (hi - lo);
       const long long o = gvar(kv, NV, args.vn, args.vt) * args.ncell + lbase + (long long)(lo + c) * cs;
-      Fm[kv * WP + S::pad(c)] = real(args.Fm_pre[o]);
-      Fp[kv * WP + S::pad(c)] = real(args.Fp_pre[o]);
+      Fm[kv * WP + S::pad(c)] = pm[o];
+      Fp[kv * WP + S::pad(c)] = pp[o];
     }
   } else {
     // ---------------------------------------------------------------- rows

@@ -570,9 +570,10 @@ struct pp_cweno_s {
   bool ytrans = false;
   float *UT = nullptr, *DT = nullptr;
   bool tuned = false;
-  // characteristic-wise reconstruction (FP64 single problem): U^- and U^+
-  // planes of the current sweep direction and the block solver's scratch
-  double *UMP = nullptr, *cscr = nullptr;
+  // characteristic-wise reconstruction (single problem): U^- and U^+ planes
+  // of the current sweep direction and the block solver's scratch, in the
+  // line arithmetic (FP64, or FP32 for the mixed form)
+  void *UMP = nullptr, *cscr = nullptr;
   // batch
   bool batch = false;
   int nprob = 1;
@@ -622,8 +623,6 @@ int check_config(const pp_cweno_config *c) {
   if (c->precision != PP_PREC_FP64 && c->precision != PP_PREC_MIXED) return PP_ERR_ARG;
   if (c->flux != PP_FLUX_HLLC && c->flux != PP_FLUX_LLF) return PP_ERR_ARG;
   if (c->recon != PP_RECON_COMPONENT && c->recon != PP_RECON_CHARACTERISTIC) return PP_ERR_ARG;
-  // the characteristic-wise form is built for FP64 single problems
-  if (c->recon == PP_RECON_CHARACTERISTIC && c->precision != PP_PREC_FP64) return PP_ERR_UNSUPPORTED;
   int nb = c->ndim == 2 ? 4 : 2;
   for (int k = 0; k < nb; ++k)
     if (!bc_valid(c->bc[k])) return PP_ERR_ARG;
@@ -648,8 +647,9 @@ void fill_common(const pp_cweno_s *h, SweepArgs &a, int stage, double eps_fixed,
   a.flux = h->cfg.flux;
   a.ctl = ctl;
   if (h->cfg.recon == PP_RECON_CHARACTERISTIC) {
+    const size_t es = is_mixed(h) ? sizeof(float) : sizeof(double);
     a.Fm_pre = h->UMP;
-    a.Fp_pre = h->UMP + (size_t)nvals(h);
+    a.Fp_pre = reinterpret_cast<const unsigned char *>(h->UMP) + es * (size_t)nvals(h);
   }
 }
 
@@ -680,6 +680,33 @@ cudaError_t dispatch(const pp_cweno_s *h, int mode, bool periodic, const SweepAr
   SweepArgs b = a;
   b.ih = a.h > 0.0 ? 1.0 / a.h : 0.0;   // batched launches take it per problem
   return launch_sweep(c, b, nlines, h->stream);
+}
+
+// Characteristic-wise handles: the face values of the sweep described by a
+// (line geometry, boundaries) from the planes U in the line arithmetic, into
+// the handle's U^- / U^+ planes (Sec. 2.3); the line kernel then limits them
+// and forms the fluxes and the update.  Nothing to do for other handles.
+cudaError_t launch_char(const pp_cweno_s *h, const SweepArgs &a, const void *U, long long nlines) {
+  if (h->cfg.recon != PP_RECON_CHARACTERISTIC) return cudaSuccess;
+  CharArgs c;
+  c.U = U;
+  c.Um = const_cast<void *>(a.Fm_pre);
+  c.Up = const_cast<void *>(a.Fp_pre);
+  c.scr = h->cscr;
+  c.ncell = h->ncell;
+  c.nlines = nlines;
+  c.cell_stride = a.cell_stride;
+  c.line_stride = a.line_stride;
+  c.n = a.n;
+  c.vn = a.vn;
+  c.vt = a.vt;
+  c.bclo = a.bclo;
+  c.bchi = a.bchi;
+  c.gamma = h->cfg.gamma;
+  c.eps_weno = h->cfg.eps_weno;
+  const bool per = a.bclo == PP_BC_PERIODIC;
+  return is_mixed(h) ? launch_char_recon_f32(c, h->nv, per, h->stream)
+                     : launch_char_recon_f64(c, h->nv, per, h->stream);
 }
 
 // Single-problem launch.  Uin, U0, Uout are state buffers (FP64 planes or
@@ -720,26 +747,8 @@ cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const void *Uin, co
     a.h_other = h->dx;
   }
   a.R = seg_count(a.n);
-  if (h->cfg.recon == PP_RECON_CHARACTERISTIC && !attrs_only) {
-    // the face values of this direction first (Sec. 2.3), then the line
-    // kernel limits them and forms the fluxes and the update
-    CharArgs c;
-    c.U = a.U;
-    c.Um = h->UMP;
-    c.Up = h->UMP + (size_t)nvals(h);
-    c.scr = h->cscr;
-    c.ncell = h->ncell;
-    c.nlines = nlines;
-    c.cell_stride = a.cell_stride;
-    c.line_stride = a.line_stride;
-    c.n = a.n;
-    c.vn = a.vn;
-    c.vt = a.vt;
-    c.bclo = a.bclo;
-    c.bchi = a.bchi;
-    c.gamma = h->cfg.gamma;
-    c.eps_weno = h->cfg.eps_weno;
-    cudaError_t e = launch_char_recon(c, h->nv, a.bclo == PP_BC_PERIODIC, h->stream);
+  if (!attrs_only) {
+    cudaError_t e = launch_char(h, a, is_mixed(h) ? (const void *)a.Uh : (const void *)a.U, nlines);
     if (e != cudaSuccess) return e;
   }
   return dispatch(h, mode, a.bclo == PP_BC_PERIODIC, a, nlines, attrs_only);
@@ -791,6 +800,8 @@ cudaError_t launch_ysweep_t(const pp_cweno_s *h, int stage) {
   a.h = h->dy;
   a.h_other = h->dx;
   a.R = seg_count(a.n);
+  cudaError_t e = launch_char(h, a, h->UT, h->nx);   // rows of the transposed planes
+  if (e != cudaSuccess) return e;
   return dispatch(h, MODE_XSWEEP, a.bclo == PP_BC_PERIODIC, a, h->nx, false);
 }
 
@@ -999,10 +1010,11 @@ int finish_create(pp_cweno_s *h) {
   if (e == cudaSuccess && tr) e = cudaMalloc(&h->UT, sizeof(float) * (size_t)nvals(h));
   if (e == cudaSuccess && tr) e = cudaMalloc(&h->DT, sizeof(float) * (size_t)nvals(h));
   if (e == cudaSuccess && h->cfg.recon == PP_RECON_CHARACTERISTIC) {
-    e = cudaMalloc(&h->UMP, 2 * bytes);
-    long long sx = char_scratch_doubles(h->nv, h->cfg.bc[0] == PP_BC_PERIODIC, h->nx, h->ny);
-    long long sy = h->nv == 4 ? char_scratch_doubles(h->nv, h->cfg.bc[2] == PP_BC_PERIODIC, h->ny, h->nx) : 0;
-    if (e == cudaSuccess) e = cudaMalloc(&h->cscr, sizeof(double) * (size_t)std::max(sx, sy));
+    const size_t es = is_mixed(h) ? sizeof(float) : sizeof(double);
+    e = cudaMalloc(&h->UMP, 2 * es * (size_t)nvals(h));
+    long long sx = char_scratch_values(h->nv, h->cfg.bc[0] == PP_BC_PERIODIC, h->nx, h->ny);
+    long long sy = h->nv == 4 ? char_scratch_values(h->nv, h->cfg.bc[2] == PP_BC_PERIODIC, h->ny, h->nx) : 0;
+    if (e == cudaSuccess) e = cudaMalloc(&h->cscr, es * (size_t)std::max(sx, sy));
   }
   if (e != cudaSuccess) return PP_ERR_CUDA;
   memset(h->hctl, 0, sizeof(Ctl) * h->nprob);
@@ -1030,8 +1042,8 @@ int finish_create(pp_cweno_s *h) {
       h->launches_per_step += (long long)h->groups.size() + (h->btrans ? 1 : 0);
   } else {
     const int sweeps = h->nv == 4 ? 2 : 1;
-    const int per_sweep = h->cfg.recon == PP_RECON_CHARACTERISTIC ? 2 : 1;
-    h->launches_per_step = 1 + 3 * (h->ytrans ? 3 : sweeps * per_sweep);
+    const int chars = h->cfg.recon == PP_RECON_CHARACTERISTIC ? sweeps : 0;
+    h->launches_per_step = 1 + 3 * ((h->ytrans ? 3 : sweeps) + chars);
   }
   return PP_OK;
 }

@@ -73,15 +73,13 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
 
 
 def test_characteristic_form_limits():
-    """The characteristic-wise form is FP64 and single-problem: an unknown
-    selector is PP_ERR_ARG, the mixed form and batches PP_ERR_UNSUPPORTED,
-    all decided before any device call."""
+    """The characteristic-wise form serves single problems: an unknown
+    selector is PP_ERR_ARG, batches and the allocation-free operator
+    PP_ERR_UNSUPPORTED, all decided before any device call."""
     L = binding.lib()
     h = ctypes.c_void_p()
     c = binding.make_config(recon=2)
     assert L.pp_cweno_create(ctypes.byref(c), None, ctypes.byref(h)) == binding.PP_ERR_ARG
-    c = binding.make_config(precision=binding.PREC_MIXED, recon=binding.RECON_CHARACTERISTIC)
-    assert L.pp_cweno_create(ctypes.byref(c), None, ctypes.byref(h)) == binding.PP_ERR_UNSUPPORTED
     c = binding.make_config(recon=binding.RECON_CHARACTERISTIC)
     arr = (binding.Config * 2)(c, c)
     assert L.pp_cweno_create_batch(arr, 2, None, ctypes.byref(h)) == binding.PP_ERR_UNSUPPORTED
