@@ -242,6 +242,41 @@ def run_native(args, ws, rank, local):
                              violations=st.violations, t=st.t, theta2=st.theta2_active)
         s.close()
 
+    # the characteristic-wise form (Sec. 2.3) on the same workload at CFL
+    # omega_1/2 (its positivity bound on the near-vacuum cases), in both
+    # arithmetics: ms per step and the split between the reconstruction
+    # kernel and the line kernel from CUDA events on the solver's stream
+    charf = {}
+    if args.characteristic:
+        for prec, pname, steps in ((1, "mixed", args.char_steps), (0, "fp64", args.char_fp64_steps)):
+            cfg = B.config_from_problem(p, prec, recon=B.RECON_CHARACTERISTIC)
+            cfg.cfl = 1.0 / 24.0
+            s = B.Solver(cfg, stream=stream)
+            s.set_state(U0)
+            s.enqueue_steps(2)
+            torch.cuda.synchronize()
+            prof = s.profile_step()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            s.enqueue_steps(steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            st = s.stats()
+            launches = s.launches_per_step()
+            s.close()
+            names = (["char_rows_x", "char_solve_x", "x_sweep", "char_rows_y", "char_solve_y",
+                      "y_sweep_transposed", "stage_combine"] if prec == 1 else
+                     ["char_rows_x", "char_solve_x", "x_sweep", "char_rows_y", "char_solve_y", "y_sweep"])
+            per = prof[1:]           # prof[0]: the per-step dt kernel
+            kms = {nm: sum(per[i::len(names)]) / max(1, len(per[i::len(names)]))
+                   for i, nm in enumerate(names)}
+            charf[pname] = {"value": ncell * 3 * steps / (ms * 1e-3), "unit": UNIT,
+                            "steps": steps, "ms_per_step": ms / steps,
+                            "kernel_ms": {k: round(v, 4) for k, v in kms.items()},
+                            "gpu_launches_per_step": int(launches),
+                            "violations": int(st.violations)}
+
     # end-to-end through the public API with host buffers: H2D initial state,
     # K steps, D2H final state, inside one wall-clock region
     s = B.Solver(B.config_from_problem(p, 1, cfl_positivity_cap=True), stream=stream)
@@ -327,7 +362,7 @@ def run_native(args, ws, rank, local):
             batches[name] = row
 
     return dict(results=results, ncell=ncell, e2e_s=e2e_s, acc=acc,
-                state_bytes=U0.nbytes, batches=batches)
+                state_bytes=U0.nbytes, batches=batches, characteristic=charf)
 
 
 def _roofline(r, prec, ncell, hbm_peak, peak_kind):
@@ -416,6 +451,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batches", type=int, default=1, help="also time the batch workloads (0: skip)")
+    ap.add_argument("--characteristic", type=int, default=1,
+                    help="also time the characteristic-wise form on the blast (0: skip)")
+    ap.add_argument("--char-steps", type=int, default=20)
+    ap.add_argument("--char-fp64-steps", type=int, default=3)
     ap.add_argument("--profile-only", choices=["mixed", "fp64"], default=None,
                     help="only run --steps steps of the blast on an --n^2 grid (for ncu)")
     ap.add_argument("--n", type=int, default=N_GRID)
@@ -490,6 +529,11 @@ def main():
                                        "exact vacuum and those an FP64 dry run of the same steps "
                                        "takes out of G, 256 2-D four-quadrant problems of "
                                        "128^2-1024^2", **out["batches"]}
+        if out["characteristic"]:
+            line["characteristic"] = {"note": "the same 4096^2 blast with the characteristic-wise "
+                                              "reconstruction of Sec. 2.3 (block tridiagonal "
+                                              "systems, Roe-averaged eigenvectors), CFL 1/24",
+                                      **out["characteristic"]}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline()
         print(json.dumps(line), flush=True)

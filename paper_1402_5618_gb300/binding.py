@@ -251,9 +251,9 @@ class Solver:
 
     def profile_step(self) -> list[float]:
         """per-kernel durations (ms) of one step, launch by launch"""
-        ms = (C.c_float * 16)()
+        ms = (C.c_float * 32)()
         nk = C.c_int()
-        _check(lib().pp_cweno_profile_step(self.h, ms, 16, C.byref(nk)), "profile_step")
+        _check(lib().pp_cweno_profile_step(self.h, ms, 32, C.byref(nk)), "profile_step")
         return [ms[i] for i in range(nk.value)]
 
     def rows_per_chunk(self) -> int:

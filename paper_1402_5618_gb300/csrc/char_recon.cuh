@@ -2,18 +2,21 @@
 // one sweep direction (Sec. 2.3, steps 1-4, eqs. (cha-1), (1DEuler-FVC)).
 //
 // For every line and each side (minus: U^-_{i+1/2}, plus: U^+_{i-1/2}) the
-// block tridiagonal system of the line is assembled and solved by one
-// thread, walking the line in the stable elimination order (minus left to
-// right, plus right to left).  At each position the thread forms the Roe
-// average of the two cells adjacent to the unknown's face, its left
+// block tridiagonal system of the line is assembled and solved in two
+// kernels.  The first runs over every row of every line in parallel: the
+// Roe average of the two cells adjacent to the row's face, its left
 // eigenvectors l^(k) (eq. (leigenv); the 4 x 4 system with the shear field in
-// 2-D), the characteristic variables l^(k) ubar of the five-cell stencil, the
-// WENO-Z weights of each field and the block row diag(a, b, c) L; the block
-// Thomas multipliers go to a scratch buffer laid out [row][entry][line] so
-// that the threads of a warp (consecutive lines) access it together.
-// Periodic lines carry the Woodbury columns of the cyclic correction through
-// the same pass.  Bounded lines close the first and last unknown with the
-// explicit WENO5-Z value of each characteristic variable at that face.
+// 2-D), the characteristic variables l^(k) ubar of the five-cell stencil, and
+// per field the WENO-Z weights and scalar row coefficients (a, b, c, r).  The
+// second walks each line in the stable elimination order (minus left to
+// right, plus right to left), one thread per (line, side), forming the block
+// row diag(a, b, c) L and one block Thomas step per position; only that
+// recurrence is serial.  The multipliers go to a scratch buffer laid out
+// [row][entry][line] so that the threads of a warp (consecutive lines) access
+// it together.  Periodic lines carry the Woodbury columns of the cyclic
+// correction through the same pass.  Bounded lines close the first and last
+// unknown with the explicit WENO5-Z value of each characteristic variable at
+// that face.
 //
 // The output planes hold U^- and U^+ of every cell in the state's layout and
 // grid variable order; the line kernel limits them, evaluates the face
@@ -28,7 +31,8 @@ struct CharArgs {
   const void *U;            // stage input: planes [nv][ncell] of the line's arithmetic
                             // (FP64, or the FP32 hi parts of the mixed form)
   void *Um, *Up;            // out: U^-_{i+1/2}, U^+_{i-1/2} of every cell, same layout and type
-  void *scr;                // scratch, char_scratch_values() values of the same type
+  void *scr;                // block Thomas scratch, char_scratch_values() values of the same type
+  void *rows;               // row coefficients, char_rows_values() values of the same type
   long long ncell;          // cells per variable plane
   long long nlines;
   long long cell_stride, line_stride;
@@ -50,9 +54,16 @@ inline long long char_scratch_values(int nv, bool periodic, long long n, long lo
   return 2 * (n * char_row_values(nv, periodic) + (long long)nv * nv) * nlines;
 }
 
-// one launch per precision, each in its own translation unit (the FP32 one
-// is compiled with the mixed form's fast division and square root)
-cudaError_t launch_char_recon_f64(const CharArgs &a, int nv, bool periodic, cudaStream_t st);
-cudaError_t launch_char_recon_f32(const CharArgs &a, int nv, bool periodic, cudaStream_t st);
+// row data of every row of both sides: the four Roe scalars the
+// eigenvectors depend on and (a, b, c, r) of every field
+inline long long char_rows_values(int nv, long long n, long long nlines) {
+  return 2 * (4 * (long long)nv + 4) * n * nlines;
+}
+
+// one entry per precision, each in its own translation unit (the FP32 one
+// is compiled with the mixed form's fast division and square root); part 0
+// launches the parallel rows kernel, part 1 the serial block solve
+cudaError_t launch_char_recon_f64(const CharArgs &a, int nv, bool periodic, int part, cudaStream_t st);
+cudaError_t launch_char_recon_f32(const CharArgs &a, int nv, bool periodic, int part, cudaStream_t st);
 
 }  // namespace ppk

@@ -3,7 +3,7 @@
 #include "char_recon_kernel.cuh"
 
 namespace ppk {
-cudaError_t launch_char_recon_f32(const CharArgs &a, int nv, bool periodic, cudaStream_t st) {
-  return chr::launch_char_recon_t<float>(a, nv, periodic, st);
+cudaError_t launch_char_recon_f32(const CharArgs &a, int nv, bool periodic, int part, cudaStream_t st) {
+  return chr::launch_char_recon_t<float>(a, nv, periodic, part, st);
 }
 }  // namespace ppk

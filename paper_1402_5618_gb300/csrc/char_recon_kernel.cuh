@@ -10,13 +10,11 @@
 namespace ppk {
 namespace chr {
 
-// Sec. 2.3: rows l^(k) of L, the left eigenvectors of the flux Jacobian at
-// the Roe average of Ua and Ub (eqs. (eigen), (leigenv)), ordered by the
-// eigenvalues u - a, u, (u,) u + a; in 2-D the third row is the shear field
-// (-v, 0, 1, 0) and v enters the acoustic rows through |u|^2 and -c1 v / 2.
+// Sec. 2.3: the Roe average of Ua and Ub, reduced to the four scalars the
+// left eigenvectors depend on: u, v (2-D), 1/a and c1 = (gamma - 1)/a^2
 template <typename real, int NV>
-__device__ __forceinline__ void roe_left(const real *Ua, const real *Ub, real gamma,
-                                         real (&L)[NV][NV]) {
+__device__ __forceinline__ void roe_scalars(const real *Ua, const real *Ub, real gamma,
+                                            real (&rs)[4]) {
   const real one = real(1), half = real(0.5);
   const real sa = sqrt(Ua[0]), sb = sqrt(Ub[0]);
   const real isab = one / (sa + sb);
@@ -24,10 +22,21 @@ __device__ __forceinline__ void roe_left(const real *Ua, const real *Ub, real ga
   const real u = (Ua[1] / sa + Ub[1] / sb) * isab;
   const real v = NV == 4 ? (Ua[2] / sa + Ub[2] / sb) * isab : real(0);
   const real H = ((Ua[NV - 1] + pa) / sa + (Ub[NV - 1] + pb) / sb) * isab;
-  const real q2 = u * u + v * v;
-  const real a2 = (gamma - one) * (H - half * q2);
-  const real ia = one / sqrt(a2);
-  const real c1 = (gamma - one) / a2, c2 = half * q2 * c1;
+  const real a2 = (gamma - one) * (H - half * (u * u + v * v));
+  rs[0] = u;
+  rs[1] = v;
+  rs[2] = one / sqrt(a2);
+  rs[3] = (gamma - one) / a2;
+}
+
+// rows l^(k) of L (eqs. (eigen), (leigenv)), ordered by the eigenvalues
+// u - a, u, (u,) u + a; in 2-D the third row is the shear field
+// (-v, 0, 1, 0) and v enters the acoustic rows through |u|^2 and -c1 v / 2
+template <typename real, int NV>
+__device__ __forceinline__ void left_from(const real (&rs)[4], real (&L)[NV][NV]) {
+  const real one = real(1), half = real(0.5);
+  const real u = rs[0], v = rs[1], ia = rs[2], c1 = rs[3];
+  const real c2 = half * (u * u + v * v) * c1;
   L[0][0] = half * (c2 + u * ia);
   L[0][1] = -half * (c1 * u + ia);
   L[0][NV - 1] = half * c1;
@@ -130,116 +139,202 @@ __device__ __forceinline__ void char_ratios(const real (&v)[5], real mag, real e
   }
 }
 
-// One thread per (line, side).  Position p of the walk is cell p (minus
-// side, left to right) or cell n-1-p (plus side, right to left); in walk
-// order both sides have the same rows (the plus row is the mirror image of
-// the minus row), so "previous" and "next" below are in walk order.
+// ghost-aware read of the line variables of line cell i (both kernels)
+template <typename real, int NV, bool PER>
+__device__ __forceinline__ void line_cell(const CharArgs &a, const real *U, long long lbase,
+                                          const int (&gv)[NV], int i, real (&out)[NV]) {
+  const int n = a.n;
+  bool neg = false;
+  if (i < 0 || i >= n) {
+    if (PER) {
+      i = (i % n + n) % n;
+    } else {
+      const int bc = i < 0 ? a.bclo : a.bchi;
+      if (bc == 1) {
+        i = i < 0 ? 0 : n - 1;
+      } else {
+        i = i < 0 ? -i - 1 : 2 * n - 1 - i;
+        neg = true;
+      }
+    }
+  }
+  const real *src = U + lbase + (long long)i * a.cell_stride;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = src[gv[k] * a.ncell];
+  if (neg) out[1] = -out[1];
+}
+
+template <int NV>
+__device__ __forceinline__ void grid_vars(const CharArgs &a, int (&gv)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) gv[k] = k == 0 ? 0 : (k == NV - 1 ? NV - 1 : (k == 1 ? a.vn : a.vt));
+}
+
+// Steps 1-3 at every face, all in parallel.  One block takes a tile of 32
+// lines x 32 cells (plus the two-cell halo) into shared memory -- loaded
+// along whichever of the two axes is contiguous in memory -- and computes
+// the rows of both sides of every cell of the tile: the Roe scalars of the
+// row's face, the characteristic variables of its five-cell stencil (walk
+// order) and, per field k, the WENO-Z weights and the scalar row (a on the
+// previous unknown of the walk, b on this one, c on the next, r the
+// right-hand side; closure rows of bounded lines 0, 1, 0 and the explicit
+// WENO5-Z value).  Output per row: the 4 Roe scalars and 4 NV coefficients,
+// laid out [side][position][entry][line] so that both this kernel's stores
+// and the serial walk's loads are contiguous over the lines of a warp.
+constexpr int CT_L = 32, CT_C = 32;   // lines x cells of a tile
+
+template <typename real, int NV, bool PER>
+__global__ void __launch_bounds__(256) char_rows_kernel(const CharArgs a) {
+  constexpr bool F32 = sizeof(real) == 4;
+  constexpr int RC = 4 * NV + 4;
+  constexpr int TW = CT_C + 4;        // cells of a tile row with the halo
+  __shared__ real tile[NV][CT_L][TW + 1];
+  const int n = a.n;
+  const long long NL = a.nlines;
+  const long long line0 = (long long)blockIdx.x * CT_L;
+  const int c0 = blockIdx.y * CT_C;
+  const real *U = reinterpret_cast<const real *>(a.U);
+  int gv[NV];
+  grid_vars<NV>(a, gv);
+  const int tid = threadIdx.x;
+  const bool along_cells = a.cell_stride == 1;
+  for (int idx = tid; idx < CT_L * TW; idx += blockDim.x) {
+    const int ll = along_cells ? idx / TW : idx % CT_L;
+    const int j = along_cells ? idx % TW : idx / CT_L;
+    const int i = c0 - 2 + j;
+    if (line0 + ll >= NL || i < -2 || i > n + 1) continue;   // never read
+    real v[NV];
+    line_cell<real, NV, PER>(a, U, (line0 + ll) * a.line_stride, gv, i, v);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tile[k][ll][j] = v[k];
+  }
+  __syncthreads();
+  const int ll = tid % CT_L;
+  const long long line = line0 + ll;
+  if (line >= NL) return;
+  real *rows = reinterpret_cast<real *>(a.rows);
+  const real gam = real(a.gamma), eps = real(a.eps_weno);
+  for (int q = tid / CT_L; q < 2 * CT_C; q += blockDim.x / CT_L) {
+    const int side = q / CT_C;
+    const int c = c0 + q % CT_C;
+    if (c >= n) continue;
+    const int dir = side == 0 ? 1 : -1;
+    const int p = side == 0 ? c : n - 1 - c;
+    const int jc = c - c0 + 2;        // the cell's column in the tile
+    real win[5][NV];
+#pragma unroll
+    for (int w = 0; w < 5; ++w)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) win[w][k] = tile[k][ll][jc + (w - 2) * dir];
+    real rs[4], L[NV][NV];
+    roe_scalars<real, NV>(win[2], win[3], gam, rs);
+    left_from<real, NV>(rs, L);
+    const bool closure = !PER && (p == 0 || p == n - 1);
+    real *dst = rows + ((long long)side * n + p) * RC * NL + line;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dst[e * NL] = rs[e];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      real cv[5];
+      real mag = real(0);
+#pragma unroll
+      for (int w = 0; w < 5; ++w) {
+        real s0 = real(0), s1 = real(0);
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+          s0 += L[k][m] * win[w][m];
+          if (F32) s1 += fabs(L[k][m]) * fabs(win[w][m]);
+        }
+        cv[w] = s0;
+        if (F32) mag = fmax(mag, s1);
+      }
+      real q0, q1, q2, w0, w1, w2, one;
+      char_ratios<real>(cv, mag, eps, q0, q1, q2, one);
+      real fa, fb, fc, fr;
+      if (closure) {
+        zweights<real>(real(0.1), real(0.6), real(0.3), q0, q1, q2, w0, w1, w2, one);
+        const real p0 = real(2) * cv[0] - real(7) * cv[1] + real(11) * cv[2];
+        const real p1 = -cv[1] + real(5) * cv[2] + real(2) * cv[3];
+        const real p2 = real(2) * cv[2] + real(5) * cv[3] - cv[4];
+        fa = real(0);
+        fb = real(1);
+        fc = real(0);
+        fr = (w0 * p0 + w1 * p1 + w2 * p2) * real(1.0 / 6.0);
+      } else {
+        zweights<real>(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
+        const Row<real> row = compact_row<real>(w0, w1, w2, cv[1], cv[2], cv[3]);
+        fa = row.a;
+        fb = row.b;
+        fc = row.c;
+        fr = row.r;
+      }
+      dst[(4 + 4 * k + 0) * NL] = fa;
+      dst[(4 + 4 * k + 1) * NL] = fb;
+      dst[(4 + 4 * k + 2) * NL] = fc;
+      dst[(4 + 4 * k + 3) * NL] = fr;
+    }
+  }
+}
+
+// Step 4, the serial part: one thread per (line, side) walks the line in
+// the elimination order.  Position p of the walk is cell p (minus side,
+// left to right) or cell n-1-p (plus side, right to left); in walk order
+// both sides have the same rows (the plus row is the mirror image of the
+// minus row), so "previous" and "next" below are in walk order.  At each
+// position the thread rebuilds L from the four Roe scalars, takes the row
+// coefficients from char_rows_kernel, and runs one step of block Thomas;
+// the next position's loads are issued before this position's arithmetic.
 // Periodic lines solve the cyclic system with the Woodbury correction
 // T = T' + U V^T, G = -B_0: T' has B_0 - G at the first position and
 // B_{n-1} - C_{n-1} G^{-1} A_0 at the last, U = (G, 0, .., 0, C_{n-1}),
 // V^T = (I, 0, .., 0, G^{-1} A_0); the NV columns of U ride along as extra
 // right-hand sides and x = y - Z (I + V^T Z)^{-1} V^T y at the end.
 template <typename real, int NV, bool PER>
-__global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
-  constexpr bool F32 = sizeof(real) == 4;
+__global__ void __launch_bounds__(32) char_solve_kernel(const CharArgs a) {
   constexpr int NC = PER ? NV + 1 : 1;       // right-hand-side columns
   constexpr int ROW = NV * NV + NV * NC;     // scratch values per row: Y, g
+  constexpr int RC = 4 * NV + 4;             // Roe scalars and row coefficients per position
   const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= a.nlines) return;
   const int side = blockIdx.y;
   const int n = a.n;
-  const int dir = side == 0 ? 1 : -1;
   const long long NL = a.nlines;
   const long long lbase = line * a.line_stride;
-  const real *U = reinterpret_cast<const real *>(a.U);
+  const real *rows = reinterpret_cast<const real *>(a.rows) + (long long)side * n * RC * NL + line;
+  auto rowv = [&](int p, int e) { return rows[((long long)p * RC + e) * NL]; };
   real *scr = reinterpret_cast<real *>(a.scr) + (long long)side * ((long long)n * ROW + NV * NV) * NL + line;
   auto slot = [&](int p, int e) -> real & { return scr[((long long)p * ROW + e) * NL]; };
   auto wslot = [&](int e) -> real & { return scr[((long long)n * ROW + e) * NL]; };
-  const real gam = real(a.gamma), eps = real(a.eps_weno);
   int gv[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) gv[k] = k == 0 ? 0 : (k == NV - 1 ? NV - 1 : (k == 1 ? a.vn : a.vt));
-
-  // line variables of line cell i (ghost cells by the boundary condition)
-  auto cell = [&](int i, real(&out)[NV]) {
-    bool neg = false;
-    if (i < 0 || i >= n) {
-      if (PER) {
-        i = (i % n + n) % n;
-      } else {
-        const int bc = i < 0 ? a.bclo : a.bchi;
-        if (bc == 1) {
-          i = i < 0 ? 0 : n - 1;
-        } else {
-          i = i < 0 ? -i - 1 : 2 * n - 1 - i;
-          neg = true;
-        }
-      }
-    }
-    const real *src = U + lbase + (long long)i * a.cell_stride;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] = src[gv[k] * a.ncell];
-    if (neg) out[1] = -out[1];
-  };
+  grid_vars<NV>(a, gv);
   auto cidx = [&](int p) { return side == 0 ? p : n - 1 - p; };
 
-  real win[5][NV];   // walk offsets -2 .. +2 of the current position
+  // the row data (Roe scalars, coefficients), loaded one position ahead
+  real co[RC], con[RC];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) cell(cidx(0) + (q - 2) * dir, win[q + 1]);
+  for (int e = 0; e < RC; ++e) co[e] = rowv(0, e);
 
   real Yp[NV][NV], gp[NV][NC];   // the previous position's multipliers
 #pragma unroll 1
   for (int p = 0; p < n; ++p) {
+    if (p + 1 < n) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) win[q][k] = win[q + 1][k];
-    cell(cidx(p) + 2 * dir, win[4]);
-
-    // step 1: eigenvectors at the unknown's face (this cell and the next)
+      for (int e = 0; e < RC; ++e) con[e] = rowv(p + 1, e);
+    }
     real L[NV][NV];
-    roe_left<real, NV>(win[2], win[3], gam, L);
-    // steps 2-3: characteristic variables of the five cells, per-field
-    // weights and scalar row (a on the previous unknown, b on this one, c on
-    // the next); closure rows 0 x + 1 x + 0 x = explicit WENO5-Z value
-    const bool closure = !PER && (p == 0 || p == n - 1);
+    {
+      const real rs[4] = {co[0], co[1], co[2], co[3]};
+      left_from<real, NV>(rs, L);
+    }
     real ca[NV], cb[NV], cc[NV], cr[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      real cv[5];
-      real mag = real(0);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        real t = real(0), s = real(0);
-#pragma unroll
-        for (int m = 0; m < NV; ++m) {
-          t += L[k][m] * win[q][m];
-          if (F32) s += fabs(L[k][m]) * fabs(win[q][m]);
-        }
-        cv[q] = t;
-        if (F32) mag = fmax(mag, s);
-      }
-      real q0, q1, q2, w0, w1, w2, one;
-      char_ratios<real>(cv, mag, eps, q0, q1, q2, one);
-      if (closure) {
-        zweights<real>(real(0.1), real(0.6), real(0.3), q0, q1, q2, w0, w1, w2, one);
-        const real p0 = real(2) * cv[0] - real(7) * cv[1] + real(11) * cv[2];
-        const real p1 = -cv[1] + real(5) * cv[2] + real(2) * cv[3];
-        const real p2 = real(2) * cv[2] + real(5) * cv[3] - cv[4];
-        ca[k] = real(0);
-        cb[k] = real(1);
-        cc[k] = real(0);
-        cr[k] = (w0 * p0 + w1 * p1 + w2 * p2) * real(1.0 / 6.0);
-      } else {
-        zweights<real>(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
-        const Row<real> r = compact_row<real>(w0, w1, w2, cv[1], cv[2], cv[3]);
-        ca[k] = r.a;
-        cb[k] = r.b;
-        cc[k] = r.c;
-        cr[k] = r.r;
-      }
+      ca[k] = co[4 + 4 * k];
+      cb[k] = co[4 + 4 * k + 1];
+      cc[k] = co[4 + 4 * k + 2];
+      cr[k] = co[4 + 4 * k + 3];
     }
-    // step 4: block row diag(ca, cb, cc) L, eliminated against the previous
+    // block row diag(ca, cb, cc) L, eliminated against the previous
     // position: Bp = B - A Y_prev, X = [C | r - A g_prev]
     real Bp[NV][NV], X[NV][NV + NC];
 #pragma unroll
@@ -334,33 +429,45 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
         slot(p, NV * NV + k * NC + c) = X[k][NV + c];
       }
     }
+#pragma unroll
+    for (int e = 0; e < RC; ++e) co[e] = con[e];
   }
 
-  // back substitution x_p = g_p - Y_p x_{p+1}
+  // back substitution x_p = g_p - Y_p x_{p+1}, the next position's
+  // multipliers loaded one position ahead
   real *out = reinterpret_cast<real *>(side == 0 ? a.Um : a.Up);
   real x[NV][NC];
 #pragma unroll
   for (int k = 0; k < NV; ++k)
 #pragma unroll
     for (int c = 0; c < NC; ++c) x[k][c] = gp[k][c];
+  real Yn[ROW];
+  if (n >= 2) {
+#pragma unroll
+    for (int e = 0; e < ROW; ++e) Yn[e] = slot(n - 2, e);
+  }
 #pragma unroll 1
   for (int p = n - 1; p >= 0; --p) {
     if (p < n - 1) {
-      real Y[NV][NV], xn[NV][NC];
+      real Yc[ROW];
 #pragma unroll
-      for (int k = 0; k < NV; ++k) {
+      for (int e = 0; e < ROW; ++e) Yc[e] = Yn[e];
+      if (p > 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) Y[k][j] = slot(p, k * NV + j);
+        for (int e = 0; e < ROW; ++e) Yn[e] = slot(p - 1, e);
+      }
+      real xn[NV][NC];
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
 #pragma unroll
         for (int c = 0; c < NC; ++c) xn[k][c] = x[k][c];
-      }
 #pragma unroll
       for (int k = 0; k < NV; ++k)
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          real s = slot(p, NV * NV + k * NC + c);
+          real s = Yc[NV * NV + k * NC + c];
 #pragma unroll
-          for (int j = 0; j < NV; ++j) s -= Y[k][j] * xn[j][c];
+          for (int j = 0; j < NV; ++j) s -= Yc[k * NV + j] * xn[j][c];
           x[k][c] = s;
         }
     }
@@ -412,17 +519,22 @@ __global__ void __launch_bounds__(32) char_recon_kernel(const CharArgs a) {
   }
 }
 
-template <typename real>
-cudaError_t launch_char_recon_t(const CharArgs &a, int nv, bool periodic, cudaStream_t st) {
-  const dim3 grid((unsigned)((a.nlines + 31) / 32), 2, 1);
-  if (nv == 3) {
-    if (periodic) char_recon_kernel<real, 3, true><<<grid, 32, 0, st>>>(a);
-    else char_recon_kernel<real, 3, false><<<grid, 32, 0, st>>>(a);
+template <typename real, int NV, bool PER>
+cudaError_t launch_nv(const CharArgs &a, int part, cudaStream_t st) {
+  if (part == 0) {
+    const dim3 grid((unsigned)((a.nlines + CT_L - 1) / CT_L), (unsigned)((a.n + CT_C - 1) / CT_C), 1);
+    char_rows_kernel<real, NV, PER><<<grid, 256, 0, st>>>(a);
   } else {
-    if (periodic) char_recon_kernel<real, 4, true><<<grid, 32, 0, st>>>(a);
-    else char_recon_kernel<real, 4, false><<<grid, 32, 0, st>>>(a);
+    char_solve_kernel<real, NV, PER><<<dim3((unsigned)((a.nlines + 31) / 32), 2, 1), 32, 0, st>>>(a);
   }
   return cudaGetLastError();
+}
+
+// part 0: the parallel rows kernel; part 1: the serial block solve
+template <typename real>
+cudaError_t launch_char_recon_t(const CharArgs &a, int nv, bool periodic, int part, cudaStream_t st) {
+  if (nv == 3) return periodic ? launch_nv<real, 3, true>(a, part, st) : launch_nv<real, 3, false>(a, part, st);
+  return periodic ? launch_nv<real, 4, true>(a, part, st) : launch_nv<real, 4, false>(a, part, st);
 }
 
 }  // namespace chr

@@ -17,6 +17,7 @@
 
 #include <new>
 #include <algorithm>
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -573,7 +574,10 @@ struct pp_cweno_s {
   // characteristic-wise reconstruction (single problem): U^- and U^+ planes
   // of the current sweep direction and the block solver's scratch, in the
   // line arithmetic (FP64, or FP32 for the mixed form)
-  void *UMP = nullptr, *cscr = nullptr;
+  void *UMP = nullptr, *cscr = nullptr, *crows = nullptr;
+  // per-kernel profiling: called after each reconstruction launch, so that
+  // the reconstruction and the line kernel get separate events
+  std::function<void()> mark_hook;
   // batch
   bool batch = false;
   int nprob = 1;
@@ -693,6 +697,7 @@ cudaError_t launch_char(const pp_cweno_s *h, const SweepArgs &a, const void *U, 
   c.Um = const_cast<void *>(a.Fm_pre);
   c.Up = const_cast<void *>(a.Fp_pre);
   c.scr = h->cscr;
+  c.rows = h->crows;
   c.ncell = h->ncell;
   c.nlines = nlines;
   c.cell_stride = a.cell_stride;
@@ -705,8 +710,13 @@ cudaError_t launch_char(const pp_cweno_s *h, const SweepArgs &a, const void *U, 
   c.gamma = h->cfg.gamma;
   c.eps_weno = h->cfg.eps_weno;
   const bool per = a.bclo == PP_BC_PERIODIC;
-  return is_mixed(h) ? launch_char_recon_f32(c, h->nv, per, h->stream)
-                     : launch_char_recon_f64(c, h->nv, per, h->stream);
+  cudaError_t e = cudaSuccess;
+  for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+    e = is_mixed(h) ? launch_char_recon_f32(c, h->nv, per, part, h->stream)
+                    : launch_char_recon_f64(c, h->nv, per, part, h->stream);
+    if (e == cudaSuccess && h->mark_hook) h->mark_hook();
+  }
+  return e;
 }
 
 // Single-problem launch.  Uin, U0, Uout are state buffers (FP64 planes or
@@ -848,11 +858,12 @@ cudaError_t transpose_state_hi(const pp_cweno_s *h) {
 
 // enqueue one step: the per-problem dt kernel, then 3 stages; with ev, an
 // event is recorded after every launch (ev[0] before the first)
-cudaError_t enqueue_step(pp_cweno_s *h, cudaEvent_t *ev = nullptr, int *nev = nullptr) {
+cudaError_t enqueue_step_body(pp_cweno_s *h, cudaEvent_t *ev, int *nev) {
   int k = 0;
   auto mark = [&]() {
     if (ev) cudaEventRecord(ev[k++], h->stream);
   };
+  if (ev) h->mark_hook = mark;   // events after the reconstruction launches too
   mark();
   step_begin_kernel<<<(h->nprob + 127) / 128, 128, 0, h->stream>>>(h->ctl, h->nprob);
   cudaError_t e = cudaGetLastError();
@@ -909,6 +920,12 @@ cudaError_t enqueue_step(pp_cweno_s *h, cudaEvent_t *ev = nullptr, int *nev = nu
   }
   if (nev) *nev = k;
   return cudaSuccess;
+}
+
+cudaError_t enqueue_step(pp_cweno_s *h, cudaEvent_t *ev = nullptr, int *nev = nullptr) {
+  cudaError_t e = enqueue_step_body(h, ev, nev);
+  h->mark_hook = nullptr;
+  return e;
 }
 
 int build_graph(pp_cweno_s *h) {
@@ -1015,6 +1032,9 @@ int finish_create(pp_cweno_s *h) {
     long long sx = char_scratch_values(h->nv, h->cfg.bc[0] == PP_BC_PERIODIC, h->nx, h->ny);
     long long sy = h->nv == 4 ? char_scratch_values(h->nv, h->cfg.bc[2] == PP_BC_PERIODIC, h->ny, h->nx) : 0;
     if (e == cudaSuccess) e = cudaMalloc(&h->cscr, es * (size_t)std::max(sx, sy));
+    const long long rx = char_rows_values(h->nv, h->nx, h->ny);
+    const long long ry = h->nv == 4 ? char_rows_values(h->nv, h->ny, h->nx) : 0;
+    if (e == cudaSuccess) e = cudaMalloc(&h->crows, es * (size_t)std::max(rx, ry));
   }
   if (e != cudaSuccess) return PP_ERR_CUDA;
   memset(h->hctl, 0, sizeof(Ctl) * h->nprob);
@@ -1042,7 +1062,7 @@ int finish_create(pp_cweno_s *h) {
       h->launches_per_step += (long long)h->groups.size() + (h->btrans ? 1 : 0);
   } else {
     const int sweeps = h->nv == 4 ? 2 : 1;
-    const int chars = h->cfg.recon == PP_RECON_CHARACTERISTIC ? sweeps : 0;
+    const int chars = h->cfg.recon == PP_RECON_CHARACTERISTIC ? 2 * sweeps : 0;
     h->launches_per_step = 1 + 3 * ((h->ytrans ? 3 : sweeps) + chars);
   }
   return PP_OK;
@@ -1731,6 +1751,7 @@ int pp_cweno_destroy(pp_cweno_t h) {
   cudaFree(h->DT);
   cudaFree(h->UMP);
   cudaFree(h->cscr);
+  cudaFree(h->crows);
   for (auto &g : h->groups) cudaFree(g.lines);
   if (h->hctl) cudaFreeHost(h->hctl);
   delete h;
