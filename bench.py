@@ -184,12 +184,12 @@ ALU_PEAK_TFLOPS = {1: 152 * 128 * 2 * 2.07e9 / 1e12, 0: 1.25}
 # the stage-1 sweeps of the first step): reads are the algorithmic bytes;
 # writes fall short of them by what is still dirty in L2 when the kernel ends.
 TRAFFIC_PER_CELL = {            # {(precision, kernel): bytes per cell}
-    (1, "x_sweep"): 27.48,
-    (1, "y_sweep_transposed"): 27.36,
-    (0, "x_sweep"): 59.70,
-    (0, "y_sweep"): 94.51,
+    (1, "x_sweep"): 27.33,
+    (1, "y_sweep_transposed"): 27.28,
+    (0, "x_sweep"): 59.72,
+    (0, "y_sweep"): 94.22,
 }
-TRAFFIC_SRC_SHA256 = "bb6dbbdce688b539f3a07f04af799220f1079b73bc0a6454168a6becc600604e"
+TRAFFIC_SRC_SHA256 = "c68c7ca33da9eda1d81cd1221b7f32901b887d7c00f68567b6f8600169393ec8"
 KERNEL_SOURCES = ("line_sweep.cuh", "physics.cuh", "dfloat.cuh")
 
 
@@ -458,6 +458,8 @@ def main():
     ap.add_argument("--profile-only", choices=["mixed", "fp64"], default=None,
                     help="only run --steps steps of the blast on an --n^2 grid (for ncu)")
     ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--recon", type=int, default=0,
+                    help="--profile-only: 0 component-wise, 1 characteristic-wise reconstruction")
     ap.add_argument("--accuracy", action="store_true",
                     help="accuracy study instead of the throughput line: the blast to t = 1 in "
                          "both forms at --blast-n, the vortex at --vortex-n against its closed form")
@@ -550,12 +552,14 @@ def profile_only(args):
     from paper_1402_5618_gb300 import workloads as W
     prec = B.PREC_MIXED if args.profile_only == "mixed" else B.PREC_FP64
     p = W.blast_2d(args.n)
-    s = B.Solver(B.config_from_problem(p, prec, cfl_positivity_cap=True))
+    cfg = B.config_from_problem(p, prec, cfl_positivity_cap=True, recon=args.recon)
+    s = B.Solver(cfg)
     s.set_state(np.ascontiguousarray(p.U0).ravel())
     s.enqueue_steps(args.steps)
     torch.cuda.synchronize()
     st = s.stats()
-    print(json.dumps({"profile_only": args.profile_only, "n": args.n, "steps": st.steps,
+    print(json.dumps({"profile_only": args.profile_only, "recon": args.recon, "n": args.n,
+                      "steps": st.steps,
                       "violations": st.violations, "rows_per_chunk": s.rows_per_chunk()}))
     s.close()
 
