@@ -139,6 +139,22 @@ __device__ __forceinline__ void char_ratios(const real (&v)[5], real mag, real e
   }
 }
 
+// asynchronous copies global -> shared (cp.async): a per-thread ring in
+// shared memory keeps several positions' loads of the serial walk in flight
+template <int B>
+__device__ __forceinline__ void cp_async(void *sdst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  if constexpr (B == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // ghost-aware read of the line variables of line cell i (both kernels)
 template <typename real, int NV, bool PER>
 __device__ __forceinline__ void line_cell(const CharArgs &a, const real *U, long long lbase,
@@ -282,8 +298,10 @@ __global__ void __launch_bounds__(256) char_rows_kernel(const CharArgs a) {
 // both sides have the same rows (the plus row is the mirror image of the
 // minus row), so "previous" and "next" below are in walk order.  At each
 // position the thread rebuilds L from the four Roe scalars, takes the row
-// coefficients from char_rows_kernel, and runs one step of block Thomas;
-// the next position's loads are issued before this position's arithmetic.
+// coefficients from char_rows_kernel, and runs one step of block Thomas.
+// The walk is bound by the latency of its own loads (few chains per SM), so
+// the row data of the next PD - 1 positions, and in the back substitution
+// their multipliers, are in flight in a per-thread shared-memory ring.
 // Periodic lines solve the cyclic system with the Woodbury correction
 // T = T' + U V^T, G = -B_0: T' has B_0 - G at the first position and
 // B_{n-1} - C_{n-1} G^{-1} A_0 at the last, U = (G, 0, .., 0, C_{n-1}),
@@ -301,7 +319,6 @@ __global__ void __launch_bounds__(32) char_solve_kernel(const CharArgs a) {
   const long long NL = a.nlines;
   const long long lbase = line * a.line_stride;
   const real *rows = reinterpret_cast<const real *>(a.rows) + (long long)side * n * RC * NL + line;
-  auto rowv = [&](int p, int e) { return rows[((long long)p * RC + e) * NL]; };
   real *scr = reinterpret_cast<real *>(a.scr) + (long long)side * ((long long)n * ROW + NV * NV) * NL + line;
   auto slot = [&](int p, int e) -> real & { return scr[((long long)p * ROW + e) * NL]; };
   auto wslot = [&](int e) -> real & { return scr[((long long)n * ROW + e) * NL]; };
@@ -309,18 +326,31 @@ __global__ void __launch_bounds__(32) char_solve_kernel(const CharArgs a) {
   grid_vars<NV>(a, gv);
   auto cidx = [&](int p) { return side == 0 ? p : n - 1 - p; };
 
-  // the row data (Roe scalars, coefficients), loaded one position ahead
-  real co[RC], con[RC];
+  // ring of PD positions: [slot][entry][thread], conflict-free
+  constexpr int PD = sizeof(real) == 4 ? 8 : 4;
+  constexpr int RING = RC > ROW ? RC : ROW;
+  __shared__ real ring[PD][RING][32];
+  const int tid = threadIdx.x;
+  auto issue_row = [&](int p) {
 #pragma unroll
-  for (int e = 0; e < RC; ++e) co[e] = rowv(0, e);
+    for (int e = 0; e < RC; ++e)
+      cp_async<sizeof(real)>(&ring[p % PD][e][tid], &rows[((long long)p * RC + e) * NL]);
+  };
+#pragma unroll 1
+  for (int j = 0; j < PD - 1; ++j) {
+    if (j < n) issue_row(j);
+    cp_async_commit();
+  }
 
+  real co[RC];
   real Yp[NV][NV], gp[NV][NC];   // the previous position's multipliers
 #pragma unroll 1
   for (int p = 0; p < n; ++p) {
-    if (p + 1 < n) {
+    if (p + PD - 1 < n) issue_row(p + PD - 1);
+    cp_async_commit();
+    cp_async_wait<PD - 1>();   // the group of position p has landed
 #pragma unroll
-      for (int e = 0; e < RC; ++e) con[e] = rowv(p + 1, e);
-    }
+    for (int e = 0; e < RC; ++e) co[e] = ring[p % PD][e][tid];
     real L[NV][NV];
     {
       const real rs[4] = {co[0], co[1], co[2], co[3]};
@@ -429,33 +459,37 @@ __global__ void __launch_bounds__(32) char_solve_kernel(const CharArgs a) {
         slot(p, NV * NV + k * NC + c) = X[k][NV + c];
       }
     }
-#pragma unroll
-    for (int e = 0; e < RC; ++e) co[e] = con[e];
   }
+  cp_async_wait<0>();
 
-  // back substitution x_p = g_p - Y_p x_{p+1}, the next position's
-  // multipliers loaded one position ahead
+  // back substitution x_p = g_p - Y_p x_{p+1}; step b = n-2-p reads the
+  // multipliers of position p through the same ring
   real *out = reinterpret_cast<real *>(side == 0 ? a.Um : a.Up);
   real x[NV][NC];
 #pragma unroll
   for (int k = 0; k < NV; ++k)
 #pragma unroll
     for (int c = 0; c < NC; ++c) x[k][c] = gp[k][c];
-  real Yn[ROW];
-  if (n >= 2) {
+  auto issue_mult = [&](int b) {
+    const int p = n - 2 - b;
 #pragma unroll
-    for (int e = 0; e < ROW; ++e) Yn[e] = slot(n - 2, e);
+    for (int e = 0; e < ROW; ++e) cp_async<sizeof(real)>(&ring[b % PD][e][tid], &slot(p, e));
+  };
+#pragma unroll 1
+  for (int j = 0; j < PD - 1; ++j) {
+    if (j < n - 1) issue_mult(j);
+    cp_async_commit();
   }
 #pragma unroll 1
   for (int p = n - 1; p >= 0; --p) {
     if (p < n - 1) {
+      const int b = n - 2 - p;
+      if (b + PD - 1 < n - 1) issue_mult(b + PD - 1);
+      cp_async_commit();
+      cp_async_wait<PD - 1>();
       real Yc[ROW];
 #pragma unroll
-      for (int e = 0; e < ROW; ++e) Yc[e] = Yn[e];
-      if (p > 0) {
-#pragma unroll
-        for (int e = 0; e < ROW; ++e) Yn[e] = slot(p - 1, e);
-      }
+      for (int e = 0; e < ROW; ++e) Yc[e] = ring[b % PD][e][tid];
       real xn[NV][NC];
 #pragma unroll
       for (int k = 0; k < NV; ++k)
@@ -482,6 +516,7 @@ __global__ void __launch_bounds__(32) char_solve_kernel(const CharArgs a) {
       for (int k = 0; k < NV; ++k) dst[gv[k] * a.ncell] = x[k][0];
     }
   }
+  cp_async_wait<0>();
   if constexpr (PER) {
     // S = I + Z_0 + G^{-1} A_0 Z_{n-1}, t = y_0 + G^{-1} A_0 y_{n-1};
     // x_p = y_p - Z_p S^{-1} t
