@@ -326,8 +326,9 @@ __global__ void __launch_bounds__(32) char_solve_kernel(const CharArgs a) {
   grid_vars<NV>(a, gv);
   auto cidx = [&](int p) { return side == 0 ? p : n - 1 - p; };
 
-  // ring of PD positions: [slot][entry][thread], conflict-free
-  constexpr int PD = sizeof(real) == 4 ? 8 : 4;
+  // ring of PD positions: [slot][entry][thread], conflict-free; as deep as
+  // the 48 KB of static shared memory allows (periodic rows are longer)
+  constexpr int PD = sizeof(real) == 4 ? (PER ? 8 : 16) : 4;
   constexpr int RING = RC > ROW ? RC : ROW;
   __shared__ real ring[PD][RING][32];
   const int tid = threadIdx.x;
