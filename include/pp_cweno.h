@@ -192,8 +192,9 @@ int pp_cweno_launches_per_step(pp_cweno_t h, int64_t *n);
 
 /* Measurement: enqueue one step launch by launch with CUDA events on the
  * handle's stream between kernels, synchronise and return each kernel's
- * duration in ms (ms[0] the dt kernel, then the sweeps in launch order) in
- * ms[0..*nk-1] (at most nmax entries). */
+ * duration in ms (ms[0] the dt kernel, then the sweeps in launch order; a
+ * characteristic-wise handle's sweep is preceded by its rows and block-solve
+ * kernels, each timed on its own) in ms[0..*nk-1] (at most nmax entries). */
 int pp_cweno_profile_step(pp_cweno_t h, float *ms, int nmax, int *nk);
 
 /* Measurement: sustained fused multiply-add throughput of this GPU's CUDA
