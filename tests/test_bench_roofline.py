@@ -1,0 +1,58 @@
+"""Host logic of bench.py's roofline object (no GPU): the dominant kernel is
+the one with the largest share of the profiled step; achieved = algorithmic
+work per launch / mean launch time; frac = achieved / peak; the DRAM traffic
+figure is reported only while the kernel sources match the revision it was
+captured on."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _profile(ms_per_kernel, steps=2):
+    # [steps, launches]: the dt kernel, then three stages of the kernels
+    row = [0.01] + list(ms_per_kernel) * 3
+    return {"prof": [row for _ in range(steps)]}
+
+
+def test_mixed_dominant_sweep_and_alu_fraction():
+    ncell = 4096 * 4096
+    r = _profile([1.5, 1.4, 0.36])             # x sweep, transposed y sweep, combine
+    out = bench._roofline(r, 1, ncell, 6777.0, "measured")
+    assert out["kernel"] == "x_sweep" and out["bound"] == "alu"
+    tf = 787.0 * ncell / 1.5e-3 / 1e12
+    assert out["achieved"] == pytest.approx(tf, rel=1e-3)
+    assert out["frac"] == pytest.approx(tf / bench.ALU_PEAK_TFLOPS[1], rel=1e-3)
+    comb = out["kernels"]["stage_combine"]
+    assert comb["bound"] == "hbm"
+    gbs = bench.KERNEL_BYTES[1][2][1] * ncell / 0.36e-3 / 1e9
+    assert comb["hbm_gbs"] == pytest.approx(gbs, rel=1e-3)
+    total = 0.01 + 3 * (1.5 + 1.4 + 0.36)
+    assert out["shares"]["x_sweep"] == pytest.approx(3 * 1.5 / total, abs=1e-3)
+
+
+def test_combine_dominant_is_reported_against_hbm():
+    r = _profile([0.2, 0.2, 1.0])
+    out = bench._roofline(r, 1, 4096 * 4096, 6777.0, "measured")
+    assert out["kernel"] == "stage_combine" and out["bound"] == "hbm" and out["unit"] == "GB/s"
+    assert out["frac"] == pytest.approx(out["achieved"] / 6777.0, abs=1e-4)
+
+
+def test_traffic_only_for_the_captured_sources(monkeypatch):
+    r = _profile([1.5, 1.4, 0.36])
+    ncell = 1000
+    monkeypatch.setattr(bench, "_kernel_src_sha256", lambda: bench.TRAFFIC_SRC_SHA256)
+    out = bench._roofline(r, 1, ncell, 6777.0, "measured")
+    assert out["traffic"] == round(bench.TRAFFIC_PER_CELL[(1, "x_sweep")] * ncell)
+    monkeypatch.setattr(bench, "_kernel_src_sha256", lambda: "0" * 64)
+    assert bench._roofline(r, 1, ncell, 6777.0, "measured")["traffic"] is None
+
+
+def test_committed_traffic_matches_committed_sources():
+    """The traffic constants in bench.py belong to the kernel sources in the
+    tree (a kernel change without a new capture nulls the figure)."""
+    assert bench.TRAFFIC_SRC_SHA256 == bench._kernel_src_sha256()
