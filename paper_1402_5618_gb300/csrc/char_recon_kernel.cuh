@@ -58,9 +58,11 @@ __device__ __forceinline__ void left_from(const real (&rs)[4], real (&L)[NV][NV]
 }
 
 // X <- M^{-1} X for an NV x NV block M and NCOL columns: Gaussian
-// elimination with partial pivoting, all indices fixed at compile time
+// elimination with partial pivoting, all indices fixed at compile time; the
+// pivots' reciprocals serve both passes (row c is final once column c is done)
 template <typename real, int NV, int NCOL>
 __device__ __forceinline__ void gauss_solve(real (&M)[NV][NV], real (&X)[NV][NCOL]) {
+  real inv[NV];
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
     real best = fabs(M[c][c]);
@@ -86,10 +88,10 @@ __device__ __forceinline__ void gauss_solve(real (&M)[NV][NV], real (&X)[NV][NCO
         X[r][j] = sw ? t : X[r][j];
       }
     }
-    const real inv = real(1) / M[c][c];
+    inv[c] = real(1) / M[c][c];
 #pragma unroll
     for (int r = c + 1; r < NV; ++r) {
-      const real f = M[r][c] * inv;
+      const real f = M[r][c] * inv[c];
 #pragma unroll
       for (int j = c + 1; j < NV; ++j) M[r][j] -= f * M[c][j];
 #pragma unroll
@@ -98,13 +100,12 @@ __device__ __forceinline__ void gauss_solve(real (&M)[NV][NV], real (&X)[NV][NCO
   }
 #pragma unroll
   for (int c = NV - 1; c >= 0; --c) {
-    const real inv = real(1) / M[c][c];
 #pragma unroll
     for (int j = 0; j < NCOL; ++j) {
       real s = X[c][j];
 #pragma unroll
       for (int q = c + 1; q < NV; ++q) s -= M[c][q] * X[q][j];
-      X[c][j] = s * inv;
+      X[c][j] = s * inv[c];
     }
   }
 }
