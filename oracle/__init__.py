@@ -34,13 +34,13 @@ class Grid(C.Structure):
         ("dx", C.c_double), ("dy", C.c_double), ("gamma", C.c_double),
         ("bc", C.c_int * 4), ("gl_weight", C.c_double), ("eps_weno", C.c_double),
         ("eps_pos", C.c_double), ("limiter", C.c_int), ("linear_weights", C.c_int),
-        ("flux", C.c_int), ("recon", C.c_int),
+        ("flux", C.c_int), ("recon", C.c_int), ("face_cfl", C.c_double),
     ]
 
 
 class Counters(C.Structure):
     _fields_ = [("theta1_active", C.c_long), ("theta2_active", C.c_long),
-                ("bad_cells", C.c_long)]
+                ("bad_cells", C.c_long), ("face_rate", C.c_double), ("rejected", C.c_long)]
 
 
 def build(force: bool = False) -> str:
@@ -119,7 +119,10 @@ def _f64(x) -> np.ndarray:
 def make_grid(ndim: int, nx: int, ny: int = 1, dx: float = 1.0, dy: float = 1.0,
               gamma: float = 1.4, bc=(0, 0, 0, 0), gl_weight: float = 1.0 / 12.0,
               eps_weno: float = 1e-13, eps_pos: float = 1e-13, limiter: bool = True,
-              linear_weights: bool = False, flux: int = 0, recon: int = 0) -> Grid:
+              linear_weights: bool = False, flux: int = 0, recon: int = 0,
+              face_cfl: float = 0.0) -> Grid:
+    """face_cfl > 0: check eq. (CFL-CD) on the limited face values of every
+    stage (bound omega_hat_1) and redo a failing step with a smaller dt."""
     g = Grid()
     g.ndim, g.nx, g.ny = ndim, nx, (ny if ndim == 2 else 1)
     g.dx, g.dy, g.gamma = dx, dy, gamma
@@ -129,6 +132,7 @@ def make_grid(ndim: int, nx: int, ny: int = 1, dx: float = 1.0, dy: float = 1.0,
     g.limiter, g.linear_weights = int(limiter), int(linear_weights)
     g.flux = int(flux)
     g.recon = int(recon)
+    g.face_cfl = float(face_cfl)
     return g
 
 

@@ -744,7 +744,8 @@ static void boundary_state(int nv, int bc, const double *in, double *out) {
 
 /* line[v*n + j] in, Lout[v*n + j] += -(F_{j+1/2} - F_{j-1/2})/h */
 static int line_operator(const orc_grid *g, int nv, long n, const double *line, int bclo,
-                         int bchi, double h, double eps, double *Lout, orc_counters *cnt) {
+                         int bchi, double h, double eps, double *Lout, orc_counters *cnt,
+                         double *smax) {
   long s = n + 4;
   int periodic = (bclo == ORC_BC_PERIODIC);
   double *ext = (double *)malloc(sizeof(double) * (size_t)(nv * s));
@@ -778,6 +779,24 @@ static int line_operator(const orc_grid *g, int nv, long n, const double *line, 
       if (cnt) { if (f & 1) cnt->theta1_active++; if (f & 2) cnt->theta2_active++; }
       for (int v = 0; v < nv; ++v) { um[v * n + j] = a[v]; up[v * n + j] = b[v]; }
     }
+  }
+  if (rc == 0 && smax) {
+    /* the largest |u| + a over the face values the fluxes use (the states
+     * of the first-order steps in the proof of the theorem of Sec. 2.4;
+     * boundary exteriors repeat an interior face's speed) */
+    double s = 0.0;
+    for (long j = 0; j < n; ++j) {
+      for (int side = 0; side < 2; ++side) {
+        const double *w = side ? up : um;
+        double W[4];
+        for (int v = 0; v < nv; ++v) W[v] = w[v * n + j];
+        double p = pressure(nv, g->gamma, W);
+        double a = sqrt(fmax(g->gamma * p / W[0], 0.0));
+        double sp = fabs(W[1] / W[0]) + a;
+        if (!(sp <= s)) s = sp;   /* a NaN speed propagates */
+      }
+    }
+    *smax = s;
   }
   if (rc == 0) {
     /* faces f = 0..n: face f lies between cells f-1 and f */
@@ -816,16 +835,22 @@ int orc_operator(const orc_grid *g, const double *U, double *L, double eps, orc_
   memset(L, 0, sizeof(double) * (size_t)(nv * ncell));
   int rc = 0;
   long t1 = 0, t2 = 0;
+  double sx = 0.0, sy = 0.0;   /* max |u| + a over the x / y face values */
+  int snan = 0;
 
   /* x sweep: one line per row; normal momentum is m_x */
-#pragma omp parallel for schedule(dynamic, 4) reduction(min : rc) reduction(+ : t1, t2)
+#pragma omp parallel for schedule(dynamic, 4) reduction(min : rc) reduction(+ : t1, t2) \
+    reduction(max : sx) reduction(| : snan)
   for (long jy = 0; jy < ny; ++jy) {
     double *line = (double *)malloc(sizeof(double) * (size_t)(nv * nx));
     double *Lo = (double *)calloc((size_t)(nv * nx), sizeof(double));
-    orc_counters c = {0, 0, 0};
+    orc_counters c = {0, 0, 0, 0.0, 0};
     for (int v = 0; v < nv; ++v)
       for (long i = 0; i < nx; ++i) line[v * nx + i] = U[v * ncell + jy * nx + i];
-    int r = line_operator(g, nv, nx, line, g->bc[0], g->bc[1], g->dx, eps, Lo, &c);
+    double sl = 0.0;
+    int r = line_operator(g, nv, nx, line, g->bc[0], g->bc[1], g->dx, eps, Lo, &c, &sl);
+    if (sl > sx) sx = sl;
+    if (sl != sl) snan = 1;
     for (int v = 0; v < nv; ++v)
       for (long i = 0; i < nx; ++i) L[v * ncell + jy * nx + i] += Lo[v * nx + i];
     if (r < rc) rc = r;
@@ -834,15 +859,19 @@ int orc_operator(const orc_grid *g, const double *U, double *L, double eps, orc_
   }
   if (g->ndim == 2) {
     /* y sweep: one line per column; line variables (rho, m_y, m_x, E) */
-#pragma omp parallel for schedule(dynamic, 4) reduction(min : rc) reduction(+ : t1, t2)
+#pragma omp parallel for schedule(dynamic, 4) reduction(min : rc) reduction(+ : t1, t2) \
+    reduction(max : sy) reduction(| : snan)
     for (long ix = 0; ix < nx; ++ix) {
       double *line = (double *)malloc(sizeof(double) * (size_t)(nv * ny));
       double *Lo = (double *)calloc((size_t)(nv * ny), sizeof(double));
-      orc_counters c = {0, 0, 0};
+      orc_counters c = {0, 0, 0, 0.0, 0};
       const int map[4] = {0, 2, 1, 3};  /* line var -> grid var */
       for (int v = 0; v < nv; ++v)
         for (long jy = 0; jy < ny; ++jy) line[v * ny + jy] = U[map[v] * ncell + jy * nx + ix];
-      int r = line_operator(g, nv, ny, line, g->bc[2], g->bc[3], g->dy, eps, Lo, &c);
+      double sl = 0.0;
+      int r = line_operator(g, nv, ny, line, g->bc[2], g->bc[3], g->dy, eps, Lo, &c, &sl);
+      if (sl > sy) sy = sl;
+      if (sl != sl) snan = 1;
       for (int v = 0; v < nv; ++v)
         for (long jy = 0; jy < ny; ++jy) L[map[v] * ncell + jy * nx + ix] += Lo[v * ny + jy];
       if (r < rc) rc = r;
@@ -850,7 +879,13 @@ int orc_operator(const orc_grid *g, const double *U, double *L, double eps, orc_
       free(line); free(Lo);
     }
   }
-  if (cnt) { cnt->theta1_active += t1; cnt->theta2_active += t2; }
+  if (cnt) {
+    cnt->theta1_active += t1;
+    cnt->theta2_active += t2;
+    /* the rate of the face values: sum over directions, as dt in 2-D */
+    double fr = snan ? NAN : sx / g->dx + (g->ndim == 2 ? sy / g->dy : 0.0);
+    if (!(fr <= cnt->face_rate)) cnt->face_rate = fr;
+  }
   return rc;
 }
 
@@ -874,8 +909,8 @@ int orc_operator_lines(const orc_grid *g, const double *U, double eps, long nr, 
     for (int v = 0; v < nv; ++v)
       for (long i = 0; i < n; ++i)
         line[v * n + i] = is_row ? U[map[v] * ncell + idx * nx + i] : U[map[v] * ncell + i * nx + idx];
-    int r = is_row ? line_operator(g, nv, n, line, g->bc[0], g->bc[1], g->dx, eps, Lo, 0)
-                   : line_operator(g, nv, n, line, g->bc[2], g->bc[3], g->dy, eps, Lo, 0);
+    int r = is_row ? line_operator(g, nv, n, line, g->bc[0], g->bc[1], g->dx, eps, Lo, 0, 0)
+                   : line_operator(g, nv, n, line, g->bc[2], g->bc[3], g->dy, eps, Lo, 0, 0);
     double *out = is_row ? Lx_rows + q * nv * nx : Ly_cols + (q - nr) * nv * ny;
     for (int v = 0; v < nv; ++v)
       for (long i = 0; i < n; ++i) out[map[v] * n + i] = Lo[v * n + i];
@@ -946,22 +981,53 @@ int orc_rk3_step(const orc_grid *g, double *U, double dt, orc_counters *cnt) {
 int orc_advance(const orc_grid *g, double *U, double cfl, double t0, double t_final,
                 long max_steps, double *t_out, long *steps_out, double *dt_last,
                 orc_counters *cnt) {
+  long ncell = g->nx * (g->ndim == 2 ? g->ny : 1);
+  long nval = (g->ndim == 2 ? 4 : 3) * ncell;
+  double *Un = g->face_cfl > 0.0 ? (double *)malloc(sizeof(double) * (size_t)nval) : NULL;
+  if (g->face_cfl > 0.0 && !Un) return -1;
   double t = t0;
   long steps = 0;
   int rc = 0;
   double dt = 0.0;
+  double frate_prev = 0.0;   /* face rate of the last accepted step */
+  if (g->face_cfl > 0.0) cfl = fmin(cfl, g->face_cfl);
   while (t < t_final) {
     if (steps >= max_steps) { rc = -2; break; }
     double rate = orc_max_rate(g, U);
     if (!(rate > 0.0)) { rc = -1; break; }
-    dt = cfl / rate;
-    int last = 0;
-    double rem = t_final - t;
-    if (dt >= rem) { dt = rem; last = 1; }
-    if (orc_rk3_step(g, U, dt, cnt) != 0) { rc = -1; break; }
+    /* eq. (CFL-CD) on the states the scheme's first-order steps use: with
+     * the check on, the rate also covers the limited face values of the
+     * last accepted step, and a step whose own face values exceed the bound
+     * is redone from U^n with the time step their rate allows */
+    double r_dt = g->face_cfl > 0.0 ? fmax(rate, frate_prev) : rate;
+    int last = 0, tries = 0;
+    if (Un) memcpy(Un, U, sizeof(double) * (size_t)nval);
+    for (;;) {
+      dt = cfl / r_dt;
+      double rem = t_final - t;
+      last = 0;
+      if (dt >= rem) { dt = rem; last = 1; }
+      orc_counters c = {0, 0, 0, 0.0, 0};
+      if (orc_rk3_step(g, U, dt, &c) != 0) { rc = -1; break; }
+      if (cnt) { cnt->theta1_active += c.theta1_active; cnt->theta2_active += c.theta2_active; }
+      if (!(g->face_cfl > 0.0) || dt * c.face_rate <= g->face_cfl) {
+        frate_prev = c.face_rate;
+        if (cnt && !(c.face_rate <= cnt->face_rate)) cnt->face_rate = c.face_rate;
+        break;
+      }
+      /* rejected: back to U^n; the observed rate exceeds face_cfl / dt >=
+       * cfl / dt, so the next dt is strictly smaller */
+      memcpy(U, Un, sizeof(double) * (size_t)nval);
+      if (cnt) cnt->rejected++;
+      if (++tries > 60) { rc = -1; break; }
+      /* a stage that left G has no finite face rate: halve dt instead */
+      r_dt = c.face_rate < INFINITY ? c.face_rate : 2.0 * cfl / dt;
+    }
+    if (rc) break;
     ++steps;
     t = last ? t_final : t + dt;
   }
+  free(Un);
   if (t_out) *t_out = t;
   if (steps_out) *steps_out = steps;
   if (dt_last) *dt_last = dt;

@@ -34,12 +34,18 @@ typedef struct {
   int    linear_weights; /* 1: force omega_k = c_k (linear compact scheme, tests) */
   int    flux;           /* 0: HLLC (Sec. 2.4); 1: local Lax-Friedrichs (Sec. 3 remark) */
   int    recon;          /* 0: component-wise (conserved variables); 1: characteristic-wise (Sec. 2.3) */
+  double face_cfl;       /* > 0: the bound omega_hat_1 of eq. (CFL-CD) checked on the limited face
+                            values of every stage; orc_advance redoes a step that exceeds it
+                            (0: no check, dt from the cell averages only) */
 } orc_grid;
 
 typedef struct {
   long theta1_active;    /* cells with theta_1 < 1 (density limited) */
   long theta2_active;    /* cells with theta_2 < 1 (internal energy limited) */
   long bad_cells;        /* cells whose average left the admissible set G */
+  double face_rate;      /* max over the operator calls of sum over directions of
+                            max (|u|+a)/h over the limited face values U^-, U^+ */
+  long rejected;         /* orc_advance: steps redone with a smaller dt (face_cfl check) */
 } orc_counters;
 
 /* ---- scalar building blocks (Sec. 2.2) ---- */
@@ -126,6 +132,10 @@ double orc_min_rho(const orc_grid *g, const double *U);
 /* One SSP-RK3 step, eq. (RK3), limiter at every stage.  Returns 0 or -1. */
 int orc_rk3_step(const orc_grid *g, double *U, double dt, orc_counters *cnt);
 /* March from t0 to t_final with dt = cfl / max rate at each step start.
+ * With g->face_cfl > 0 the cfl is capped at face_cfl, the rate is max(rate
+ * of the cell averages, face rate of the last accepted step), and a step
+ * whose stages' face rate r gives
+ * dt r > face_cfl is redone from U^n with dt = cfl / r (Zhang-Shu restart).
  * Returns 0, -1 on a failed stage, -2 if max_steps was reached. */
 int orc_advance(const orc_grid *g, double *U, double cfl, double t0, double t_final,
                 long max_steps, double *t_out, long *steps_out, double *dt_last,

@@ -128,6 +128,20 @@ def riemann_batch(nprob: int = 4096, n_lo: int = 256, n_hi: int = 8192, stream: 
     return out
 
 
+def opens_vacuum(q: Problem) -> bool:
+    """True when the 1-D Riemann data of q generate a vacuum in the exact
+    solution: u_R - u_L >= 2 (a_L + a_R) / (gamma - 1) between the end states."""
+    g = q.gamma
+    ends = []
+    for c in (0, q.nx - 1):
+        rho, m, E = q.U0[:, c]
+        u = m / rho
+        pr = (g - 1.0) * (E - 0.5 * rho * u * u)
+        ends.append((u, np.sqrt(g * pr / rho)))
+    (ul, al), (ur, ar) = ends
+    return bool(ur - ul >= 2.0 * (al + ar) / (g - 1.0))
+
+
 # paper Sec. 3 examples used as Riemann instances (domain, jump, t_final, BC)
 PAPER_RIEMANN = {
     "lax": dict(WL=(0.445, 0.698, 3.528), WR=(0.5, 0.0, 0.571), x0=-5.0, x1=5.0, xd=0.0, t=1.4),
