@@ -104,7 +104,16 @@ typedef struct {
                               form adds 4096 (u max|ubar|)^2 over each 5-cell stencil
                               (u = 2^-24), the FP32 rounding floor of the indicators */
   double eps_pos;          /* cap of the limiter epsilon, Sec. 2.4 step 1 (1e-13) */
-  int cfl_positivity_cap;  /* 1: use min(cfl, gl_weight), the bound of eq. (CFL-CD) */
+  int cfl_positivity_cap;  /* 1: enforce eq. (CFL-CD) of the theorem of Sec. 2.4 on the states
+                              its first-order steps act on, the limited face values:
+                              dt = min(cfl, gl_weight / 2) / max(rate of the cell averages,
+                              face rate of the last accepted step), and a step whose stages'
+                              face values have dt max((|u|+a)/dx [+ (|v|+a)/dy]) > gl_weight
+                              is redone from U^n with dt = min(cfl, gl_weight / 2) / that
+                              rate (half its dt if a stage had no finite rate); the
+                              factor 1/2 is the first-order positivity CFL that brute
+                              force supports (the Sec. 2.4 remark states 1).  Batches:
+                              the same value for every problem */
   int limiter;             /* 1: Zhang-Shu limiter on (default); 0: off */
   int flux;                /* pp_flux_t: face flux (PP_FLUX_HLLC default) */
   int recon;               /* pp_recon_t: reconstructed variables (PP_RECON_COMPONENT default) */
@@ -121,6 +130,7 @@ typedef struct {
   double last_dt;          /* last time step */
   double max_rate;         /* max (|u|+a)/dx (+(|v|+a)/dy) at the current state */
   double min_rho;          /* min density average at the current state */
+  int64_t rejected;        /* checked steps redone with a smaller dt (cfl_positivity_cap) */
 } pp_cweno_stats_t;
 
 /* Fill *cfg with the defaults above (1-D, periodic, FP64, gamma 1.4, cfl 0.5). */
@@ -147,7 +157,9 @@ int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0);
 int pp_cweno_get_state(pp_cweno_t h, double *U, int on_device, double *t, int64_t *steps);
 
 /* One SSP-RK3 step with dt = min(cfl-limited dt, dt_max); *dt_taken may be
- * NULL.  Synchronises.  Batch handles: every problem takes one step. */
+ * NULL.  Synchronises.  Batch handles: every problem takes one step.  With
+ * cfl_positivity_cap a step that fails the face check is redone (up to 64
+ * attempts) until it is accepted. */
 int pp_cweno_step(pp_cweno_t h, double dt_max, double *dt_taken);
 
 /* March every problem until its t reaches t_final (the last step is cut to
@@ -159,7 +171,8 @@ int pp_cweno_advance(pp_cweno_t h, double t_final, int64_t max_steps, int64_t *s
 
 /* Enqueue exactly nsteps steps on the handle's stream with no host
  * synchronisation and no stopping time (for timing); errors are reported by
- * the next synchronising call. */
+ * the next synchronising call.  With cfl_positivity_cap a rejected step is
+ * one of the nsteps (stats.rejected counts them). */
 int pp_cweno_enqueue_steps(pp_cweno_t h, int64_t nsteps);
 
 /* Evaluate the spatial operator once: L = L(U) (eq. (1DEulerFV-b); in 2-D
@@ -213,7 +226,10 @@ int pp_cweno_fma_peak(int fp64, double *gflops);
  * computes it, with the same kernels; cfg describes the grid as for
  * pp_cweno_create and must select PP_PREC_FP64.  eps > 0 is the limiter
  * epsilon; eps <= 0 takes min(eps_pos, min rho) on the device, and then a
- * state with a cell outside G leaves L unwritten.
+ * state with a cell outside G is not evaluated: the call still returns
+ * PP_OK (it does not synchronise) and L is filled with NaN.  A pending
+ * CUDA error left by the caller's own work is not cleared; the call then
+ * returns PP_ERR_CUDA without launching anything.
  *
  * Scratch: the x-sweep flux difference and a control block live in one
  * fixed 32 MiB device array inside the library (every GPU that loads the

@@ -793,7 +793,7 @@ static int line_operator(const orc_grid *g, int nv, long n, const double *line, 
         double p = pressure(nv, g->gamma, W);
         double a = sqrt(fmax(g->gamma * p / W[0], 0.0));
         double sp = fabs(W[1] / W[0]) + a;
-        if (!(sp <= s)) s = sp;   /* a NaN speed propagates */
+        if (sp > s || sp != sp) s = sp;   /* a NaN speed stays */
       }
     }
     *smax = s;
@@ -884,7 +884,7 @@ int orc_operator(const orc_grid *g, const double *U, double *L, double eps, orc_
     cnt->theta2_active += t2;
     /* the rate of the face values: sum over directions, as dt in 2-D */
     double fr = snan ? NAN : sx / g->dx + (g->ndim == 2 ? sy / g->dy : 0.0);
-    if (!(fr <= cnt->face_rate)) cnt->face_rate = fr;
+    if (fr > cnt->face_rate || fr != fr) cnt->face_rate = fr;
   }
   return rc;
 }
@@ -1012,7 +1012,7 @@ int orc_advance(const orc_grid *g, double *U, double cfl, double t0, double t_fi
       if (cnt) { cnt->theta1_active += c.theta1_active; cnt->theta2_active += c.theta2_active; }
       if (!(g->face_cfl > 0.0) || dt * c.face_rate <= g->face_cfl) {
         frate_prev = c.face_rate;
-        if (cnt && !(c.face_rate <= cnt->face_rate)) cnt->face_rate = c.face_rate;
+        if (cnt && (c.face_rate > cnt->face_rate || c.face_rate != c.face_rate)) cnt->face_rate = c.face_rate;
         break;
       }
       /* rejected: back to U^n; the observed rate exceeds face_cfl / dt >=

@@ -38,7 +38,7 @@ class Stats(C.Structure):
         ("steps", C.c_int64), ("stages", C.c_int64), ("theta1_active", C.c_int64),
         ("theta2_active", C.c_int64), ("violations", C.c_int64), ("first_bad_cell", C.c_int64),
         ("t", C.c_double), ("last_dt", C.c_double), ("max_rate", C.c_double),
-        ("min_rho", C.c_double),
+        ("min_rho", C.c_double), ("rejected", C.c_int64),
     ]
 
 

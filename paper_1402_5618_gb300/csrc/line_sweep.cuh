@@ -60,6 +60,17 @@ struct Ctl {
   unsigned long long theta1, theta2;   // limiter activations
   double last_dt;
   double eps_pos;
+  // eq. (CFL-CD) on the limited face values (face_cfl > 0): the largest
+  // (|u| + a)/h over the face values of this step's stages per direction
+  // (double bits; NaN propagates), the rate of the last accepted step, and
+  // what a step that is redone restores
+  unsigned long long frate[2];
+  double face_cfl;
+  double frate_prev;
+  double t_prev;
+  unsigned long long rate_n, minrho_n;
+  long long nreject;
+  int nrej_run;
 };
 
 enum { MODE_XSWEEP = 0, MODE_FINAL = 1, MODE_OPERATOR = 2 };
@@ -103,6 +114,8 @@ struct SweepArgs {
   double eps_fixed;   // > 0: fixed limiter epsilon, no control-block checks (operator evaluation)
   int limiter;
   int flux;           // 0 HLLC, 1 local Lax-Friedrichs
+  int fcheck;         // 1: reduce the face speeds into ctl->frate[fdir]
+  int fdir;           // 0: x faces, 1: y faces
   // face values U^-, U^+ computed by another kernel (planes of the line's
   // arithmetic in the state's layout); nullptr: the kernel reconstructs them
   const void *Fm_pre, *Fp_pre;
@@ -1300,7 +1313,9 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   // ---------------------------------------------------------------- flux
   // HLLC (or local Lax-Friedrichs) at face f (between cells f-1 and f): the
   // left state is U^- of cell f-1, the right state U^+ of cell f; the two
-  // segment-end faces read a neighbour CTA's value
+  // segment-end faces read a neighbour CTA's value.  fsmax: the largest
+  // |u| + a over this thread's face states
+  real fsmax = real(0);
   auto face = [&](int f) {
     real Ul[NV], Ur[NV], F[NV];
     const real *srcL = nullptr;
@@ -1336,8 +1351,10 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       for (int kv = 0; kv < NV; ++kv) Ur[kv] = Ul[kv];
       if (args.bchi == 2) Ur[1] = -Ur[1];
     }
-    if (args.flux) llf<real, NV>(Ul, Ur, gam, F);
-    else hllc<real, NV>(Ul, Ur, gam, F);
+    real sf;
+    if (args.flux) llf<real, NV>(Ul, Ur, gam, F, sf);
+    else hllc<real, NV>(Ul, Ur, gam, F, sf);
+    if (sf > fsmax || sf != sf) fsmax = sf;   // a NaN speed stays
 #pragma unroll
     for (int kv = 0; kv < NV; ++kv) Fl[kv * (SEG + 2) + (f - lo)] = F[kv];
   };
@@ -1485,6 +1502,17 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   }
 
   // ---------------------------------------------------------------- reduce
+  // eq. (CFL-CD) checked on the face values: the stage's largest face rate
+  // of this direction (max over the step's stages; NaN wins the bit max)
+  if (MODE != MODE_OPERATOR && args.fcheck && args.eps_fixed <= 0.0) {
+    double fr = double(fsmax) * args.ih;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const double o = __shfl_down_sync(0xffffffffu, fr, d);
+      if (o > fr || o != o) fr = o;
+    }
+    if (lane == 0) atomicMax(&ctl->frate[args.fdir], double_bits(fr));
+  }
   if (MODE == MODE_FINAL) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {

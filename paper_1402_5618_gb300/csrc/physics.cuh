@@ -183,9 +183,11 @@ __device__ __forceinline__ void phys_flux(const real *U, real p, real *F) {
 // HLLC flux (Sec. 2.4, eqs. (HLLC), (contact-v), (star-l), (acoustic ws)).
 // S_M's denominator uses rho_r on the right-state term, S_R is the max of
 // the two estimates and the right star flux uses S_R.  In 2-D the
-// tangential velocity is carried by the contact.
+// tangential velocity is carried by the contact.  smax receives the larger
+// |u| + a of the two face states (the speed eq. (CFL-CD) bounds).
 template <typename real, int NV>
-__device__ __forceinline__ void hllc(const real *Ul, const real *Ur, real gamma, real *F) {
+__device__ __forceinline__ void hllc(const real *Ul, const real *Ur, real gamma, real *F,
+                                     real &smax) {
   real rl = Ul[0], rr = Ur[0];
   real ul = Ul[1] / rl, ur = Ur[1] / rr;
   real vl = NV == 4 ? Ul[2] / rl : real(0), vr = NV == 4 ? Ur[2] / rr : real(0);
@@ -196,6 +198,7 @@ __device__ __forceinline__ void hllc(const real *Ul, const real *Ur, real gamma,
     pr = fmaxf(pr, 0.0f);
   }
   real al = sqrt(gamma * pl / rl), ar = sqrt(gamma * pr / rr);
+  smax = fmax(fabs(ul) + al, fabs(ur) + ar);
   real Hl = (El + pl) / rl, Hr = (Er + pr) / rr;
   real R = sqrt(rr / rl);
   real ut = (ul + ur * R) / (real(1) + R);
@@ -237,9 +240,10 @@ __device__ __forceinline__ void hllc(const real *Ul, const real *Ur, real gamma,
 // Local Lax-Friedrichs flux, the alternative Sec. 3 names for the
 // near-vacuum double rarefaction: the mean of the two physical fluxes minus
 // alpha/2 times the jump, alpha the larger signal speed |u| + a of the two
-// face states
+// face states (also returned in smax, the speed eq. (CFL-CD) bounds)
 template <typename real, int NV>
-__device__ __forceinline__ void llf(const real *Ul, const real *Ur, real gamma, real *F) {
+__device__ __forceinline__ void llf(const real *Ul, const real *Ur, real gamma, real *F,
+                                    real &smax) {
   real pl = pressure<real, NV>(Ul, gamma), pr = pressure<real, NV>(Ur, gamma);
   if constexpr (sizeof(real) == 4) {
     pl = fmaxf(pl, 0.0f);
@@ -247,7 +251,8 @@ __device__ __forceinline__ void llf(const real *Ul, const real *Ur, real gamma, 
   }
   real al = fabs(Ul[1] / Ul[0]) + sqrt(gamma * pl / Ul[0]);
   real ar = fabs(Ur[1] / Ur[0]) + sqrt(gamma * pr / Ur[0]);
-  real ha = real(0.5) * fmax(al, ar);
+  smax = fmax(al, ar);
+  real ha = real(0.5) * smax;
   real Fl[NV], Fr[NV];
   phys_flux<real, NV>(Ul, pl, Fl);
   phys_flux<real, NV>(Ur, pr, Fr);

@@ -50,6 +50,16 @@ __global__ void step_begin_kernel(Ctl *ctls, int nprob) {
   if (ctl->step >= ctl->step_limit) { ctl->err_steps = 1; return; }
   double rate = bitsd(ctl->rate);
   if (!(rate > 0.0) || !isfinite(rate)) { ctl->err_rate = 1; return; }
+  if (ctl->face_cfl > 0.0) {
+    // eq. (CFL-CD) on the face values: the rate also covers the limited face
+    // values of the last accepted step; keep what a redone step restores
+    rate = fmax(rate, ctl->frate_prev);
+    ctl->t_prev = ctl->t;
+    ctl->rate_n = ctl->rate;
+    ctl->minrho_n = ctl->minrho[2];
+    ctl->frate[0] = 0ull;
+    ctl->frate[1] = 0ull;
+  }
   double dt = ctl->cfl / rate;
   dt = fmin(dt, ctl->dt_cap);
   double rem = ctl->t_final - ctl->t;
@@ -67,6 +77,63 @@ __global__ void step_begin_kernel(Ctl *ctls, int nprob) {
   ctl->minrho[1] = inf;
   ctl->minrho[2] = inf;
   ctl->rate = 0ull;
+}
+
+// a step of a checked problem is accepted when its stages' face rate obeys
+// eq. (CFL-CD): dt (rate_x + rate_y) <= omega_hat_1 (NaN fails)
+__device__ __forceinline__ bool step_accepted(const Ctl *ctl) {
+  const double fr = bitsd(ctl->frate[0]) + bitsd(ctl->frate[1]);
+  return ctl->dt * fr <= ctl->face_cfl;
+}
+
+// End of a checked step (after the commit copy): an accepted step keeps its
+// face rate for the next dt; a rejected one is undone (U^n is still in the
+// state buffer) and redone next time with dt = cfl / (its face rate), or
+// half its dt when a stage had no finite face rate (the Zhang-Shu restart).
+__global__ void step_end_kernel(Ctl *ctls, int nprob) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  Ctl *ctl = ctls + p;
+  if (!ctl->active) return;
+  const double fr = bitsd(ctl->frate[0]) + bitsd(ctl->frate[1]);
+  if (step_accepted(ctl)) {
+    ctl->frate_prev = fr;
+    ctl->nrej_run = 0;
+    return;
+  }
+  ctl->t = ctl->t_prev;
+  ctl->step -= 1;
+  ctl->done = 0;
+  ctl->rate = ctl->rate_n;
+  ctl->minrho[2] = ctl->minrho_n;
+  ctl->nviol = 0;            // cells of the discarded stages
+  ctl->first_bad = ~0ull;
+  ctl->nreject += 1;
+  ctl->frate_prev = fr < INFINITY ? fr : 2.0 * ctl->cfl / ctl->dt;
+  if (++ctl->nrej_run > 60) ctl->err_rate = 1;
+}
+
+// Checked steps write U^{n+1} into the stage buffer: copy it over U^n where
+// the step was accepted.  Problem p (blockIdx.y) owns the 32-bit words
+// [a0, a0 + n) and [a1, a1 + n) of both buffers (FP64 values, or the FP32 hi
+// and lo planes of the mixed form).
+__global__ void commit_kernel(const unsigned int *src, unsigned int *dst, const ProbDesc *probs,
+                              long long nvals, int mixed, int nv, const Ctl *ctls) {
+  const int p = blockIdx.y;
+  const Ctl *ctl = ctls + p;
+  if (!ctl->active || !step_accepted(ctl)) return;
+  long long a0 = 0, a1 = nvals, n = nvals;   // single problem: everything
+  if (probs) {
+    const ProbDesc pd = probs[p];
+    n = (long long)nv * pd.ncell;
+    a0 = mixed ? pd.off : 2 * pd.off;
+    a1 = mixed ? nvals + pd.off : 2 * pd.off + n;
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    dst[a0 + i] = src[a0 + i];
+    dst[a1 + i] = src[a1 + i];
+  }
 }
 
 // Reductions of a state: min density, max rate, cells outside G.  The
@@ -184,7 +251,11 @@ __device__ __forceinline__ void transpose_tile(const float *src, float *dst, int
   }
 }
 
-__global__ void transpose_planes_kernel(const float *in, float *out, int nx, int ny, long long ncell) {
+// gate (checked steps): transpose only when the step just taken was
+// rejected, restoring the transposed planes of U^n
+__global__ void transpose_planes_kernel(const float *in, float *out, int nx, int ny, long long ncell,
+                                        const Ctl *gate) {
+  if (gate && (!gate->active || step_accepted(gate))) return;
   const int v = blockIdx.z;
   transpose_tile(in + v * ncell, out + v * ncell, blockIdx.x * TT, blockIdx.y * TT, nx, ny);
 }
@@ -195,8 +266,9 @@ struct TileRef {
 };
 
 __global__ void transpose_planes_b_kernel(const float *in, float *out, const TileRef *tiles,
-                                          const ProbDesc *probs) {
+                                          const ProbDesc *probs, const Ctl *gates) {
   const TileRef t = tiles[blockIdx.x];
+  if (gates && (!gates[t.prob].active || step_accepted(gates + t.prob))) return;
   const ProbDesc pd = probs[t.prob];
   const long long o = pd.off + blockIdx.y * pd.ncell;
   transpose_tile(in + o, out + o, t.i0, t.j0, pd.nx, pd.ny);
@@ -541,6 +613,15 @@ __global__ void noalloc_ctl_arm(Ctl *ctl, double eps_pos, double eps) {
   ctl->active = ctl->nviol == 0 && ctl->eps0 > 0.0;
 }
 
+// a state the operator is not evaluated on (a cell outside G with eps <= 0)
+// gets L = NaN everywhere, so the caller sees it in its own output
+__global__ void noalloc_nan_fill(double *L, long long n, const Ctl *ctl) {
+  if (ctl->active) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    L[i] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
 // a batched launch group: lines of equal cluster size and boundary kind
 struct LineGroup {
   int R;
@@ -571,6 +652,10 @@ struct pp_cweno_s {
   bool ytrans = false;
   float *UT = nullptr, *DT = nullptr;
   bool tuned = false;
+  // eq. (CFL-CD) checked on the face values of every stage (the positivity
+  // cap): stage 3 writes the stage buffer, a commit kernel copies it over
+  // U^n where the step was accepted
+  bool fcheck = false;
   // characteristic-wise reconstruction (single problem): U^- and U^+ planes
   // of the current sweep direction and the block solver's scratch, in the
   // line arithmetic (FP64, or FP32 for the mixed form)
@@ -637,8 +722,12 @@ int check_config(const pp_cweno_config *c) {
   return PP_OK;
 }
 
+// With the positivity cap the time step takes half the bound of eq.
+// (CFL-CD) (the first-order factor 1/2 of the Sec. 2.4 remark that brute
+// force supports), and each step is checked against the full bound on its
+// stages' face values.
 double effective_cfl(const pp_cweno_config &c) {
-  return c.cfl_positivity_cap ? fmin(c.cfl, c.gl_weight) : c.cfl;
+  return c.cfl_positivity_cap ? fmin(c.cfl, 0.5 * c.gl_weight) : c.cfl;
 }
 
 void fill_common(const pp_cweno_s *h, SweepArgs &a, int stage, double eps_fixed, Ctl *ctl) {
@@ -649,6 +738,7 @@ void fill_common(const pp_cweno_s *h, SweepArgs &a, int stage, double eps_fixed,
   a.eps_fixed = eps_fixed;
   a.limiter = h->cfg.limiter;
   a.flux = h->cfg.flux;
+  a.fcheck = h->fcheck ? 1 : 0;
   a.ctl = ctl;
   if (h->cfg.recon == PP_RECON_CHARACTERISTIC) {
     const size_t es = is_mixed(h) ? sizeof(float) : sizeof(double);
@@ -744,10 +834,12 @@ cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const void *Uin, co
     a.bchi = h->cfg.bc[1];
     a.h = h->dx;
     a.h_other = h->nv == 4 ? h->dy : 0.0;
+    a.fdir = 0;
   } else {
     a.n = (int)h->ny;
     a.cell_stride = h->nx;
     a.line_stride = 1;
+    a.fdir = 1;
     nlines = h->nx;
     a.vn = 2;
     a.vt = 1;
@@ -788,6 +880,7 @@ cudaError_t launch_group(const pp_cweno_s *h, const LineGroup &g, int mode, cons
   }
   a.vn = g.xdir ? 1 : 2;
   a.vt = h->nv == 4 ? (g.xdir ? 2 : 1) : -1;
+  a.fdir = g.xdir ? 0 : 1;
   return dispatch(h, mode, g.periodic, a, g.nlines, attrs_only);
 }
 
@@ -809,6 +902,7 @@ cudaError_t launch_ysweep_t(const pp_cweno_s *h, int stage) {
   a.bchi = h->cfg.bc[3];
   a.h = h->dy;
   a.h_other = h->dx;
+  a.fdir = 1;
   a.R = seg_count(a.n);
   cudaError_t e = launch_char(h, a, h->UT, h->nx);   // rows of the transposed planes
   if (e != cudaSuccess) return e;
@@ -844,16 +938,44 @@ cudaError_t launch_combine_b(const pp_cweno_s *h, const void *Uin, void *Uout, i
   return cudaGetLastError();
 }
 
-cudaError_t transpose_state_hi(const pp_cweno_s *h) {
+// transposed hi planes of U^n; gated: only for the problems whose checked
+// step was just rejected
+cudaError_t transpose_state_hi(const pp_cweno_s *h, bool gated = false) {
+  const Ctl *gate = gated ? h->ctl : nullptr;
   if (h->btrans) {
     transpose_planes_b_kernel<<<dim3((unsigned)h->ntiles, (unsigned)h->nv), dim3(TT, 8), 0,
-                                h->stream>>>(hi_of(h->U0), h->UT, h->tiles, h->probs);
+                                h->stream>>>(hi_of(h->U0), h->UT, h->tiles, h->probs, gate);
     return cudaGetLastError();
   }
   dim3 grid((unsigned)((h->nx + TT - 1) / TT), (unsigned)((h->ny + TT - 1) / TT), (unsigned)h->nv);
   transpose_planes_kernel<<<grid, dim3(TT, 8), 0, h->stream>>>(hi_of(h->U0), h->UT, (int)h->nx,
-                                                               (int)h->ny, h->ncell);
+                                                               (int)h->ny, h->ncell, gate);
   return cudaGetLastError();
+}
+
+// end of a checked step: U^{n+1} (in the stage buffer) over U^n where the
+// step was accepted, the transposed planes of U^n back where it was
+// rejected, then the per-problem bookkeeping
+cudaError_t finish_checked_step(pp_cweno_s *h, const std::function<void()> &mark) {
+  const long long per = h->batch ? 0 : nvals(h);
+  long long longest = per;
+  if (h->batch)
+    for (const ProbDesc &d : h->probs_h) longest = std::max(longest, (long long)h->nv * d.ncell);
+  const unsigned bx = (unsigned)std::min<long long>(h->batch ? 64 : 4096, (longest + 255) / 256);
+  commit_kernel<<<dim3(std::max(1u, bx), (unsigned)h->nprob), 256, 0, h->stream>>>(
+      reinterpret_cast<const unsigned int *>(h->U1), reinterpret_cast<unsigned int *>(h->U0),
+      h->batch ? h->probs : nullptr, nvals(h), is_mixed(h) ? 1 : 0, h->nv, h->ctl);
+  cudaError_t e = cudaGetLastError();
+  mark();
+  if (e == cudaSuccess && (h->ytrans || h->btrans)) {
+    e = transpose_state_hi(h, true);
+    mark();
+  }
+  if (e != cudaSuccess) return e;
+  step_end_kernel<<<(h->nprob + 127) / 128, 128, 0, h->stream>>>(h->ctl, h->nprob);
+  e = cudaGetLastError();
+  mark();
+  return e;
 }
 
 // enqueue one step: the per-problem dt kernel, then 3 stages; with ev, an
@@ -871,7 +993,8 @@ cudaError_t enqueue_step_body(pp_cweno_s *h, cudaEvent_t *ev, int *nev) {
   if (e != cudaSuccess) return e;
   for (int s = 0; s < 3; ++s) {
     const void *Uin = s == 0 ? h->U0 : h->U1;
-    void *Uout = s == 2 ? h->U0 : h->U1;
+    // checked steps keep U^n until the step is accepted
+    void *Uout = (s == 2 && !h->fcheck) ? h->U0 : h->U1;
     if (h->ytrans) {
       e = launch(h, MODE_XSWEEP, true, Uin, h->U0, nullptr, h->D, nullptr, s, 0.0, h->ctl);
       mark();
@@ -917,6 +1040,10 @@ cudaError_t enqueue_step_body(pp_cweno_s *h, cudaEvent_t *ev, int *nev) {
       e = launch_group(h, g, MODE_FINAL, Uin, h->U0, h->D, nullptr, Uout, s);
       if (e != cudaSuccess) return e;
     }
+  }
+  if (h->fcheck) {
+    e = finish_checked_step(h, mark);
+    if (e != cudaSuccess) return e;
   }
   if (nev) *nev = k;
   return cudaSuccess;
@@ -1023,6 +1150,7 @@ int finish_create(pp_cweno_s *h) {
   if (e == cudaSuccess) e = cudaMalloc(&h->ctl_scratch, sizeof(Ctl) * h->nprob);
   if (e == cudaSuccess) e = cudaMallocHost(&h->hctl, sizeof(Ctl) * h->nprob);
   h->ytrans = is_mixed(h) && h->nv == 4 && !h->batch;
+  h->fcheck = h->cfg.cfl_positivity_cap != 0;
   const bool tr = h->ytrans || h->btrans;
   if (e == cudaSuccess && tr) e = cudaMalloc(&h->UT, sizeof(float) * (size_t)nvals(h));
   if (e == cudaSuccess && tr) e = cudaMalloc(&h->DT, sizeof(float) * (size_t)nvals(h));
@@ -1065,6 +1193,7 @@ int finish_create(pp_cweno_s *h) {
     const int chars = h->cfg.recon == PP_RECON_CHARACTERISTIC ? 2 * sweeps : 0;
     h->launches_per_step = 1 + 3 * ((h->ytrans ? 3 : sweeps) + chars);
   }
+  if (h->fcheck) h->launches_per_step += 2 + ((h->ytrans || h->btrans) ? 1 : 0);
   return PP_OK;
 }
 
@@ -1196,7 +1325,8 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
     const pp_cweno_config &c = cfgs[p];
     if (c.ndim != c0.ndim || c.gamma != c0.gamma || c.precision != c0.precision ||
         c.gl_weight != c0.gl_weight || c.eps_weno != c0.eps_weno || c.eps_pos != c0.eps_pos ||
-        c.limiter != c0.limiter || c.flux != c0.flux || c.recon != c0.recon)
+        c.limiter != c0.limiter || c.flux != c0.flux || c.recon != c0.recon ||
+        c.cfl_positivity_cap != c0.cfl_positivity_cap)
       return PP_ERR_ARG;
     if (c.recon != PP_RECON_COMPONENT) return PP_ERR_UNSUPPORTED;
   }
@@ -1334,6 +1464,14 @@ int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) 
     c->err_rate = 0;
     c->eps_pos = h->cfg.eps_pos;
     c->theta1 = c->theta2 = 0;
+    c->face_cfl = h->cfgs[p].cfl_positivity_cap ? h->cfgs[p].gl_weight : 0.0;
+    c->frate[0] = c->frate[1] = 0;
+    c->frate_prev = 0.0;
+    c->t_prev = t0;
+    c->rate_n = c->rate;
+    c->minrho_n = c->minrho[2];
+    c->nreject = 0;
+    c->nrej_run = 0;
   }
   if ((rc = push_ctl(h))) return rc;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PP_ERR_CUDA;
@@ -1392,13 +1530,25 @@ int pp_cweno_step(pp_cweno_t h, double dt_max, double *dt_taken) {
     c->err_steps = 0;
   }
   if ((rc = push_ctl(h))) return rc;
-  if (enqueue_step(h) != cudaSuccess) return PP_ERR_CUDA;
-  if ((rc = pull_ctl(h))) return rc;
+  // a checked step that fails eq. (CFL-CD) on its face values is redone
+  // (the step count then stays put) until every problem took its step
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    if (enqueue_step(h) != cudaSuccess) return PP_ERR_CUDA;
+    if ((rc = pull_ctl(h))) return rc;
+    bool all = true;
+    for (int p = 0; p < h->nprob; ++p) {
+      const Ctl *c = h->hctl + p;
+      if (c->nviol || c->err_rate || c->err_steps) continue;
+      if (c->step < c->step_limit) all = false;
+    }
+    if (all || !h->fcheck) break;
+  }
   for (int p = 0; p < h->nprob; ++p) {
     Ctl *c = h->hctl + p;
     c->t_final = c->t;
     c->dt_cap = INFINITY;
     c->done = 1;
+    if (c->step >= c->step_limit) c->err_steps = 0;   // a redo attempt after its step
   }
   if (dt_taken) *dt_taken = h->hctl[0].last_dt;
   if ((rc = push_ctl(h))) return rc;
@@ -1521,6 +1671,7 @@ int pp_cweno_stats(pp_cweno_t h, pp_cweno_stats_t *out) {
     out->theta1_active += (int64_t)c->theta1;
     out->theta2_active += (int64_t)c->theta2;
     out->violations += (int64_t)c->nviol;
+    out->rejected += (int64_t)c->nreject;
     if (c->nviol && out->first_bad_cell < 0)
       out->first_bad_cell = (int64_t)c->first_bad + (h->batch ? h->probs_h[p].off / h->nv : 0);
     out->t = fmax(out->t, c->t);
@@ -1553,6 +1704,7 @@ int pp_cweno_problem_stats(pp_cweno_t h, int64_t k, pp_cweno_stats_t *out) {
   out->theta1_active = (int64_t)c->theta1;
   out->theta2_active = (int64_t)c->theta2;
   out->violations = (int64_t)c->nviol;
+  out->rejected = (int64_t)c->nreject;
   out->first_bad_cell = c->nviol ? (int64_t)c->first_bad : -1;
   out->t = c->t;
   out->last_dt = c->last_dt;
@@ -1671,6 +1823,9 @@ int pp_cweno_operator_noalloc(const pp_cweno_config *cfg, const double *U_dev, d
   if (dbytes > NOALLOC_BYTES - NOALLOC_CTL_BYTES) return PP_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return PP_ERR_CUDA;
+  // an error left pending by the caller's own work is not taken (and not
+  // cleared) as one of this call's launches
+  if (cudaPeekAtLastError() != cudaSuccess) return PP_ERR_CUDA;
 
   // a stack handle that borrows the fixed scratch: nothing is allocated
   pp_cweno_s h;
@@ -1723,6 +1878,7 @@ int pp_cweno_operator_noalloc(const pp_cweno_config *cfg, const double *U_dev, d
           U_dev, nullptr, h.ncell, h.nx, h.dx, h.dy, cfg->gamma, ctl);
   }
   noalloc_ctl_arm<<<1, 32, 0, h.stream>>>(ctl, cfg->eps_pos, eps);
+  noalloc_nan_fill<<<grid_for(nvals(&h)), 256, 0, h.stream>>>(L_dev, nvals(&h), ctl);
   if (cudaGetLastError() != cudaSuccess) return PP_ERR_CUDA;
   cudaError_t e;
   if (nv == 4) {

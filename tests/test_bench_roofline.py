@@ -51,3 +51,17 @@ def test_traffic_only_for_the_captured_sources(monkeypatch):
     monkeypatch.setattr(bench, "_kernel_src_sha256", lambda: "0" * 64)
     assert bench._roofline(r, 1, ncell, 6777.0, "measured")["traffic"] is None
 
+
+
+def test_checked_step_tail_is_kept_out_of_the_stage_kernels():
+    """Checked steps (eq. (CFL-CD) on the face values) end with a commit copy,
+    a transposed-plane restore and the step-end kernel: they get their own
+    entry and leave the per-stage kernel averages unchanged."""
+    ncell = 4096 * 4096
+    row = [0.01] + [1.5, 1.4, 0.36] * 3 + [0.2, 0.001, 0.003]
+    out = bench._roofline({"prof": [row, row]}, 1, ncell, 6777.0, "measured")
+    assert out["kernel"] == "x_sweep" and out["avg_launch_ms"] == pytest.approx(1.5)
+    tail = out["kernels"]["step_end"]
+    assert tail["launches_per_step"] == 3
+    assert tail["avg_ms_per_step"] == pytest.approx(0.204, abs=1e-4)
+    assert tail["share"] == pytest.approx(0.204 / sum(row), abs=1e-3)

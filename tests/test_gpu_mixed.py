@@ -124,8 +124,12 @@ def test_mixed_full_size_blast_4096_one_step(B):
     st = s.stats()
     s.close()
     assert st.violations == 0
-    rate = oracle.max_rate(g, p.U0)
-    assert abs(dt - (1.0 / 12.0) / rate) <= 1e-12 * dt
+    # the positivity cap: dt = (omega_1 / 2) / rate, the step checked against
+    # eq. (CFL-CD) on its face values (the oracle's checked step, same rule)
+    gc = oracle.make_grid(p.ndim, p.nx, p.ny, p.dx, p.dy, p.gamma, p.bc, face_cfl=1.0 / 12.0)
+    _, _, so, dt_o, cnt, _ = oracle.advance(gc, p.U0, 1.0 / 24.0, 1e9, max_steps=1)
+    assert so == 1 and st.rejected == cnt.rejected
+    assert abs(dt - dt_o) <= 1e-12 * dt, (dt, dt_o)
     Uo = oracle.rk3_step(g, p.U0, dt)
     for v in range(4):
         err = np.abs(Ug[v] - Uo[v]).max() / np.abs(Uo[v]).max()

@@ -52,9 +52,9 @@ def _handle_operator(B, p, Ud, eps):
 def test_noalloc_operator_matches_handle_operator_twice(B, name, make, eps):
     p = make()
     Ud = torch.from_numpy(np.ascontiguousarray(p.U0).ravel()).cuda()
-    ref = _handle_operator(B, p, Ud, eps if eps > 0 else min(1e-13, p.U0[0].min()))
-    scale = _scale(p, p.U0)
     cfg = B.config_from_problem(p)
+    ref = _handle_operator(B, p, Ud, eps if eps > 0 else min(cfg.eps_pos, p.U0[0].min()))
+    scale = _scale(p, p.U0)
     for _ in range(2):
         L = torch.full_like(Ud, float("nan"))
         B.operator_noalloc(cfg, Ud, L, eps)
@@ -74,4 +74,33 @@ def test_noalloc_rejects_oversized_and_mixed(B):
     u = torch.zeros(3 * 64, dtype=torch.float64, device="cuda")
     with pytest.raises(B.PPError) as e:
         B.operator_noalloc(mixed, u, u)
+    assert e.value.code == B.PP_ERR_UNSUPPORTED
+
+
+def test_noalloc_state_outside_G_gives_nan(B):
+    """With eps <= 0 the device takes the limiter epsilon from the state; a
+    state with one cell outside G is not evaluated and L comes back NaN
+    (the call itself does not synchronise and returns PP_OK)."""
+    p = W.riemann_1d(300, (1.0, 0.4, 1.0), (0.2, -0.2, 0.1), bc=(2, 1))
+    U = np.ascontiguousarray(p.U0).copy()
+    U[2, 150] = 0.5 * U[1, 150] ** 2 / U[0, 150] * 0.5   # E below the kinetic energy: e < 0
+    Ud = torch.from_numpy(U.ravel()).cuda()
+    L = torch.zeros_like(Ud)
+    B.operator_noalloc(B.config_from_problem(p), Ud, L, 0.0)
+    torch.cuda.synchronize()
+    assert torch.isnan(L).all()
+    # the same call on the admissible state writes finite values again
+    Ud = torch.from_numpy(np.ascontiguousarray(p.U0).ravel()).cuda()
+    B.operator_noalloc(B.config_from_problem(p), Ud, L, 0.0)
+    torch.cuda.synchronize()
+    assert torch.isfinite(L).all()
+
+
+def test_noalloc_rejects_characteristic_form(B):
+    """The characteristic-wise form needs the handle's block-solve scratch:
+    PP_ERR_UNSUPPORTED, with real device buffers."""
+    cfg = B.make_config(ndim=1, nx=64, recon=B.RECON_CHARACTERISTIC)
+    u = torch.zeros(3 * 64, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.PPError) as e:
+        B.operator_noalloc(cfg, u, u)
     assert e.value.code == B.PP_ERR_UNSUPPORTED
