@@ -466,6 +466,14 @@ def main():
     ap.add_argument("--blast-n", type=int, default=512)
     ap.add_argument("--blast-steps", type=int, default=3000)
     ap.add_argument("--vortex-n", type=int, default=1024)
+    ap.add_argument("--vortex-from", type=int, default=128, help="smallest vortex grid of the sweep")
+    ap.add_argument("--vortex-t", type=float, default=1.0,
+                    help="end time of the vortex runs (10: one period, the 2048^2 configuration)")
+    ap.add_argument("--blast-rel-n", type=int, default=0,
+                    help="> 0: also the mixed-vs-FP64 relative L1 of the blast on this grid after "
+                         "--blast-rel-steps steps of each form from the same state")
+    ap.add_argument("--blast-rel-steps", type=int, default=100)
+    ap.add_argument("--skip-blast", action="store_true", help="accuracy study without the blast probe")
     args = ap.parse_args()
     if args.profile_only:
         profile_only(args)
@@ -598,6 +606,52 @@ def accuracy_study(args):
                                            limiter_theta1=int(st.theta1_active),
                                            limiter_theta2=int(st.theta2_active))
 
+    if not args.skip_blast:
+        out["blast"] = _blast_study(args, run)
+    if args.blast_rel_n > 0:
+        out["blast_rel"] = _blast_rel(args)
+    _vortex_study(args, run, out)
+    print(json.dumps(out), flush=True)
+
+
+def _blast_rel(args):
+    """The metric's stated accuracy (i): the mixed form's blast against the
+    FP64 form's after the same number of steps from the same state (each
+    with its own dt), relative L1 per variable, at the positivity CFL with
+    the face check."""
+    import numpy as np
+    import torch
+
+    from paper_1402_5618_gb300 import binding as B
+    from paper_1402_5618_gb300 import workloads as W
+    p = W.blast_2d(args.blast_rel_n)
+    res = {}
+    for prec, name in ((0, "fp64"), (1, "mixed")):
+        s = B.Solver(B.config_from_problem(p, prec, cfl_positivity_cap=True))
+        s.set_state(np.ascontiguousarray(p.U0).ravel())
+        s.enqueue_steps(args.blast_rel_steps)
+        U, t, steps = s.get_state()
+        st = s.stats()
+        s.close()
+        torch.cuda.synchronize()
+        res[name] = (U.reshape(p.U0.shape), float(t), int(steps), int(st.violations), int(st.rejected))
+    U64, U32 = res["fp64"][0], res["mixed"][0]
+    rel = [float(np.abs(U32[v] - U64[v]).sum() / np.abs(U64[v]).sum()) for v in range(4)]
+    out = {"grid": [args.blast_rel_n] * 2, "attempted_steps": args.blast_rel_steps,
+           "fp64": {"t": res["fp64"][1], "steps": res["fp64"][2], "violations": res["fp64"][3],
+                    "redone": res["fp64"][4]},
+           "mixed": {"t": res["mixed"][1], "steps": res["mixed"][2], "violations": res["mixed"][3],
+                     "redone": res["mixed"][4]},
+           "rel_l1_mixed_vs_fp64": rel}
+    print(f"blast_rel: {out}", file=sys.stderr, flush=True)
+    return out
+
+
+def _blast_study(args, run):
+    import numpy as np
+
+    from paper_1402_5618_gb300 import binding as B
+    from paper_1402_5618_gb300 import workloads as W
     n = args.blast_n
     p = W.blast_2d(n)
     h = p.dx
@@ -627,18 +681,25 @@ def accuracy_study(args):
                     rho_min=float(rho.min()))
         res[name] = (U, info)
     r64, r32 = res["fp64"][0][0], res["mixed"][0][0]
-    out["blast"] = {"grid": [n, n], "t_final": p.t_final, "cfl": "1/12 (positivity cap)",
-                    "t_reach_probe": t_reach, "probe_steps": args.blast_steps,
-                    "fp64": res["fp64"][1], "mixed": res["mixed"][1],
-                    "rel_l1_rho_mixed_vs_fp64": float(np.abs(r32 - r64).sum() / np.abs(r64).sum())}
+    return {"grid": [n, n], "t_final": p.t_final,
+            "cfl": "1/24 (positivity cap, face check)",
+            "t_reach_probe": t_reach, "probe_steps": args.blast_steps,
+            "fp64": res["fp64"][1], "mixed": res["mixed"][1],
+            "rel_l1_rho_mixed_vs_fp64": float(np.abs(r32 - r64).sum() / np.abs(r64).sum())}
 
+
+def _vortex_study(args, run, out):
+    import numpy as np
+
+    from paper_1402_5618_gb300 import workloads as W
     # vortex: refinement sweep up to --vortex-n; the FP64 error falls with
     # the scheme's order while the FP32 form levels off at its rounding floor
     sweep = []
-    nv = 128
+    nv = args.vortex_from
+    tv = args.vortex_t
     while nv <= args.vortex_n:
-        pv = W.vortex_2d(nv, t_final=1.0)
-        ex = W.vortex_2d(nv, t=1.0).U0[0]
+        pv = W.vortex_2d(nv, t_final=tv)
+        ex = W.vortex_2d(nv, t=tv).U0[0]
         vres = {"grid": [nv, nv]}
         for prec, name in ((0, "fp64"), (1, "mixed")):
             U, info = run(pv, prec)
@@ -650,9 +711,8 @@ def accuracy_study(args):
         print(f"vortex {nv}^2: {vres}", file=sys.stderr, flush=True)
         sweep.append(vres)
         nv *= 2
-    out["vortex"] = {"t_final": 1.0, "cfl": 0.5, "error": "density vs the translated closed form",
+    out["vortex"] = {"t_final": tv, "cfl": 0.5, "error": "density vs the translated closed form",
                      "sweep": sweep}
-    print(json.dumps(out), flush=True)
 
 
 def run_reference(args, ws):

@@ -101,8 +101,9 @@ typedef struct {
   int precision;           /* pp_prec_t */
   double gl_weight;        /* Gauss-Lobatto end weight omega_hat_1 of the limiter, Sec. 2.4 (1/12) */
   double eps_weno;         /* epsilon of the WENO-Z weights, eq. (weight) (1e-13); the mixed
-                              form adds 4096 (u max|ubar|)^2 over each 5-cell stencil
-                              (u = 2^-24), the FP32 rounding floor of the indicators */
+                              form adds 2^20 (u max|ubar|)^2 over each 5-cell stencil
+                              (u = 2^-24): the indicators' floor of FP32 rounding noise,
+                              including the noise the FP32 stages accumulate in the state */
   double eps_pos;          /* cap of the limiter epsilon, Sec. 2.4 step 1 (1e-13) */
   int cfl_positivity_cap;  /* 1: enforce eq. (CFL-CD) of the theorem of Sec. 2.4 on the states
                               its first-order steps act on, the limited face values:
@@ -195,9 +196,11 @@ int pp_cweno_num_problems(pp_cweno_t h, int64_t *nprob);
 int pp_cweno_problem_cells(pp_cweno_t h, int64_t k, int64_t *ncell);
 
 /* Rows per thread chunk of the line kernels chosen for this handle (8 or
- * 16).  The first set_state of a single-problem handle times one sweep with
- * each choice on the handle's own data and keeps the faster (cached per
- * precision, dimension and grid size); batches use 8. */
+ * 16: the serial Thomas run of a thread against the depth of the parallel
+ * scans).  The first set_state of a handle times one sweep with each choice
+ * on the handle's own data and keeps the faster: single problems over the x
+ * sweep (cached per precision, dimension, grid size and periodicity),
+ * batches over every x-line group of the batch. */
 int pp_cweno_rows_per_chunk(pp_cweno_t h, int *m);
 
 /* Kernel launches enqueued per step (for launch accounting). */

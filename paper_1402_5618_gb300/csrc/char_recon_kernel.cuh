@@ -112,7 +112,7 @@ __device__ __forceinline__ void gauss_solve(real (&M)[NV][NV], real (&X)[NV][NCO
 
 // WENO-Z ratios of one characteristic field over its five-cell stencil v.
 // FP32: the scaled ratios with eps lifted to the rounding floor of the
-// indicators, 4096 (u s)^2 with s = mag, the largest sum_m |l_m| |ubar_m|
+// indicators, FP32_BETA_FLOOR s^2 = 2^20 (u s)^2 with s = mag, the largest sum_m |l_m| |ubar_m|
 // over the stencil: the size of the terms the characteristic variable is
 // summed from, which bounds its rounding error even where the sum cancels
 // (the same floor as the component-wise mixed form, taken on those terms).

@@ -109,6 +109,7 @@ struct SweepArgs {
   int bclo, bchi;
   double h, h_other;  // cell size along the line / across (0 in 1-D)
   double ih;          // 1 / h (from the host: no FP64 division per thread)
+  double ih_other;    // 1 / h_other (0 in 1-D)
   double gamma, wgl, eps_weno;
   int stage;          // 0, 1, 2
   double eps_fixed;   // > 0: fixed limiter epsilon, no control-block checks (operator evaluation)
@@ -140,15 +141,15 @@ __device__ __forceinline__ void bind_line(SweepArgs &a, long long &line) {
   if (a.xdir == 1) {
     a.n = pd.nx; a.cell_stride = 1; a.line_stride = pd.nx;
     a.bclo = pd.bc[0]; a.bchi = pd.bc[1];
-    a.h = pd.dx; a.h_other = NV == 4 ? pd.dy : 0.0; a.ih = pd.idx;
+    a.h = pd.dx; a.h_other = NV == 4 ? pd.dy : 0.0; a.ih = pd.idx; a.ih_other = NV == 4 ? pd.idy : 0.0;
   } else if (a.xdir == 2) {   // a row of the problem's transposed planes: a y line
     a.n = pd.ny; a.cell_stride = 1; a.line_stride = pd.ny;
     a.bclo = pd.bc[2]; a.bchi = pd.bc[3];
-    a.h = pd.dy; a.h_other = pd.dx; a.ih = pd.idy;
+    a.h = pd.dy; a.h_other = pd.dx; a.ih = pd.idy; a.ih_other = pd.idx;
   } else {
     a.n = pd.ny; a.cell_stride = pd.nx; a.line_stride = 1;
     a.bclo = pd.bc[2]; a.bchi = pd.bc[3];
-    a.h = pd.dy; a.h_other = pd.dx; a.ih = pd.idy;
+    a.h = pd.dy; a.h_other = pd.dx; a.ih = pd.idy; a.ih_other = pd.idx;
   }
   const long long o = pd.off;
   if (a.U) a.U += o;
@@ -240,6 +241,40 @@ __device__ __forceinline__ float pow2_inv(float m) {
 __device__ __forceinline__ double pow2_inv(double m) {
   long long e = (__double_as_longlong(m) >> 52) & 0x7ff;
   return (e > 0 && e < 2046) ? __longlong_as_double((2046 - e) << 52) : 1.0;
+}
+
+// FP64 WENO-Z weights (w0, w2) of the minus side and (v0, v2) of the plus
+// side (eq. (weight), linear weights 0.2, 0.5, 0.3, the plus side on the
+// mirrored indicators) with one division for both: with d_k = beta_k + eps
+// and D = d0 d1 d2, alpha_k D^2 = c_k (D^2 + tau^2 (D / d_k)^2), a common
+// factor of each side's weights, and one reciprocal of the product of the
+// two sides' sums normalises both.  (d, tau) are first scaled by a power of
+// two near 1/max d (exact, the weights are homogeneous in them) so that the
+// sixth powers stay in range.
+__device__ __forceinline__ void zweights_both_fp64(double um2, double um1, double u0, double up1,
+                                                   double up2, double eps, double &w0, double &w2,
+                                                   double &v0, double &v2) {
+  const double c13 = 13.0 / 12.0;
+  const double b0 = c13 * sqr(um2 - 2.0 * um1 + u0) + 0.25 * sqr(um2 - 4.0 * um1 + 3.0 * u0);
+  const double b1 = c13 * sqr(um1 - 2.0 * u0 + up1) + 0.25 * sqr(um1 - up1);
+  const double b2 = c13 * sqr(u0 - 2.0 * up1 + up2) + 0.25 * sqr(3.0 * u0 - 4.0 * up1 + up2);
+  double tau = fabs(b2 - b0);
+  double d0 = b0 + eps, d1 = b1 + eps, d2 = b2 + eps;
+  const double sc = pow2_inv(fmax(fmax(d0, d1), d2));
+  d0 *= sc; d1 *= sc; d2 *= sc; tau *= sc;
+  const double p01 = d0 * d1, p02 = d0 * d2, p12 = d1 * d2;
+  const double D2 = sqr(p01 * d2), t2 = tau * tau;
+  const double e0 = t2 * sqr(p12), e1 = t2 * sqr(p02), e2 = t2 * sqr(p01);
+  // minus: (c0, c1, c2) on (e0, e1, e2); plus: the same c on (e2, e1, e0)
+  const double am0 = 0.2 * (D2 + e0), am1 = 0.5 * (D2 + e1), am2 = 0.3 * (D2 + e2);
+  const double ap0 = 0.2 * (D2 + e2), ap2 = 0.3 * (D2 + e0);
+  const double sm = am0 + am1 + am2, sp = ap0 + am1 + ap2;
+  const double inv = 1.0 / (sm * sp);
+  const double ism = sp * inv, isp = sm * inv;
+  w0 = am0 * ism;
+  w2 = am2 * ism;
+  v0 = ap0 * isp;
+  v2 = ap2 * isp;
 }
 
 // rescale the map (its projective action is unchanged) so that the largest
@@ -469,6 +504,16 @@ __device__ __forceinline__ double bits_double(unsigned long long b) {
   return __longlong_as_double((long long)b);
 }
 
+// grid-wide extrema on a few control-block words: every warp of every CTA
+// reports, so an atomic whose value cannot change the word is skipped (the
+// words only move one way during a launch; a stale read only costs an atomic)
+__device__ __forceinline__ void atomic_max_bits(unsigned long long *w, unsigned long long v) {
+  if (v > *reinterpret_cast<volatile unsigned long long *>(w)) atomicMax(w, v);
+}
+__device__ __forceinline__ void atomic_min_bits(unsigned long long *w, unsigned long long v) {
+  if (v < *reinterpret_cast<volatile unsigned long long *>(w)) atomicMin(w, v);
+}
+
 // ---------------------------------------------------------------- kernel
 // Resident CTAs per SM the kernel is compiled for: the mixed form is bound by
 // latency, so it asks for three at M = 8 (85 registers a thread; the shared
@@ -691,14 +736,15 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
             rm.a = real(0); rm.b = real(1); rm.c = real(0); rm.r = fmv;
             rp.a = real(0); rp.b = real(1); rp.c = real(0); rp.r = fpv;
           } else {
-            real q0, q1, q2, one, w0, w1, w2, v0, v1, v2;
-            zratios_any(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w, q0, q1, q2, one);
+            real w0, w2, v0, v2;
             if constexpr (MIXED) {
+              real q0, q1, q2, one;
+              zratios_any(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w, q0, q1, q2,
+                          one);
               zweights_pair(q0, q1, q2, one, w0, w2, v0, v2);
-              (void)w1; (void)v1;
             } else {
-              zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
-              zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, v0, v1, v2, one);
+              zweights_both_fp64(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w, w0,
+                                 w2, v0, v2);
             }
             wt[cb + j] = w0;
             wt[WP + cb + j] = w2;
@@ -924,6 +970,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       real Pp = cpp, Qp = real(1), Dp = dpp, Zp = zpp;
       real pim = real(1), Am = real(0), Azm = real(0);
       real pip = real(1), Ap = real(0), Azp = real(0);
+      (void)Qm; (void)Qp;   // the FP64 chains carry no Q
       auto elim = [&](const Row<real> &r, real zr, real &P, real &Qs, real &D, real &Z,
                       real &co, real &dout, real &zo) {
         if constexpr (MIXED) {
@@ -936,64 +983,84 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
           co = P * iq;
           dout = D * iq;
           zo = PER ? Z * iq : real(0);
+        }
+      };
+      // the row of cell s0 + j of side sd (0 minus, 1 plus) and its z entry
+      auto row_of = [&](int sd, int j, real &zr) -> Row<real> {
+        const int i = s0 + j;
+        const real *o = wt + 2 * sd * WP + cb + j;
+        Row<real> r;
+        zr = real(0);
+        if (bounded && (i == 0 || i == n - 1)) {
+          r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
+        } else if (PER && (i == 0 || i == n - 1)) {
+          r = per_row(i, sd, zr);
+        } else if (sd == 0) {
+          r = compact_row02(o[0], o[WP], win[j + 1], win[j + 2], win[j + 3]);
         } else {
-          real ip = real(1) / (r.b - r.a * P);
-          D = (r.r - r.a * D) * ip;
-          if (PER) Z = (zr - r.a * Z) * ip;
-          P = r.c * ip;
-          co = P;
-          dout = D;
-          zo = Z;
+          r = compact_row02(o[0], o[WP], win[j + 3], win[j + 2], win[j + 1]);
+        }
+        return r;
+      };
+      // c', d' (and z') of a row stored over its weights; the back map grows
+      auto finish = [&](int sd, int j, real co, real dd, real zz) {
+        real *o = wt + 2 * sd * WP + cb + j;
+        o[0] = co;
+        o[WP] = dd;
+        if (sd == 0) {
+          if (PER) zmv[j] = zz;
+          Am += pim * dd;
+          if (PER) Azm += pim * zz;
+          pim *= -co;
+        } else {
+          if (PER) zpv[j] = zz;
+          Ap += pip * dd;
+          if (PER) Azp += pip * zz;
+          pip *= -co;
         }
       };
   #pragma unroll
       for (int jj = 0; jj < M; ++jj) {
-        {   // minus: cell s0 + jj
-          const int j = jj;
-          if (j < len) {
-            const int i = s0 + j;
-            real *o = wt + cb + j;
-            Row<real> r;
-            real zr = real(0);
-            if (bounded && (i == 0 || i == n - 1)) {
-              r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
-            } else if (PER && (i == 0 || i == n - 1)) {
-              r = per_row(i, 0, zr);
-            } else {
-              r = compact_row02(o[0], o[WP], win[j + 1], win[j + 2], win[j + 3]);
-            }
-            real co, dd, zz;
+        const int jm = jj, jp = M - 1 - jj;    // minus left to right, plus right to left
+        const bool am = jm < len, ap = jp < len;
+        if constexpr (MIXED) {
+          if (am) {
+            real zr, co, dd, zz;
+            const Row<real> r = row_of(0, jm, zr);
             elim(r, zr, Pm, Qm, Dm, Zm, co, dd, zz);
-            o[0] = co;
-            o[WP] = dd;
-            if (PER) zmv[j] = zz;
-            Am += pim * dd;
-            if (PER) Azm += pim * zz;
-            pim *= -co;
+            finish(0, jm, co, dd, zz);
           }
-        }
-        {   // plus: cell s0 + M - 1 - jj
-          const int j = M - 1 - jj;
-          if (j < len) {
-            const int i = s0 + j;
-            real *o = wt + 2 * WP + cb + j;
-            Row<real> r;
-            real zr = real(0);
-            if (bounded && (i == 0 || i == n - 1)) {
-              r.a = real(0); r.b = real(1); r.c = real(0); r.r = o[0];
-            } else if (PER && (i == 0 || i == n - 1)) {
-              r = per_row(i, 1, zr);
-            } else {
-              r = compact_row02(o[0], o[WP], win[j + 3], win[j + 2], win[j + 1]);
-            }
-            real co, dd, zz;
+          if (ap) {
+            real zr, co, dd, zz;
+            const Row<real> r = row_of(1, jp, zr);
             elim(r, zr, Pp, Qp, Dp, Zp, co, dd, zz);
-            o[0] = co;
-            o[WP] = dd;
-            if (PER) zpv[j] = zz;
-            Ap += pip * dd;
-            if (PER) Azp += pip * zz;
-            pip *= -co;
+            finish(1, jp, co, dd, zz);
+          }
+        } else {
+          // FP64: one division for the pivots of both chains,
+          // 1/(q_m q_p) times q_p and q_m
+          real zrm = real(0), zrp = real(0);
+          Row<real> rm, rp;
+          rm.a = rm.c = rm.r = rp.a = rp.c = rp.r = real(0);
+          rm.b = rp.b = real(1);
+          if (am) rm = row_of(0, jm, zrm);
+          if (ap) rp = row_of(1, jp, zrp);
+          const real qm = am ? rm.b - rm.a * Pm : real(1);
+          const real qp = ap ? rp.b - rp.a * Pp : real(1);
+          const real inv = real(1) / (qm * qp);
+          if (am) {
+            const real ip = qp * inv;
+            Dm = (rm.r - rm.a * Dm) * ip;
+            if (PER) Zm = (zrm - rm.a * Zm) * ip;
+            Pm = rm.c * ip;
+            finish(0, jm, Pm, Dm, Zm);
+          }
+          if (ap) {
+            const real ip = qm * inv;
+            Dp = (rp.r - rp.a * Dp) * ip;
+            if (PER) Zp = (zrp - rp.a * Zp) * ip;
+            Pp = rp.c * ip;
+            finish(1, jp, Pp, Dp, Zp);
           }
         }
       }
@@ -1421,7 +1488,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
         double un;
         if (args.stage == 0) un = uk + dt * L;
         else if (args.stage == 1) un = 0.75 * args.U0[g * args.ncell + addr] + 0.25 * uk + 0.25 * dt * L;
-        else un = args.U0[g * args.ncell + addr] / 3.0 + 2.0 / 3.0 * uk + 2.0 / 3.0 * dt * L;
+        else un = args.U0[g * args.ncell + addr] * (1.0 / 3.0) + 2.0 / 3.0 * uk + 2.0 / 3.0 * dt * L;
         args.Uout[g * args.ncell + addr] = un;
         Ut[kv] = un;   // line-variable order (no run-time register index)
       }
@@ -1429,7 +1496,9 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       double rho = Ut[0], E = Ut[NV - 1];
       double mx = NV == 4 && args.vn != 1 ? Ut[2] : Ut[1];
       double my = NV == 4 ? (args.vn != 1 ? Ut[1] : Ut[2]) : 0.0;
-      double e = E / rho - 0.5 * (mx * mx + my * my) / (rho * rho);
+      // one division per cell: 1/rho (1/h from the host)
+      const double irho = 1.0 / rho;
+      double e = (E - 0.5 * (mx * mx + my * my) * irho) * irho;
       bool ok = (rho > 0.0) && (e > 0.0) && isfinite(E) && isfinite(mx) && isfinite(my);
       if (!ok) {
         ++nbad;
@@ -1439,11 +1508,11 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
         double a = sqrt(args.gamma * (args.gamma - 1.0) * e);
         double rate;
         if (NV == 4) {
-          double hx = args.vn == 1 ? args.h : args.h_other;
-          double hy = args.vn == 1 ? args.h_other : args.h;
-          rate = (fabs(mx / rho) + a) / hx + (fabs(my / rho) + a) / hy;
+          const double ihx = args.vn == 1 ? args.ih : args.ih_other;
+          const double ihy = args.vn == 1 ? args.ih_other : args.ih;
+          rate = (fabs(mx) * irho + a) * ihx + (fabs(my) * irho + a) * ihy;
         } else {
-          rate = (fabs(mx / rho) + a) / args.h;
+          rate = (fabs(mx) * irho + a) * args.ih;
         }
         mymax = fmax(mymax, rate);
       }
@@ -1511,7 +1580,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       const double o = __shfl_down_sync(0xffffffffu, fr, d);
       if (o > fr || o != o) fr = o;
     }
-    if (lane == 0) atomicMax(&ctl->frate[args.fdir], double_bits(fr));
+    if (lane == 0) atomic_max_bits(&ctl->frate[args.fdir], double_bits(fr));
   }
   if (MODE == MODE_FINAL) {
 #pragma unroll
@@ -1525,8 +1594,8 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       firstbad = fb < firstbad ? fb : firstbad;
     }
     if (lane == 0) {
-      atomicMin(&ctl->minrho[args.stage], double_bits(mymin));
-      if (args.stage == 2) atomicMax(&ctl->rate, double_bits(mymax));
+      atomic_min_bits(&ctl->minrho[args.stage], double_bits(mymin));
+      if (args.stage == 2) atomic_max_bits(&ctl->rate, double_bits(mymax));
       if (nbad) {
         atomicAdd(&ctl->nviol, (unsigned long long)nbad);
         atomicMin(&ctl->first_bad, firstbad);

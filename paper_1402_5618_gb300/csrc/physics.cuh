@@ -40,16 +40,22 @@ __device__ __forceinline__ void zratios(real um2, real um1, real u0, real up1, r
 // becomes s = (dmin/tau)^2; the normalised weights are unchanged
 // (near a jump of 3e6 the plain q_k reaches 1e52, beyond FP32's range).
 //
-// eps is lifted to the FP32 noise floor of the indicators.  Each FP32
-// average carries a rounding error of up to u max|ubar| (u = 2^-24), so the
-// indicators of a flat stencil are not 0 but up to about 33 (u max|ubar|)^2;
+// eps is lifted to the FP32 noise floor of the indicators.  The FP32
+// averages the indicators are computed from carry, besides their own
+// rounding (up to u max|ubar|, u = 2^-24), the rounding noise the FP32
+// fluxes leave in the state step after step: a random walk of about
+// cfl u |F| per step, tens to hundreds of u max|ubar| after 10^4 steps.
 // eps of eq. (weight), meant to sit above the indicators' zero level and
-// below every real one, becomes eps + 4096 (u max|ubar|)^2 over the stencil
-// (about a hundred times that noise bound).  With the FP64 value alone the
-// weights follow rounding noise wherever the solution is flat to FP32
-// precision, and a grid-scale mode that the nonlinear weights otherwise damp
-// grows from that noise.
-constexpr float FP32_BETA_FLOOR = 4096.0f * 5.9604645e-08f * 5.9604645e-08f;
+// below every real one, becomes eps + 2^20 (u max|ubar|)^2 over the stencil:
+// above 33 (150 u max|ubar|)^2, the indicators of a flat stencil carrying
+// that noise, and still about 4e-9 max|ubar|^2, below the indicators of
+// any feature the FP32 form resolves.  With the FP64 value alone, or a
+// floor that the accumulated noise overtakes, the weights follow rounding
+// noise where the solution is flat to FP32 precision and a grid-scale mode
+// that the nonlinear weights otherwise damp grows from it (isentropic
+// vortex on 1024^2 to t = 10: density L1 1.9e-4 with the floor at
+// 4096 (u max|ubar|)^2, 1.7e-6 at 2^20 (u max|ubar|)^2).
+constexpr float FP32_BETA_FLOOR = 1048576.0f * 5.9604645e-08f * 5.9604645e-08f;
 
 __device__ __forceinline__ void zratios_scaled(float um2, float um1, float u0, float up1, float up2,
                                                float eps, float &q0, float &q1, float &q2,
@@ -180,61 +186,75 @@ __device__ __forceinline__ void phys_flux(const real *U, real p, real *F) {
   F[NV - 1] = un * (U[NV - 1] + p);
 }
 
+// the same with the normal velocity un = m_n / rho already known
+template <typename real, int NV>
+__device__ __forceinline__ void phys_flux_u(const real *U, real un, real p, real *F) {
+  F[0] = U[1];
+  F[1] = U[1] * un + p;
+  if (NV == 4) F[2] = U[2] * un;
+  F[NV - 1] = un * (U[NV - 1] + p);
+}
+
 // HLLC flux (Sec. 2.4, eqs. (HLLC), (contact-v), (star-l), (acoustic ws)).
 // S_M's denominator uses rho_r on the right-state term, S_R is the max of
 // the two estimates and the right star flux uses S_R.  In 2-D the
 // tangential velocity is carried by the contact.  smax receives the larger
 // |u| + a of the two face states (the speed eq. (CFL-CD) bounds).
+// Four divisions per face (1/(rho_l rho_r) for both inverse densities,
+// 1/(1 + R) for the Roe averages, S_M, and the star state's 1/(S_K - S_M)):
+// in FP64 each one expands to a sequence on the FP64 pipe.
 template <typename real, int NV>
 __device__ __forceinline__ void hllc(const real *Ul, const real *Ur, real gamma, real *F,
                                      real &smax) {
-  real rl = Ul[0], rr = Ur[0];
-  real ul = Ul[1] / rl, ur = Ur[1] / rr;
-  real vl = NV == 4 ? Ul[2] / rl : real(0), vr = NV == 4 ? Ur[2] / rr : real(0);
-  real El = Ul[NV - 1], Er = Ur[NV - 1];
-  real pl = pressure<real, NV>(Ul, gamma), pr = pressure<real, NV>(Ur, gamma);
+  const real rl = Ul[0], rr = Ur[0];
+  const real irr_irl = real(1) / (rl * rr);
+  const real irl = rr * irr_irl, irr = rl * irr_irl;
+  const real ml = Ul[1], mr = Ur[1];
+  const real ul = ml * irl, ur = mr * irr;
+  const real vl = NV == 4 ? Ul[2] * irl : real(0), vr = NV == 4 ? Ur[2] * irr : real(0);
+  const real El = Ul[NV - 1], Er = Ur[NV - 1];
+  // p = (gamma - 1)(E - |m|^2 / (2 rho)) with |m|^2 / rho = m . u
+  real pl = (gamma - real(1)) * (El - real(0.5) * (ml * ul + (NV == 4 ? Ul[2] * vl : real(0))));
+  real pr = (gamma - real(1)) * (Er - real(0.5) * (mr * ur + (NV == 4 ? Ur[2] * vr : real(0))));
   if constexpr (sizeof(real) == 4) {   // FP32 form: never a NaN sound speed from rounding
     pl = fmaxf(pl, 0.0f);
     pr = fmaxf(pr, 0.0f);
   }
-  real al = sqrt(gamma * pl / rl), ar = sqrt(gamma * pr / rr);
+  const real al = sqrt(gamma * pl * irl), ar = sqrt(gamma * pr * irr);
   smax = fmax(fabs(ul) + al, fabs(ur) + ar);
-  real Hl = (El + pl) / rl, Hr = (Er + pr) / rr;
-  real R = sqrt(rr / rl);
-  real ut = (ul + ur * R) / (real(1) + R);
-  real vt = (vl + vr * R) / (real(1) + R);
-  real Ht = (Hl + Hr * R) / (real(1) + R);
-  real at = sqrt((gamma - real(1)) * (Ht - real(0.5) * (ut * ut + vt * vt)));
-  real SL = fmin(ul - al, ut - at);
-  real SR = fmax(ur + ar, ut + at);
-  real SM = (rr * ur * (SR - ur) - rl * ul * (SL - ul) + pl - pr) / (rr * (SR - ur) - rl * (SL - ul));
+  const real Hl = (El + pl) * irl, Hr = (Er + pr) * irr;
+  const real R = sqrt(rr * irl);
+  const real iR = real(1) / (real(1) + R);
+  const real ut = (ul + ur * R) * iR;
+  const real vt = (vl + vr * R) * iR;
+  const real Ht = (Hl + Hr * R) * iR;
+  const real at = sqrt((gamma - real(1)) * (Ht - real(0.5) * (ut * ut + vt * vt)));
+  const real SL = fmin(ul - al, ut - at);
+  const real SR = fmax(ur + ar, ut + at);
   if (SL > real(0)) {
-    phys_flux<real, NV>(Ul, pl, F);
-  } else if (SM > real(0)) {
-    real Fk[NV], Us[NV];
-    real ps = rl * (ul - SL) * (ul - SM) + pl;
-    real inv = real(1) / (SL - SM);
-    Us[0] = rl * (SL - ul) * inv;
-    Us[1] = ((SL - ul) * rl * ul + (ps - pl)) * inv;
-    if (NV == 4) Us[2] = Us[0] * vl;
-    Us[NV - 1] = ((SL - ul) * El - pl * ul + ps * SM) * inv;
-    phys_flux<real, NV>(Ul, pl, Fk);
-#pragma unroll
-    for (int k = 0; k < NV; ++k) F[k] = Fk[k] + SL * (Us[k] - Ul[k]);
-  } else if (SR >= real(0)) {
-    real Fk[NV], Us[NV];
-    real ps = rr * (ur - SR) * (ur - SM) + pr;
-    real inv = real(1) / (SR - SM);
-    Us[0] = rr * (SR - ur) * inv;
-    Us[1] = ((SR - ur) * rr * ur + (ps - pr)) * inv;
-    if (NV == 4) Us[2] = Us[0] * vr;
-    Us[NV - 1] = ((SR - ur) * Er - pr * ur + ps * SM) * inv;
-    phys_flux<real, NV>(Ur, pr, Fk);
-#pragma unroll
-    for (int k = 0; k < NV; ++k) F[k] = Fk[k] + SR * (Us[k] - Ur[k]);
-  } else {
-    phys_flux<real, NV>(Ur, pr, F);
+    phys_flux_u<real, NV>(Ul, ul, pl, F);
+    return;
   }
+  const real SM = (rr * ur * (SR - ur) - rl * ul * (SL - ul) + pl - pr) / (rr * (SR - ur) - rl * (SL - ul));
+  const bool left = SM > real(0);
+  if (!left && !(SR >= real(0))) {
+    phys_flux_u<real, NV>(Ur, ur, pr, F);
+    return;
+  }
+  // the star state of side K (K = l if S_M > 0, else r) and F = F_K + S_K (U*_K - U_K)
+  const real *UK = left ? Ul : Ur;
+  const real rK = left ? rl : rr, uK = left ? ul : ur, pK = left ? pl : pr;
+  const real SK = left ? SL : SR, EK = left ? El : Er, vK = left ? vl : vr;
+  real Fk[NV], Us[NV];
+  const real ps = rK * (uK - SK) * (uK - SM) + pK;
+  const real inv = real(1) / (SK - SM);
+  Us[0] = rK * (SK - uK) * inv;
+  Us[1] = ((SK - uK) * rK * uK + (ps - pK)) * inv;
+  if (NV == 4) Us[2] = Us[0] * vK;
+  Us[NV - 1] = ((SK - uK) * EK - pK * uK + ps * SM) * inv;
+  phys_flux_u<real, NV>(UK, uK, pK, Fk);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) F[k] = Fk[k] + SK * (Us[k] - UK[k]);
 }
 
 // Local Lax-Friedrichs flux, the alternative Sec. 3 names for the

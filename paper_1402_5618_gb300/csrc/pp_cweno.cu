@@ -113,15 +113,18 @@ __global__ void step_end_kernel(Ctl *ctls, int nprob) {
   if (++ctl->nrej_run > 60) ctl->err_rate = 1;
 }
 
-// Checked steps write U^{n+1} into the stage buffer: copy it over U^n where
-// the step was accepted.  Problem p (blockIdx.y) owns the 32-bit words
-// [a0, a0 + n) and [a1, a1 + n) of both buffers (FP64 values, or the FP32 hi
-// and lo planes of the mixed form).
-__global__ void commit_kernel(const unsigned int *src, unsigned int *dst, const ProbDesc *probs,
-                              long long nvals, int mixed, int nv, const Ctl *ctls) {
+// Checked steps leave U^n in its buffer and U^{n+1} in the stage buffer,
+// and the two buffers swap roles for the next step; where a step was
+// rejected, or a problem took no step (finished, stopped, or past its step
+// limit), U^n is copied into the stage buffer so that the next step starts
+// from it again.  Problem p (blockIdx.y) owns the 32-bit words [a0, a0 + n)
+// and [a1, a1 + n) of both buffers (FP64 values, or the FP32 hi and lo planes
+// of the mixed form).
+__global__ void restore_kernel(const unsigned int *src, unsigned int *dst, const ProbDesc *probs,
+                               long long nvals, int mixed, int nv, const Ctl *ctls) {
   const int p = blockIdx.y;
   const Ctl *ctl = ctls + p;
-  if (!ctl->active || !step_accepted(ctl)) return;
+  if (ctl->active && step_accepted(ctl)) return;
   long long a0 = 0, a1 = nvals, n = nvals;   // single problem: everything
   if (probs) {
     const ProbDesc pd = probs[p];
@@ -642,7 +645,11 @@ struct pp_cweno_s {
   void *D = nullptr;
   Ctl *ctl = nullptr, *ctl_scratch = nullptr;   // [nprob]
   Ctl *hctl = nullptr;   // pinned mirror [nprob]
-  cudaGraphExec_t graph = nullptr;
+  // graphs of GRAPH_STEPS steps; checked steps swap the two state buffers
+  // after every step, so a graph is kept per buffer holding U^n when it
+  // starts (index 0: the first allocation, buf0)
+  cudaGraphExec_t graphs[2] = {nullptr, nullptr};
+  void *buf0 = nullptr;
   long long launches_per_step = 0;
   int m = 8;                  // rows per thread chunk of the line kernels (autotuned)
   bool btrans = false;        // mixed 2-D batch: transposed y sweeps and batched combination
@@ -670,6 +677,13 @@ struct pp_cweno_s {
   std::vector<pp_cweno_config> cfgs;
   ProbDesc *probs = nullptr;   // device
   std::vector<LineGroup> groups;
+  // the groups of one sweep direction are independent (different problems):
+  // each runs on its own stream between a fork and a join event, so that one
+  // group's last wave of clusters overlaps the next group's (in a captured
+  // graph: parallel branches)
+  std::vector<cudaStream_t> gstreams;
+  std::vector<cudaEvent_t> gevents;
+  cudaEvent_t fork_ev = nullptr;
 };
 
 namespace {
@@ -763,7 +777,7 @@ void fill_state(const pp_cweno_s *h, SweepArgs &a, const void *Uin, const void *
 }
 
 cudaError_t dispatch(const pp_cweno_s *h, int mode, bool periodic, const SweepArgs &a,
-                     long long nlines, bool attrs_only) {
+                     long long nlines, bool attrs_only, cudaStream_t st_override = nullptr) {
   LaunchCfg c;
   c.precision = h->cfg.precision;
   c.nv = h->nv;
@@ -773,7 +787,8 @@ cudaError_t dispatch(const pp_cweno_s *h, int mode, bool periodic, const SweepAr
   c.m = h->m;
   SweepArgs b = a;
   b.ih = a.h > 0.0 ? 1.0 / a.h : 0.0;   // batched launches take it per problem
-  return launch_sweep(c, b, nlines, h->stream);
+  b.ih_other = a.h_other > 0.0 ? 1.0 / a.h_other : 0.0;
+  return launch_sweep(c, b, nlines, st_override ? st_override : h->stream);
 }
 
 // Characteristic-wise handles: the face values of the sweep described by a
@@ -856,16 +871,19 @@ cudaError_t launch(const pp_cweno_s *h, int mode, bool xdir, const void *Uin, co
   return dispatch(h, mode, a.bclo == PP_BC_PERIODIC, a, nlines, attrs_only);
 }
 
-// Batched launch of one line group.
+// Batched launch of one line group.  eps_fixed > 0 with ctl: a measurement
+// launch (the autotuner's) that reduces into a scratch control block array.
 cudaError_t launch_group(const pp_cweno_s *h, const LineGroup &g, int mode, const void *Uin,
                          const void *U0, const void *Din, void *Dout, void *Uout, int stage,
-                         bool attrs_only = false) {
+                         bool attrs_only = false, double eps_fixed = 0.0, Ctl *ctl = nullptr,
+                         double *Lout = nullptr, cudaStream_t st = nullptr) {
   SweepArgs a;
   memset(&a, 0, sizeof(a));
   fill_state(h, a, Uin, U0, Uout);
-  fill_common(h, a, stage, 0.0, h->ctl);
+  fill_common(h, a, stage, eps_fixed, ctl ? ctl : h->ctl);
   a.Din = Din;
   a.Dout = Dout;
+  a.Lout = Lout;
   a.R = g.R;
   a.lines = g.lines;
   a.probs = h->probs;
@@ -881,7 +899,7 @@ cudaError_t launch_group(const pp_cweno_s *h, const LineGroup &g, int mode, cons
   a.vn = g.xdir ? 1 : 2;
   a.vt = h->nv == 4 ? (g.xdir ? 2 : 1) : -1;
   a.fdir = g.xdir ? 0 : 1;
-  return dispatch(h, mode, g.periodic, a, g.nlines, attrs_only);
+  return dispatch(h, mode, g.periodic, a, g.nlines, attrs_only, st);
 }
 
 // y sweep of the mixed 2-D form over the transposed hi planes: a row sweep
@@ -953,17 +971,17 @@ cudaError_t transpose_state_hi(const pp_cweno_s *h, bool gated = false) {
   return cudaGetLastError();
 }
 
-// end of a checked step: U^{n+1} (in the stage buffer) over U^n where the
-// step was accepted, the transposed planes of U^n back where it was
-// rejected, then the per-problem bookkeeping
+// end of a checked step: where it was rejected, U^n (still in U0) into the
+// stage buffer and its transposed planes back; then the per-problem
+// bookkeeping.  The caller swaps U0 and U1 afterwards.
 cudaError_t finish_checked_step(pp_cweno_s *h, const std::function<void()> &mark) {
   const long long per = h->batch ? 0 : nvals(h);
   long long longest = per;
   if (h->batch)
     for (const ProbDesc &d : h->probs_h) longest = std::max(longest, (long long)h->nv * d.ncell);
   const unsigned bx = (unsigned)std::min<long long>(h->batch ? 64 : 4096, (longest + 255) / 256);
-  commit_kernel<<<dim3(std::max(1u, bx), (unsigned)h->nprob), 256, 0, h->stream>>>(
-      reinterpret_cast<const unsigned int *>(h->U1), reinterpret_cast<unsigned int *>(h->U0),
+  restore_kernel<<<dim3(std::max(1u, bx), (unsigned)h->nprob), 256, 0, h->stream>>>(
+      reinterpret_cast<const unsigned int *>(h->U0), reinterpret_cast<unsigned int *>(h->U1),
       h->batch ? h->probs : nullptr, nvals(h), is_mixed(h) ? 1 : 0, h->nv, h->ctl);
   cudaError_t e = cudaGetLastError();
   mark();
@@ -975,6 +993,28 @@ cudaError_t finish_checked_step(pp_cweno_s *h, const std::function<void()> &mark
   step_end_kernel<<<(h->nprob + 127) / 128, 128, 0, h->stream>>>(h->ctl, h->nprob);
   e = cudaGetLastError();
   mark();
+  return e;
+}
+
+// the line groups of one direction (xdir) of a batch, each on its own
+// stream between a fork and a join on the handle's stream
+cudaError_t launch_groups(const pp_cweno_s *h, bool xdir, int mode, const void *Uin,
+                          const void *Din, void *Dout, void *Uout, int stage) {
+  cudaError_t e = cudaEventRecord(h->fork_ev, h->stream);
+  size_t used = 0;
+  for (size_t i = 0; i < h->groups.size() && e == cudaSuccess; ++i) {
+    const LineGroup &g = h->groups[i];
+    if (g.xdir != xdir) continue;
+    cudaStream_t st = h->gstreams[i];
+    e = cudaStreamWaitEvent(st, h->fork_ev, 0);
+    if (e == cudaSuccess)
+      e = launch_group(h, g, mode, Uin, h->U0, Din, Dout, Uout, stage, false, 0.0, nullptr, nullptr, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->gevents[i], st);
+    ++used;
+  }
+  for (size_t i = 0; i < h->groups.size() && e == cudaSuccess; ++i)
+    if (h->groups[i].xdir == xdir) e = cudaStreamWaitEvent(h->stream, h->gevents[i], 0);
+  (void)used;
   return e;
 }
 
@@ -1019,27 +1059,19 @@ cudaError_t enqueue_step_body(pp_cweno_s *h, cudaEvent_t *ev, int *nev) {
       if (e != cudaSuccess) return e;
       continue;
     }
-    for (const LineGroup &g : h->groups) {   // x groups come first
-      if (!g.xdir) continue;
-      if (h->nv == 4) e = launch_group(h, g, MODE_XSWEEP, Uin, h->U0, nullptr, h->D, nullptr, s);
-      else e = launch_group(h, g, MODE_FINAL, Uin, h->U0, nullptr, nullptr, Uout, s);
-      if (e != cudaSuccess) return e;
-    }
+    // x groups, then (2-D) y groups, each set concurrently
+    if (h->nv == 4) e = launch_groups(h, true, MODE_XSWEEP, Uin, nullptr, h->D, nullptr, s);
+    else e = launch_groups(h, true, MODE_FINAL, Uin, nullptr, nullptr, Uout, s);
+    if (e != cudaSuccess) return e;
+    if (h->nv == 3) continue;
     if (h->btrans) {   // mixed 2-D: transposed y rows, then the batched combination
-      for (const LineGroup &g : h->groups) {
-        if (g.xdir) continue;
-        e = launch_group(h, g, MODE_XSWEEP, Uin, h->U0, nullptr, h->DT, nullptr, s);
-        if (e != cudaSuccess) return e;
-      }
-      e = launch_combine_b(h, Uin, Uout, s);
+      e = launch_groups(h, false, MODE_XSWEEP, Uin, nullptr, h->DT, nullptr, s);
+      if (e == cudaSuccess) e = launch_combine_b(h, Uin, Uout, s);
       if (e != cudaSuccess) return e;
       continue;
     }
-    for (const LineGroup &g : h->groups) {
-      if (g.xdir) continue;
-      e = launch_group(h, g, MODE_FINAL, Uin, h->U0, h->D, nullptr, Uout, s);
-      if (e != cudaSuccess) return e;
-    }
+    e = launch_groups(h, false, MODE_FINAL, Uin, h->D, nullptr, Uout, s);
+    if (e != cudaSuccess) return e;
   }
   if (h->fcheck) {
     e = finish_checked_step(h, mark);
@@ -1052,11 +1084,23 @@ cudaError_t enqueue_step_body(pp_cweno_s *h, cudaEvent_t *ev, int *nev) {
 cudaError_t enqueue_step(pp_cweno_s *h, cudaEvent_t *ev = nullptr, int *nev = nullptr) {
   cudaError_t e = enqueue_step_body(h, ev, nev);
   h->mark_hook = nullptr;
+  if (e == cudaSuccess && h->fcheck) std::swap(h->U0, h->U1);   // U^{n+1} (or U^n again)
   return e;
 }
 
+int graph_key(const pp_cweno_s *h) { return h->U0 == h->buf0 ? 0 : 1; }
+
+void drop_graphs(pp_cweno_s *h) {
+  for (auto &g : h->graphs)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
 int build_graph(pp_cweno_s *h) {
-  if (h->graph) return PP_OK;
+  cudaGraphExec_t &graph = h->graphs[graph_key(h)];
+  if (graph) return PP_OK;
   cudaGraph_t g;
   cudaStream_t cap;
   if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return PP_ERR_CUDA;
@@ -1070,7 +1114,7 @@ int build_graph(pp_cweno_s *h) {
   }
   h->stream = keep;
   if (e == cudaSuccess) {
-    e = cudaGraphInstantiate(&h->graph, g, 0);
+    e = cudaGraphInstantiate(&graph, g, 0);
     cudaGraphDestroy(g);
   }
   cudaStreamDestroy(cap);
@@ -1145,6 +1189,7 @@ int finish_create(pp_cweno_s *h) {
                   (size_t)nvals(h);
   cudaError_t e = cudaMalloc(&h->U0, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->U1, bytes);
+  h->buf0 = h->U0;
   if (e == cudaSuccess && h->nv == 4) e = cudaMalloc(&h->D, dbytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->ctl, sizeof(Ctl) * h->nprob);
   if (e == cudaSuccess) e = cudaMalloc(&h->ctl_scratch, sizeof(Ctl) * h->nprob);
@@ -1214,10 +1259,54 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::vector<std::pair<TuneKey, int>> g_tune_cache;
 
+// Batches: the same choice, timed on one sweep over every x-line group of
+// the batch (the y groups run the same kernel), reducing into the scratch
+// control blocks and writing only scratch (the x-sweep output, or the stage
+// buffer as operator output).  Batches are not cached: their line mix is
+// their own.
+int autotune_batch(pp_cweno_s *h) {
+  std::vector<Ctl> z((size_t)h->nprob);
+  memset(z.data(), 0, sizeof(Ctl) * z.size());
+  if (cudaMemcpyAsync(h->ctl_scratch, z.data(), sizeof(Ctl) * z.size(), cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess)
+    return PP_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PP_ERR_CUDA;
+  float best = 1e30f;
+  int best_m = 8;
+  cudaError_t e = cudaSuccess;
+  for (int mm = 8; mm <= 16 && e == cudaSuccess; mm += 8) {
+    h->m = mm;
+    float t_min = 1e30f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      for (const LineGroup &g : h->groups) {
+        if (!g.xdir || e != cudaSuccess) continue;
+        if (h->nv == 4)
+          e = launch_group(h, g, MODE_XSWEEP, h->U0, h->U0, nullptr, h->D, nullptr, 0, false, 1e-13,
+                           h->ctl_scratch);
+        else
+          e = launch_group(h, g, MODE_OPERATOR, h->U0, h->U0, nullptr, nullptr, nullptr, 0, false,
+                           1e-13, h->ctl_scratch, reinterpret_cast<double *>(h->U1));
+      }
+      cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0 && t < t_min) t_min = t;   // first launch is a warm-up
+    }
+    if (t_min < best) { best = t_min; best_m = mm; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->m = best_m;
+  return e == cudaSuccess ? PP_OK : PP_ERR_CUDA;
+}
+
 int autotune(pp_cweno_s *h) {
   if (h->tuned) return PP_OK;
   h->tuned = true;
-  if (h->batch) return PP_OK;   // batches keep the default chunk length
+  if (h->batch) return autotune_batch(h);
   TuneKey key{h->cfg.precision, h->nv == 4 ? 2 : 1, h->nx, h->ny, h->cfg.bc[0] == PP_BC_PERIODIC};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -1414,6 +1503,15 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
     if (e == cudaSuccess)
       e = cudaMemcpy(h->tiles, tiles.data(), sizeof(TileRef) * tiles.size(), cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
+  for (size_t g = 0; g < h->groups.size() && e == cudaSuccess; ++g) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) h->gstreams.push_back(st);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) h->gevents.push_back(ev);
+  }
   int rc = e == cudaSuccess ? finish_create(h) : PP_ERR_CUDA;
   if (rc) {
     pp_cweno_destroy(h);
@@ -1479,10 +1577,7 @@ int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0) 
   if (!h->tuned) {
     int m0 = h->m;
     if ((rc = autotune(h))) return rc;
-    if (h->m != m0 && h->graph) {
-      cudaGraphExecDestroy(h->graph);
-      h->graph = nullptr;
-    }
+    if (h->m != m0) drop_graphs(h);
   }
   return PP_OK;
 }
@@ -1575,7 +1670,7 @@ int pp_cweno_advance(pp_cweno_t h, double t_final, int64_t max_steps, int64_t *s
   if ((rc = push_ctl(h))) return rc;
   if ((rc = build_graph(h))) return rc;
   for (;;) {
-    if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return PP_ERR_CUDA;
+    if (cudaGraphLaunch(h->graphs[graph_key(h)], h->stream) != cudaSuccess) return PP_ERR_CUDA;
     if ((rc = pull_ctl(h))) return rc;
     bool finished = true;
     for (int p = 0; p < h->nprob; ++p) {
@@ -1610,7 +1705,7 @@ int pp_cweno_enqueue_steps(pp_cweno_t h, int64_t nsteps) {
   if ((rc = build_graph(h))) return rc;
   int64_t left = nsteps;
   while (left >= GRAPH_STEPS) {
-    if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return PP_ERR_CUDA;
+    if (cudaGraphLaunch(h->graphs[graph_key(h)], h->stream) != cudaSuccess) return PP_ERR_CUDA;
     left -= GRAPH_STEPS;
   }
   while (left > 0) {
@@ -1895,7 +1990,7 @@ int pp_cweno_operator_noalloc(const pp_cweno_config *cfg, const double *U_dev, d
 
 int pp_cweno_destroy(pp_cweno_t h) {
   if (!h) return PP_OK;
-  if (h->graph) cudaGraphExecDestroy(h->graph);
+  drop_graphs(h);
   cudaFree(h->U0);
   cudaFree(h->U1);
   cudaFree(h->D);
@@ -1909,6 +2004,9 @@ int pp_cweno_destroy(pp_cweno_t h) {
   cudaFree(h->cscr);
   cudaFree(h->crows);
   for (auto &g : h->groups) cudaFree(g.lines);
+  for (cudaStream_t st : h->gstreams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : h->gevents) cudaEventDestroy(ev);
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->hctl) cudaFreeHost(h->hctl);
   delete h;
   return PP_OK;

@@ -4,7 +4,7 @@ against the oracle run with recon = 1 on the same seeded inputs.
 FP64 tolerances, as for the component-wise form: one operator evaluation
 element-wise within 1e-12 of the variable's flux scale (max |F_v| + max |U_v|
 max(|u|+a)) / h; whole runs with an identical step count and relative L1
-within max(1e-11, 20 d_ref), d_ref the oracle's own change under a 1e-16
+within max(1e-11, 8 d_ref), d_ref the oracle's own change under a 1e-16
 relative perturbation of the input (the WENO-Z weights amplify rounding
 near jumps).  The GPU walks each line's block system in the same
 elimination order as the oracle with the same partial pivoting; the
@@ -125,7 +125,7 @@ def test_char_run_parity(B, name, make, max_steps):
     Uo, to, so, _, cnt, rc = oracle.advance(g, p.U0, p.cfl, p.t_final, max_steps=max_steps)
     noise = W.rng(999).standard_normal(p.U0.shape)
     Ub, *_ = oracle.advance(g, p.U0 * (1 + 1e-16 * noise), p.cfl, p.t_final, max_steps=max_steps)
-    tol = np.maximum(1e-11, 20 * _rel_l1(Ub, Uo))
+    tol = np.maximum(1e-11, 8 * _rel_l1(Ub, Uo))
     s = B.Solver(B.config_from_problem(p, recon=B.RECON_CHARACTERISTIC))
     s.set_state(np.ascontiguousarray(p.U0).ravel())
     n, rcg = s.advance(p.t_final, max_steps, check=False)
@@ -135,6 +135,7 @@ def test_char_run_parity(B, name, make, max_steps):
     assert rc in (0, -2) and rcg in (0, B.PP_ERR_STEPS)
     assert sg == so
     rel = _rel_l1(Ug.reshape(p.U0.shape), Uo)
+    print(f"PARITY char run {name}: rel-L1 {rel} d_ref {_rel_l1(Ub, Uo)} bound {tol}")
     assert np.all(rel <= tol), (rel, tol)
     assert st.violations == 0
 
@@ -186,7 +187,10 @@ MIXED_CASES = [
     ("smooth_1d_1500", lambda: W.random_smooth_1d(1500, stream=52), 2e-6),
     ("riemann_1300", lambda: W.riemann_1d(1300, (1.0, 0.75, 1.0), (0.125, -0.3, 0.1), bc=(2, 1)), 1e-4),
     ("smooth_periodic_8192", lambda: W.random_smooth_1d(8192, stream=56), 2e-6),
-    ("vortex_64", lambda: W.vortex_2d(64), 2e-6),
+    # the FP32 WENO-Z floor 2^20 (u s)^2 (s the size of the characteristic
+    # sums) linearises the weights on the vortex's outer indicators, which
+    # the oracle's 1e-13 leaves nonlinear: 2.2e-6 of the flux scale
+    ("vortex_64", lambda: W.vortex_2d(64), 4e-6),
     ("jumps_600x530", lambda: W.random_jumps_2d(600, 530, stream=61), 1e-4),
     ("jumps_periodic_1100x600", lambda: W.random_jumps_2d(1100, 600, stream=64, bc=(0, 0, 0, 0)), 1e-4),
 ]

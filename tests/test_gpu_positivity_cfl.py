@@ -67,7 +67,7 @@ def test_checked_batch_matches_oracle(B):
     """FP64: the two problems that leave G without the check and six
     vacuum-opening ones, 23 steps as one checked batch, each against the
     oracle's checked run on it alone: identical step and redo counts,
-    relative L1 per variable within max(1e-11, 20 d_ref) (d_ref: the
+    relative L1 per variable within max(1e-11, 8 d_ref) (d_ref: the
     oracle's own change under a 1e-16 relative perturbation of its input),
     and in G."""
     ks, sub = _subset()
@@ -82,7 +82,7 @@ def test_checked_batch_matches_oracle(B):
         assert rco == -2 and so == 23 and ps.steps == 23
         assert ps.rejected == cnt.rejected, (k, ps.rejected, cnt.rejected)
         rej_o += cnt.rejected
-        rel, tol = _rel(Ug, Uo), np.maximum(1e-11, 20 * _rel(Up, Uo))
+        rel, tol = _rel(Ug, Uo), np.maximum(1e-11, 8 * _rel(Up, Uo))
         print(f"problem {k}: n={q.nx} redone={ps.rejected} rel-L1={rel} bound={tol}")
         assert np.all(rel <= tol), (k, rel, tol)
         assert _in_G(Ug)
@@ -124,3 +124,29 @@ def test_checked_step_api_redoes_until_accepted(B):
     assert sg == 23 and st.violations == 0 and st.rejected == cnt.rejected
     assert abs(tg - to) <= 1e-12 * to
     assert np.all(_rel(Ug.reshape(q.U0.shape), Uo) <= 1e-9)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_checked_graph_replay_equals_single_steps(B, precision):
+    """Checked steps alternate the two state buffers; a graph replay that
+    runs past the step limit (21 steps from graphs of 16) must leave the
+    same state as 21 single pp_cweno_step calls, bit for bit, on the 2-D
+    corner blast (the mixed form also keeps its transposed planes)."""
+    p = W.blast_2d(64, cfl=0.5, t_final=1e9)
+    prec = B.PREC_FP64 if precision == "fp64" else B.PREC_MIXED
+    res = []
+    for mode in ("advance", "step"):
+        s = B.Solver(B.config_from_problem(p, prec, cfl_positivity_cap=True))
+        s.set_state(np.ascontiguousarray(p.U0).ravel())
+        if mode == "advance":
+            s.advance(1e9, 21, check=False)
+        else:
+            for _ in range(21):
+                s.step()
+        U, t, steps = s.get_state()
+        st = s.stats()
+        s.close()
+        assert steps == 21 and st.violations == 0
+        res.append((U, t, st.rejected))
+    assert res[0][1] == res[1][1] and res[0][2] == res[1][2]
+    assert np.array_equal(res[0][0], res[1][0])
