@@ -345,10 +345,10 @@ def run_native(args, ws, rank, local):
                 per = [sb.problem_stats(k) for k in range(len(probs))]
                 stb = sb.stats()
                 sb.close()
-                acc = np.array([ps.steps for ps in per]) - k0
-                row[pname] = {"value": float((cells * 3 * acc).sum() / (ms * 1e-3)), "unit": UNIT,
+                taken = np.array([ps.steps for ps in per]) - k0
+                row[pname] = {"value": float((cells * 3 * taken).sum() / (ms * 1e-3)), "unit": UNIT,
                               "steps": steps, "ms_per_step": ms / steps,
-                              "accepted_step_fraction": float(acc.sum() / (steps * len(probs))),
+                              "accepted_step_fraction": float(taken.sum() / (steps * len(probs))),
                               "redone_steps": int(stb.rejected),
                               "violations": int(stb.violations),
                               "problems_outside_G": int(sum(1 for ps in per if ps.violations))}

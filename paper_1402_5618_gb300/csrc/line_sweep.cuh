@@ -110,6 +110,10 @@ struct SweepArgs {
   double h, h_other;  // cell size along the line / across (0 in 1-D)
   double ih;          // 1 / h (from the host: no FP64 division per thread)
   double ih_other;    // 1 / h_other (0 in 1-D)
+  // FP32 copies for the mixed form's kernels (converting a double costs a
+  // slot of GB300's FP64 pipe per warp): gamma, wgl, eps_weno, 1/h,
+  // 1/h_other, gamma (gamma - 1), and the limiter epsilon of eps_fixed
+  float gamma_f, wgl_f, eps_weno_f, ih_f, ih_other_f, gg1_f, eps_fixed_f;
   double gamma, wgl, eps_weno;
   int stage;          // 0, 1, 2
   double eps_fixed;   // > 0: fixed limiter epsilon, no control-block checks (operator evaluation)
@@ -142,14 +146,17 @@ __device__ __forceinline__ void bind_line(SweepArgs &a, long long &line) {
     a.n = pd.nx; a.cell_stride = 1; a.line_stride = pd.nx;
     a.bclo = pd.bc[0]; a.bchi = pd.bc[1];
     a.h = pd.dx; a.h_other = NV == 4 ? pd.dy : 0.0; a.ih = pd.idx; a.ih_other = NV == 4 ? pd.idy : 0.0;
+    a.ih_f = (float)a.ih; a.ih_other_f = (float)a.ih_other;
   } else if (a.xdir == 2) {   // a row of the problem's transposed planes: a y line
     a.n = pd.ny; a.cell_stride = 1; a.line_stride = pd.ny;
     a.bclo = pd.bc[2]; a.bchi = pd.bc[3];
     a.h = pd.dy; a.h_other = pd.dx; a.ih = pd.idy; a.ih_other = pd.idx;
+    a.ih_f = (float)a.ih; a.ih_other_f = (float)a.ih_other;
   } else {
     a.n = pd.ny; a.cell_stride = pd.nx; a.line_stride = 1;
     a.bclo = pd.bc[2]; a.bchi = pd.bc[3];
     a.h = pd.dy; a.h_other = pd.dx; a.ih = pd.idy; a.ih_other = pd.idx;
+    a.ih_f = (float)a.ih; a.ih_other_f = (float)a.ih_other;
   }
   const long long o = pd.off;
   if (a.U) a.U += o;
@@ -464,6 +471,14 @@ struct Exch {
   real warp_xn[NV][2][WPV][2];   // x, z after each warp
   Bwd<real> seg_bwd[NV][2];
   double sm[NV][2][6];           // y_f, z_f, y_l, z_l, -a0/b0 (periodic)
+  // mixed form, the line's reference state R (difference form): per
+  // variable the hi / lo pair of the median of five sampled cells, R in
+  // FP32, the reference fluxes F(R), (u_R, v_R, p_R, E_R + p_R), whether
+  // the sampled densities and energies lie within a factor 2 of R (gate)
+  float rh[NV], rl[NV], rf[NV], rF[NV], rp[4];
+  int rgate[NV];
+  float rspread[NV];             // largest |sample - R| per variable (hi parts)
+  float epsf;                    // mixed form: the limiter epsilon of this stage
 };
 
 // Segment planes in shared memory carry one pad word per 128 bytes: segment
@@ -489,7 +504,11 @@ struct Smem {
   static constexpr size_t fl_off = fp_off + sizeof(real) * NV * WP;      // real Fl[NV][SEG+2]
   static constexpr size_t rm_off = fl_off + sizeof(real) * NV * (SEG + 2);  // remote stencils
   static constexpr size_t ex_off = (rm_off + sizeof(real) * NV * 2 * 6 + 15) / 16 * 16;
-  static constexpr size_t bytes = ex_off + sizeof(Exch<real, NV, WPV>);
+  // mixed form: one byte per cell (its face values stored in full, not as
+  // differences from R) and one per face (its flux stored as F - F(R))
+  static constexpr size_t cf_off = ex_off + sizeof(Exch<real, NV, WPV>);
+  static constexpr size_t ff_off = cf_off + SEG;
+  static constexpr size_t bytes = (ff_off + SEG + 2 + 15) / 16 * 16;
 };
 
 // line-variable k -> grid variable
@@ -569,22 +588,55 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   // a finished problem skips the launch (uniform over the grid)
   if (args.eps_fixed <= 0.0 && !ctl->active) return;
 
-  const real eps_w = real(args.eps_weno);
-  const real gam = real(args.gamma);
-  const real wgl = real(args.wgl);
+  const real eps_w = MIXED ? real(args.eps_weno_f) : real(args.eps_weno);
+  const real gam = MIXED ? real(args.gamma_f) : real(args.gamma);
+  const real wgl = MIXED ? real(args.wgl_f) : real(args.wgl);
   real eps_pos;
-  if (args.eps_fixed > 0.0) eps_pos = real(args.eps_fixed);
-  else if (args.stage == 0) eps_pos = real(ctl->eps0);
-  else eps_pos = real(fmin(ctl->eps_pos, bits_double(ctl->minrho[args.stage - 1])));
+  if constexpr (MIXED) {
+    // one thread takes the FP64 minimum; the others read it after the
+    // load phase's barrier (the limiter comes later)
+    if (tid == 0) {
+      double e = args.eps_fixed > 0.0 ? args.eps_fixed
+                 : (args.stage == 0 ? ctl->eps0
+                                    : fmin(ctl->eps_pos, bits_double(ctl->minrho[args.stage - 1])));
+      ex.epsf = (float)e;
+    }
+    eps_pos = real(0);   // set after the barrier
+  } else {
+    if (args.eps_fixed > 0.0) eps_pos = real(args.eps_fixed);
+    else if (args.stage == 0) eps_pos = real(ctl->eps0);
+    else eps_pos = real(fmin(ctl->eps_pos, bits_double(ctl->minrho[args.stage - 1])));
+  }
 
   const long long lbase = line * args.line_stride;
   const long long cs = args.cell_stride;
+  unsigned char *cfull = smem_raw + S::cf_off;   // mixed: cell's faces stored in full
+  unsigned char *fdel = smem_raw + S::ff_off;    // mixed: face flux stored as F - F(R)
+
+  // difference form possible: the reference samples load with the hi parts;
+  // the lo parts, and the differences, only for lines that take the form
+  const bool two = MIXED && !PRE && args.Ul != nullptr;
+  float sh[5], sl[5];
+  if constexpr (MIXED && !PRE) {
+    if (two && tid < NV) {
+      const int g = gvar(tid, NV, args.vn, args.vt);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const int i = (int)(((long long)(2 * q + 1) * n) / 10);
+        const long long a = g * args.ncell + lbase + (long long)i * cs;
+        sh[q] = args.Uh[a];
+        sl[q] = args.Ul[a];
+      }
+    }
+  }
+  (void)sh; (void)sl;
 
   // ---------------------------------------------------------------- load
-  auto cell_val = [&](int kv, int i) -> real {
-    // line variable kv at line cell i (any i; ghosts by the boundary condition)
+  // line cell i (any i; ghosts by the boundary condition): its address and
+  // whether the ghost negates the value (reflective, normal momentum)
+  auto cell_addr = [&](int kv, int i, bool &neg) -> long long {
     int g = gvar(kv, NV, args.vn, args.vt);
-    bool neg = false;
+    neg = false;
     if (i < 0 || i >= n) {
       if (PER) {
         i = (i % n + n) % n;
@@ -598,7 +650,11 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
         }
       }
     }
-    long long a = g * args.ncell + lbase + (long long)i * cs;
+    return g * args.ncell + lbase + (long long)i * cs;
+  };
+  auto cell_val = [&](int kv, int i) -> real {
+    bool neg;
+    const long long a = cell_addr(kv, i, neg);
     real x;
     if constexpr (MIXED) x = args.Uh[a];
     else x = args.U[a];
@@ -606,17 +662,18 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   };
 
   bool vec = false;
+  int nq = 0;
   if constexpr (MIXED) {
     // contiguous line with 16-byte aligned segments: the segment's cells
     // come in as float4, only the halo and a ragged tail cell by cell
     vec = cs == 1 && !args.lines && ((lbase + lo) & 3) == 0 && (args.ncell & 3) == 0 &&
           ((reinterpret_cast<unsigned long long>(args.Uh) & 15) == 0);
     if (vec) {
-      const int nq = (hi - lo) >> 2;
+      nq = (hi - lo) >> 2;
       for (int idx = tid; idx < NV * nq; idx += T) {
         int kv = idx / nq, q = idx - kv * nq;
         int g = gvar(kv, NV, args.vn, args.vt);
-        float4 x = *reinterpret_cast<const float4 *>(args.Uh + g * args.ncell + lbase + lo + 4 * q);
+        const float4 x = *reinterpret_cast<const float4 *>(args.Uh + g * args.ncell + lbase + lo + 4 * q);
         real *d = Us + kv * UWP + UH + S::pad(4 * q);
         d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
       }
@@ -645,7 +702,138 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       Rm[(kv * 2 + s) * 6 + j] = cell_val(kv, c0 - 2 + j);
     }
   }
+
+  // ------------------------------------------------ reference state (mixed)
+  // The mixed form reconstructs the differences ubar - R from a reference
+  // state R of the line (shift invariance of eq. (CWENO-FV): every row's
+  // coefficients and right-hand side weights sum to one, the indicators of
+  // eq. (weight) see differences only) and evaluates the fluxes as F - F(R)
+  // where the face states lie near R, so that FP32 rounding is relative to
+  // |U - R| rather than |U|.  R: per variable the median of five sampled
+  // cells (hi parts), the same in every CTA of the line.  The plain FP32 form
+  // on the hi parts (R = 0) stays where the difference form cannot help:
+  // lines whose sampled densities or energies spread beyond a factor 4 of R
+  // (strong jumps, vacuum), and lines flat to FP32 precision (every
+  // variable's samples within 2^-20 of its scale: R's magnitude, for the
+  // momenta at least sqrt(rho_R E_R)).  A face whose states are farther than
+  // half of R's density or energy from R is evaluated in full.  The
+  // characteristic-wise path (PRE) takes its face values from outside and
+  // keeps R = 0.  All in FP32: FP64 instructions here would cost each CTA
+  // thousands of cycles on GB300's FP64 pipe while its other warps wait.
+  bool dlt = false;
+  if constexpr (MIXED && !PRE) {
+    if (two && tid < NV) {
+      const int kv = tid;
+      // the median of the hi parts by rank (ties by index), picked by
+      // unrolled selects (no run-time indexing of the arrays)
+      float mh = 0.0f, ml = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        int below = 0;
+#pragma unroll
+        for (int r = 0; r < 5; ++r) below += (sh[r] < sh[q]) || (sh[r] == sh[q] && r < q);
+        if (below == 2) { mh = sh[q]; ml = sl[q]; }
+      }
+      bool gate = true;
+      float spread = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        if (kv == 0 || kv == NV - 1) gate = gate && sh[q] >= 0.25f * mh && sh[q] <= 4.0f * mh;
+        spread = fmaxf(spread, fabsf(sh[q] - mh));
+      }
+      if (kv == 0 || kv == NV - 1) gate = gate && mh > 0.0f;
+      ex.rh[kv] = mh;
+      ex.rl[kv] = ml;
+      ex.rf[kv] = mh + ml;
+      ex.rgate[kv] = gate ? 1 : 0;
+      ex.rspread[kv] = spread;
+    }
+  }
   __syncthreads();
+  if constexpr (MIXED) eps_pos = ex.epsf;
+  if constexpr (MIXED && !PRE) {
+    if (two) {
+      const float mom = sqrtf(fabsf(ex.rf[0] * ex.rf[NV - 1]));
+      bool flat = true;
+#pragma unroll
+      for (int kv = 0; kv < NV; ++kv) {
+        const float scale = (kv == 0 || kv == NV - 1) ? fabsf(ex.rf[kv]) : fmaxf(fabsf(ex.rf[kv]), mom);
+        flat = flat && ex.rspread[kv] <= 9.5367432e-07f * scale;   // 2^-20
+      }
+      dlt = ex.rgate[0] && ex.rgate[NV - 1] && !flat;
+    }
+    if (dlt && tid == 0) {
+      // F(R) and (u_R, v_R, p_R, E_R + p_R), FP32 (O(1) factors of the
+      // difference terms; F(R) only meets fluxes of full-form faces)
+      const float r0 = ex.rf[0], m = ex.rf[1], t = NV == 4 ? ex.rf[2] : 0.0f;
+      const float E = ex.rf[NV - 1];
+      const float ir = 1.0f / r0;
+      const float u = m * ir, vv = t * ir;
+      const float pr = (args.gamma_f - 1.0f) * (E - 0.5f * (m * u + t * vv));
+      ex.rF[0] = m;
+      ex.rF[1] = m * u + pr;
+      if (NV == 4) ex.rF[2] = t * u;
+      ex.rF[NV - 1] = (E + pr) * u;
+      ex.rp[0] = u;
+      ex.rp[1] = vv;
+      ex.rp[2] = pr;
+      ex.rp[3] = E + pr;
+    }
+    if (dlt) {
+      // (hi - R_hi) + (lo - R_lo), exact where hi and R_hi are within a
+      // factor of two of each other: each thread brings in the lo parts of
+      // the cells it loaded (the same loops) and replaces their hi parts
+      auto conv = [&](int kv, int slot, float l) {
+        Us[slot] = (Us[slot] - ex.rh[kv]) + (l - ex.rl[kv]);
+      };
+      auto conv_cell = [&](int kv, int j) {
+        const int i = lo - 2 + j;
+        if (i >= hi + 2) return;
+        bool neg;
+        const long long a = cell_addr(kv, i, neg);
+        const float l = args.Ul[a];
+        conv(kv, kv * UWP + UH + S::pad(j - 2), neg ? -l : l);
+      };
+      if (vec) {
+        for (int idx = tid; idx < NV * nq; idx += T) {
+          const int kv = idx / nq, q = idx - kv * nq;
+          const int g = gvar(kv, NV, args.vn, args.vt);
+          const float4 y = *reinterpret_cast<const float4 *>(args.Ul + g * args.ncell + lbase + lo + 4 * q);
+          const int b = kv * UWP + UH + S::pad(4 * q);
+          conv(kv, b, y.x); conv(kv, b + 1, y.y); conv(kv, b + 2, y.z); conv(kv, b + 3, y.w);
+        }
+        const int nr = UW - 4 * nq;
+        for (int idx = tid; idx < NV * nr; idx += T) {
+          const int kv = idx / nr, r = idx - kv * nr;
+          conv_cell(kv, r < 2 ? r : 4 * nq + r);
+        }
+      } else {
+        for (int idx = tid; idx < NV * UW; idx += T) conv_cell(idx / UW, idx % UW);
+      }
+      if (PER) {
+        for (int idx = tid; idx < NV * 2 * 5; idx += T) {
+          const int kv = idx / 10, s = (idx / 5) % 2, j = idx % 5;
+          bool neg;
+          const long long a = cell_addr(kv, (s == 0 ? 0 : n - 1) - 2 + j, neg);
+          const float l = args.Ul[a];
+          const int o = (kv * 2 + s) * 6 + j;
+          Rm[o] = (Rm[o] - ex.rh[kv]) + ((neg ? -l : l) - ex.rl[kv]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  (void)dlt;
+  // epsilon of eq. (weight) for this thread's variable v.  The difference
+  // form's indicators see U - R, but the rounding noise the FP32 stages
+  // leave in the state scales with |U| wherever a line or a face took the
+  // plain form; the floor therefore keeps the reference's share,
+  // 2^20 u^2 (R^2 + max|U - R|^2) >= 2^19 u^2 max|U|^2 over the stencil
+  real eps_v = eps_w;
+  if constexpr (MIXED) {
+    if (dlt) eps_v = eps_w + FP32_BETA_FLOOR * ex.rf[v] * ex.rf[v];
+  }
+
 
   // face values computed outside (the characteristic-wise reconstruction):
   // U^- and U^+ of the segment's cells in the state's layout
@@ -683,7 +871,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
     auto far_row = [&](int side, real &a0, real &b0) {
       const real *y = Rm + (v * 2 + side) * 6 + 2;
       real q0, q1, q2, one, w0, w1, w2;
-      zratios_any(y[-2], y[-1], y[0], y[1], y[2], eps_w, q0, q1, q2, one);
+      zratios_any(y[-2], y[-1], y[0], y[1], y[2], eps_v, q0, q1, q2, one);
       if (side == 0) zweights(real(0.2), real(0.5), real(0.3), q0, q1, q2, w0, w1, w2, one);
       else zweights(real(0.2), real(0.5), real(0.3), q2, q1, q0, w0, w1, w2, one);
       Row<real> r = compact_row02(w0, w2, real(0), real(0), real(0));
@@ -729,8 +917,8 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
           real zm = real(0), zp = real(0);
           Row<real> rm, rp;
           if (bounded && (i == 0 || i == n - 1)) {
-            real fmv = weno5z_face(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w);
-            real fpv = weno5z_face(win[j + 4], win[j + 3], win[j + 2], win[j + 1], win[j], eps_w);
+            real fmv = weno5z_face(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_v);
+            real fpv = weno5z_face(win[j + 4], win[j + 3], win[j + 2], win[j + 1], win[j], eps_v);
             wt[cb + j] = fmv;
             wt[2 * WP + cb + j] = fpv;
             rm.a = real(0); rm.b = real(1); rm.c = real(0); rm.r = fmv;
@@ -739,11 +927,11 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
             real w0, w2, v0, v2;
             if constexpr (MIXED) {
               real q0, q1, q2, one;
-              zratios_any(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w, q0, q1, q2,
+              zratios_any(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_v, q0, q1, q2,
                           one);
               zweights_pair(q0, q1, q2, one, w0, w2, v0, v2);
             } else {
-              zweights_both_fp64(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_w, w0,
+              zweights_both_fp64(win[j], win[j + 1], win[j + 2], win[j + 3], win[j + 4], eps_v, w0,
                                  w2, v0, v2);
             }
             wt[cb + j] = w0;
@@ -1331,6 +1519,16 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   // ---------------------------------------------------------------- limit
   unsigned int t1 = 0, t2 = 0;
   const real inv12 = real(1) / (real(1) - real(2) * wgl);
+  // difference form: the face values hold U - R until a cell is limited,
+  // then the limited values in full (cfull[c] = 1)
+  float rf[NV];
+#pragma unroll
+  for (int kv = 0; kv < NV; ++kv) rf[kv] = dlt ? ex.rf[kv] : 0.0f;
+  int anyfull = 0;   // this thread limited a cell (difference form)
+  if constexpr (MIXED) {
+    if (dlt)
+      for (int c = tid; c < hi - lo; c += T) cfull[c] = 0;
+  }
   if (args.limiter) {
     // FP32 pretest of every cell of this thread (a superset of the cells
     // the exact test limits: its thresholds carry twice the FP32 round-off
@@ -1345,9 +1543,9 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       float ub[NV], a[NV], b[NV];
 #pragma unroll
       for (int kv = 0; kv < NV; ++kv) {
-        ub[kv] = float(Us[kv * UWP + UH + S::pad(c)]);
-        a[kv] = float(Fm[kv * WP + S::pad(c)]);
-        b[kv] = float(Fp[kv * WP + S::pad(c)]);
+        ub[kv] = float(Us[kv * UWP + UH + S::pad(c)]) + rf[kv];
+        a[kv] = float(Fm[kv * WP + S::pad(c)]) + rf[kv];
+        b[kv] = float(Fp[kv * WP + S::pad(c)]) + rf[kv];
       }
       if (limit_need_mixed<NV>(ub, a, b, wgl_f, inv12_f, eps_f)) mask |= 1u << q;
     }
@@ -1363,6 +1561,19 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
         a[kv] = Fm[kv * WP + S::pad(c)];
         b[kv] = Fp[kv * WP + S::pad(c)];
       }
+      if constexpr (MIXED) {
+        if (dlt) {
+          // the average as the plain form has it (the FP32 hi part, not
+          // R + (ubar - R): exact relative to ubar however far it is from R)
+          // and the face values in full
+#pragma unroll
+          for (int kv = 0; kv < NV; ++kv) {
+            ub[kv] = args.Uh[gvar(kv, NV, args.vn, args.vt) * args.ncell + lbase + (long long)(lo + c) * cs];
+            a[kv] += rf[kv];
+            b[kv] += rf[kv];
+          }
+        }
+      }
       int f;
       if constexpr (MIXED) f = limit_cell_mixed_fp64<NV>(ub, a, b, wgl, eps_pos);
       else f = limit_cell<real, NV>(ub, a, b, wgl, eps_pos, unit_roundoff<real>());
@@ -1371,6 +1582,9 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
         for (int kv = 0; kv < NV; ++kv) {
           Fm[kv * WP + S::pad(c)] = a[kv];
           Fp[kv * WP + S::pad(c)] = b[kv];
+        }
+        if constexpr (MIXED) {
+          if (dlt) { cfull[c] = 1; anyfull = 1; }
         }
       }
       t1 += f & 1;
@@ -1387,18 +1601,27 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
     real Ul[NV], Ur[NV], F[NV];
     const real *srcL = nullptr;
     const real *srcR = nullptr;
+    const unsigned char *cfL = cfull, *cfR = cfull;   // (difference form)
     int il = 0, ir = 0;
     // left state: U^- of cell f-1
     if (f == 0) {
-      if (PER) { srcL = cluster.map_shared_rank(Fm, R - 1); il = (n - 1) - (R - 1) * SEG; }
+      if (PER) {
+        srcL = cluster.map_shared_rank(Fm, R - 1); il = (n - 1) - (R - 1) * SEG;
+        cfL = cluster.map_shared_rank(cfull, R - 1);
+      }
     } else if (f - 1 < lo) {
       srcL = cluster.map_shared_rank(Fm, rank - 1); il = f - 1 - (rank - 1) * SEG;
+      cfL = cluster.map_shared_rank(cfull, rank - 1);
     } else { srcL = Fm; il = f - 1 - lo; }
     // right state: U^+ of cell f
     if (f == n) {
-      if (PER) { srcR = cluster.map_shared_rank(Fp, 0); ir = 0; }
+      if (PER) {
+        srcR = cluster.map_shared_rank(Fp, 0); ir = 0;
+        cfR = cluster.map_shared_rank(cfull, 0);
+      }
     } else if (f >= hi) {
       srcR = cluster.map_shared_rank(Fp, rank + 1); ir = f - (rank + 1) * SEG;
+      cfR = cluster.map_shared_rank(cfull, rank + 1);
     } else { srcR = Fp; ir = f - lo; }
     if (srcL) {
 #pragma unroll
@@ -1407,6 +1630,53 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
     if (srcR) {
 #pragma unroll
       for (int kv = 0; kv < NV; ++kv) Ur[kv] = srcR[kv * WP + S::pad(ir)];
+    }
+    real sf;
+    if constexpr (MIXED) {
+      if (dlt) {
+        // stored values are U - R (or the limited U in full): both forms of
+        // each state, the exterior of a boundary face by its condition
+        float dl[NV], dr[NV];
+        // flags of this CTA's cells only where one of them was limited
+        const bool fulL = srcL && (cfL != cfull || anyfull) && cfL[il];
+        const bool fulR = srcR && (cfR != cfull || anyfull) && cfR[ir];
+        if (srcL) {
+#pragma unroll
+          for (int kv = 0; kv < NV; ++kv) {
+            dl[kv] = fulL ? Ul[kv] - rf[kv] : Ul[kv];
+            Ul[kv] = fulL ? Ul[kv] : Ul[kv] + rf[kv];
+          }
+        }
+        if (srcR) {
+#pragma unroll
+          for (int kv = 0; kv < NV; ++kv) {
+            dr[kv] = fulR ? Ur[kv] - rf[kv] : Ur[kv];
+            Ur[kv] = fulR ? Ur[kv] : Ur[kv] + rf[kv];
+          }
+        }
+        if (!srcL) {
+#pragma unroll
+          for (int kv = 0; kv < NV; ++kv) { Ul[kv] = Ur[kv]; dl[kv] = dr[kv]; }
+          if (args.bclo == 2) { Ul[1] = -Ul[1]; dl[1] = -dr[1] - 2.0f * rf[1]; }
+        }
+        if (!srcR) {
+#pragma unroll
+          for (int kv = 0; kv < NV; ++kv) { Ur[kv] = Ul[kv]; dr[kv] = dl[kv]; }
+          if (args.bchi == 2) { Ur[1] = -Ur[1]; dr[1] = -dl[1] - 2.0f * rf[1]; }
+        }
+        const bool near = !args.flux && !fulL && !fulR &&
+                          fabsf(dl[0]) <= 0.5f * rf[0] && fabsf(dr[0]) <= 0.5f * rf[0] &&
+                          fabsf(dl[NV - 1]) <= 0.5f * rf[NV - 1] &&
+                          fabsf(dr[NV - 1]) <= 0.5f * rf[NV - 1];
+        if (near) hllc_delta<NV>(Ul, Ur, dl, dr, rf, ex.rp, gam, F, sf);
+        else if (args.flux) llf<real, NV>(Ul, Ur, gam, F, sf);
+        else hllc<real, NV>(Ul, Ur, gam, F, sf);
+        fdel[f - lo] = near ? 1 : 0;
+        if (sf > fsmax || sf != sf) fsmax = sf;   // a NaN speed stays
+#pragma unroll
+        for (int kv = 0; kv < NV; ++kv) Fl[kv * (SEG + 2) + (f - lo)] = F[kv];
+        return;
+      }
     }
     if (!srcL) {  // boundary face 0: exterior = BC(interior)
 #pragma unroll
@@ -1418,7 +1688,6 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       for (int kv = 0; kv < NV; ++kv) Ur[kv] = Ul[kv];
       if (args.bchi == 2) Ur[1] = -Ur[1];
     }
-    real sf;
     if (args.flux) llf<real, NV>(Ul, Ur, gam, F, sf);
     else hllc<real, NV>(Ul, Ur, gam, F, sf);
     if (sf > fsmax || sf != sf) fsmax = sf;   // a NaN speed stays
@@ -1427,8 +1696,9 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   };
   if constexpr (MIXED) {
     // faces with both states in this CTA first, then (after the cluster
-    // barrier completes) the two segment-end faces, on two warps
-    __syncthreads();
+    // barrier completes) the two segment-end faces, on two warps; whether
+    // any of this CTA's cells holds its face values in full
+    anyfull = __syncthreads_or(anyfull);
     cluster_arrive();   // this CTA's limited face values, for the neighbours
     const bool lo_remote = PER || lo > 0, hi_remote = PER || hi < n;
 #pragma unroll 1
@@ -1456,19 +1726,31 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   cluster_arrive_relaxed();
 
   // ---------------------------------------------------------------- update
-  double mymin = 1.0e300, mymax = 0.0;
+  // the stage's extrema in the line's arithmetic (converted once per warp)
+  real mymin = real(sizeof(real) == 4 ? 3.0e38 : 1.0e300), mymax = real(0);
   unsigned int nbad = 0;
   unsigned long long firstbad = ~0ull;
-  const real ih = real(args.ih);
+  const real ih = MIXED ? real(args.ih_f) : real(args.ih);
   const double dt = (MODE == MODE_FINAL) ? ctl->dt : 0.0;
   const real *Din = reinterpret_cast<const real *>(args.Din);
   for (int c = tid; c < hi - lo; c += T) {
     int i = lo + c;
     long long addr = lbase + (long long)i * cs;
     real Lv[NV];
+    // difference form: a face flux stored as F - F(R) next to one stored as F
+    // (a limited or distant face state) is put on the same footing
+    int fmix = 0;   // 1: only the left face is F - F(R), 2: only the right one
+    if constexpr (MIXED) {
+      if (dlt) fmix = (fdel[c] != fdel[c + 1]) ? (fdel[c] ? 2 : 1) : 0;
+    }
 #pragma unroll
     for (int kv = 0; kv < NV; ++kv) {
-      Lv[kv] = (Fl[kv * (SEG + 2) + c] - Fl[kv * (SEG + 2) + c + 1]) * ih;
+      real fa = Fl[kv * (SEG + 2) + c], fb = Fl[kv * (SEG + 2) + c + 1];
+      if constexpr (MIXED) {
+        if (fmix == 2) fb -= ex.rF[kv];
+        else if (fmix == 1) fa -= ex.rF[kv];
+      }
+      Lv[kv] = (fa - fb) * ih;
       if (MODE != MODE_XSWEEP && Din) Lv[kv] += Din[gvar(kv, NV, args.vn, args.vt) * args.ncell + addr];
     }
     if (MODE == MODE_XSWEEP) {
@@ -1554,18 +1836,18 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
         ++nbad;
         firstbad = min(firstbad, (unsigned long long)addr);
       } else {
-        mymin = fmin(mymin, (double)rho);
+        mymin = fminf(mymin, rho);
         float e = gq.hi / (rho * rho);
-        float a = sqrtf(float(args.gamma * (args.gamma - 1.0)) * e);
+        float a = sqrtf(args.gg1_f * e);
         float rate;
         if (NV == 4) {
-          float hx = float(args.vn == 1 ? args.h : args.h_other);
-          float hy = float(args.vn == 1 ? args.h_other : args.h);
-          rate = (fabsf(mx / rho) + a) / hx + (fabsf(my / rho) + a) / hy;
+          const float ihx = args.vn == 1 ? args.ih_f : args.ih_other_f;
+          const float ihy = args.vn == 1 ? args.ih_other_f : args.ih_f;
+          rate = (fabsf(mx / rho) + a) * ihx + (fabsf(my / rho) + a) * ihy;
         } else {
-          rate = (fabsf(mx / rho) + a) / float(args.h);
+          rate = (fabsf(mx / rho) + a) * args.ih_f;
         }
-        mymax = fmax(mymax, (double)rate);
+        mymax = fmaxf(mymax, rate);
       }
     }
   }
@@ -1573,20 +1855,22 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   // ---------------------------------------------------------------- reduce
   // eq. (CFL-CD) checked on the face values: the stage's largest face rate
   // of this direction (max over the step's stages; NaN wins the bit max)
+  // (in the line's arithmetic: FP64 instructions cost the FP32 form 1/64 of
+  // an issue slot's worth each, and one conversion per warp suffices)
   if (MODE != MODE_OPERATOR && args.fcheck && args.eps_fixed <= 0.0) {
-    double fr = double(fsmax) * args.ih;
+    real fr = fsmax * (MIXED ? real(args.ih_f) : real(args.ih));
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
-      const double o = __shfl_down_sync(0xffffffffu, fr, d);
+      const real o = shfl_down_r(fr, d);
       if (o > fr || o != o) fr = o;
     }
-    if (lane == 0) atomic_max_bits(&ctl->frate[args.fdir], double_bits(fr));
+    if (lane == 0) atomic_max_bits(&ctl->frate[args.fdir], double_bits(double(fr)));
   }
   if (MODE == MODE_FINAL) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
-      mymin = fmin(mymin, __shfl_down_sync(0xffffffffu, mymin, d));
-      mymax = fmax(mymax, __shfl_down_sync(0xffffffffu, mymax, d));
+      mymin = fmin(mymin, shfl_down_r(mymin, d));
+      mymax = fmax(mymax, shfl_down_r(mymax, d));
       nbad += __shfl_down_sync(0xffffffffu, nbad, d);
       t1 += __shfl_down_sync(0xffffffffu, t1, d);
       t2 += __shfl_down_sync(0xffffffffu, t2, d);
@@ -1594,8 +1878,8 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
       firstbad = fb < firstbad ? fb : firstbad;
     }
     if (lane == 0) {
-      atomic_min_bits(&ctl->minrho[args.stage], double_bits(mymin));
-      if (args.stage == 2) atomic_max_bits(&ctl->rate, double_bits(mymax));
+      atomic_min_bits(&ctl->minrho[args.stage], double_bits(double(mymin)));
+      if (args.stage == 2) atomic_max_bits(&ctl->rate, double_bits(double(mymax)));
       if (nbad) {
         atomicAdd(&ctl->nviol, (unsigned long long)nbad);
         atomicMin(&ctl->first_bad, firstbad);

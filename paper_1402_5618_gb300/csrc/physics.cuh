@@ -242,7 +242,9 @@ __device__ __forceinline__ void hllc(const real *Ul, const real *Ur, real gamma,
     return;
   }
   // the star state of side K (K = l if S_M > 0, else r) and F = F_K + S_K (U*_K - U_K)
-  const real *UK = left ? Ul : Ur;
+  real UK[NV];   // element-wise selects: no run-time indexing of the arrays
+#pragma unroll
+  for (int k = 0; k < NV; ++k) UK[k] = left ? Ul[k] : Ur[k];
   const real rK = left ? rl : rr, uK = left ? ul : ur, pK = left ? pl : pr;
   const real SK = left ? SL : SR, EK = left ? El : Er, vK = left ? vl : vr;
   real Fk[NV], Us[NV];
@@ -255,6 +257,89 @@ __device__ __forceinline__ void hllc(const real *Ul, const real *Ur, real gamma,
   phys_flux_u<real, NV>(UK, uK, pK, Fk);
 #pragma unroll
   for (int k = 0; k < NV; ++k) F[k] = Fk[k] + SK * (Us[k] - UK[k]);
+}
+
+// The HLLC flux of the same two face states relative to a reference state
+// R (FP32, the mixed form): returns F_HLLC(U_l, U_r) - F(R) from the full
+// states U_K (wave speeds, signal speed smax) and their differences
+// d_K = U_K - R, arranged so that every term that reaches the result is a
+// product of a difference with an O(1) factor: its rounding is relative to
+// |U - R|, not to |F|.  With u_K - u_R = (dm_K - u_R drho_K) / rho_K and
+// p_K - p_R from (gamma-1)(dE - d(m.u)/2), the physical flux difference is
+//   d(rho u) = dm, d(rho u^2 + p) = dm u + m_R du + dp,
+//   d(rho u v) = dt u + t_R du, d((E+p) u) = (dE + dp) u + (E_R + p_R) du,
+// and the star-state jump of eq. (star-l) is proportional to S_M - u_K,
+//   S_M - u_l = (p_r - p_l - rho_r (S_R - u_r)(u_r - u_l)) / den,
+//   S_M - u_r = (p_r - p_l - rho_l (S_L - u_l)(u_r - u_l)) / den,
+// with den the denominator of S_M, p_r - p_l and u_r - u_l again from the
+// differences.  R carries (rho, m_n, [m_t,] E) and rp = (u_R, v_R, p_R,
+// E_R + p_R).  The branches and wave speeds are those of hllc().
+template <int NV>
+__device__ __forceinline__ void hllc_delta(const float *Ul, const float *Ur, const float *dl,
+                                           const float *dr, const float *R, const float *rp,
+                                           float gamma, float *dF, float &smax) {
+  const float rl = Ul[0], rr = Ur[0];
+  const float ipair = 1.0f / (rl * rr);
+  const float irl = rr * ipair, irr = rl * ipair;
+  const float ul = Ul[1] * irl, ur = Ur[1] * irr;
+  const float vl = NV == 4 ? Ul[2] * irl : 0.0f, vr = NV == 4 ? Ur[2] * irr : 0.0f;
+  const float El = Ul[NV - 1], Er = Ur[NV - 1];
+  const float g1 = gamma - 1.0f;
+  const float uR = rp[0], vR = rp[1], pR = rp[2], HR = rp[3];
+  // differences of the primitive quantities from the reference
+  const float dul = (dl[1] - uR * dl[0]) * irl, dur = (dr[1] - uR * dr[0]) * irr;
+  const float dvl = NV == 4 ? (dl[2] - vR * dl[0]) * irl : 0.0f;
+  const float dvr = NV == 4 ? (dr[2] - vR * dr[0]) * irr : 0.0f;
+  const float dmul = dl[1] * ul + R[1] * dul + (NV == 4 ? dl[2] * vl + R[2] * dvl : 0.0f);
+  const float dmur = dr[1] * ur + R[1] * dur + (NV == 4 ? dr[2] * vr + R[2] * dvr : 0.0f);
+  const float dpl = g1 * (dl[NV - 1] - 0.5f * dmul), dpr = g1 * (dr[NV - 1] - 0.5f * dmur);
+  const float pl = fmaxf(pR + dpl, 0.0f), pr = fmaxf(pR + dpr, 0.0f);
+  const float al = sqrtf(gamma * pl * irl), ar = sqrtf(gamma * pr * irr);
+  smax = fmaxf(fabsf(ul) + al, fabsf(ur) + ar);
+  const float Hl = (El + pl) * irl, Hr = (Er + pr) * irr;
+  const float Rq = sqrtf(rr * irl);
+  const float iR = 1.0f / (1.0f + Rq);
+  const float ut = (ul + ur * Rq) * iR, vt = (vl + vr * Rq) * iR, Ht = (Hl + Hr * Rq) * iR;
+  const float at = sqrtf(g1 * (Ht - 0.5f * (ut * ut + vt * vt)));
+  const float SL = fminf(ul - al, ut - at);
+  const float SR = fmaxf(ur + ar, ut + at);
+  // the physical flux difference of side K
+  auto dphys = [&](const float *d, float u, float du, float dp, float *o) {
+    o[0] = d[1];
+    o[1] = d[1] * u + R[1] * du + dp;
+    if (NV == 4) o[2] = d[2] * u + R[2] * du;
+    o[NV - 1] = (d[NV - 1] + dp) * u + HR * du;
+  };
+  if (SL > 0.0f) {
+    dphys(dl, ul, dul, dpl, dF);
+    return;
+  }
+  const float den = rl * (SL - ul) - rr * (SR - ur);
+  const float dpn = dpr - dpl, dun = dur - dul;
+  const float sml = (dpn - rr * (SR - ur) * dun) / den;   // S_M - u_l
+  const float SM = ul + sml;
+  const bool left = SM > 0.0f;
+  if (!left && !(SR >= 0.0f)) {
+    dphys(dr, ur, dur, dpr, dF);
+    return;
+  }
+  const float d = left ? sml : (dpn - rl * (SL - ul) * dun) / den;   // S_M - u_K
+  const float rK = left ? rl : rr, uK = left ? ul : ur, pK = left ? pl : pr, SK = left ? SL : SR;
+  const float vK = left ? vl : vr, EKr = left ? El * irl : Er * irr;
+  float dK[NV];   // element-wise selects: no run-time indexing of the arrays
+#pragma unroll
+  for (int k = 0; k < NV; ++k) dK[k] = left ? dl[k] : dr[k];
+  const float iss = 1.0f / (SK - SM);
+  const float Jr = rK * d * iss;                 // rho*_K - rho_K
+  const float chi = (SK - uK) * iss;
+  float J[NV];
+  J[0] = Jr;
+  J[1] = Jr * SM + rK * d;
+  if (NV == 4) J[2] = Jr * vK;
+  J[NV - 1] = EKr * Jr + chi * d * (rK * SM + pK / (SK - uK));
+  dphys(dK, uK, left ? dul : dur, left ? dpl : dpr, dF);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) dF[k] += SK * J[k];
 }
 
 // Local Lax-Friedrichs flux, the alternative Sec. 3 names for the

@@ -269,11 +269,14 @@ struct TileRef {
 };
 
 __global__ void transpose_planes_b_kernel(const float *in, float *out, const TileRef *tiles,
-                                          const ProbDesc *probs, const Ctl *gates) {
+                                          const ProbDesc *probs, long long nvals, int nv,
+                                          const Ctl *gates) {
   const TileRef t = tiles[blockIdx.x];
   if (gates && (!gates[t.prob].active || step_accepted(gates + t.prob))) return;
   const ProbDesc pd = probs[t.prob];
-  const long long o = pd.off + blockIdx.y * pd.ncell;
+  // planes 0 .. nv-1: hi parts; nv .. 2 nv - 1: the lo parts nvals behind
+  const int v = (int)blockIdx.y;
+  const long long o = (v < nv ? 0 : nvals) + pd.off + (v % nv) * pd.ncell;
   transpose_tile(in + o, out + o, t.i0, t.j0, pd.nx, pd.ny);
 }
 
@@ -286,8 +289,11 @@ __global__ void __launch_bounds__(256, 4)
                       const float *Dx, const float *DyT, float *Uoh, float *Uol, float *UT, int nx,
                       int ny, long long ncell, int stage, float ihx, float ihy, float gg1,
                       Ctl *ctl) {
-  // D_y tile [v][i][j] in, then (same element, same thread) the new hi part out
+  // D_y tile [v][i][j] in, then (same element, same thread) the new hi part
+  // out; the new lo part through its own tile (the transposed lo planes lie
+  // NV ncell behind the hi planes)
   __shared__ float tile[NV][TT][TT + 1];
+  __shared__ float tlo[NV][TT][TT + 1];
   __shared__ float red_min[8], red_max[8];
   __shared__ unsigned int red_bad[8];
   __shared__ unsigned long long red_first[8];
@@ -349,6 +355,7 @@ __global__ void __launch_bounds__(256, 4)
         Th[v][q] = un.hi;
         Tl[v][q] = un.lo;
         tile[v][4 * tx + q][ty] = un.hi;
+        tlo[v][4 * tx + q][ty] = un.lo;
       }
       *reinterpret_cast<float4 *>(Uoh + a) = make_float4(oh[0], oh[1], oh[2], oh[3]);
       *reinterpret_cast<float4 *>(Uol + a) = make_float4(ol[0], ol[1], ol[2], ol[3]);
@@ -376,10 +383,15 @@ __global__ void __launch_bounds__(256, 4)
   __syncthreads();
   if (i0 + ty < nx && j0 + 4 * tx < ny) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      *reinterpret_cast<float4 *>(UT + v * ncell + (long long)(i0 + ty) * ny + j0 + 4 * tx) =
+    for (int v = 0; v < NV; ++v) {
+      const long long at = v * ncell + (long long)(i0 + ty) * ny + j0 + 4 * tx;
+      *reinterpret_cast<float4 *>(UT + at) =
           make_float4(tile[v][ty][4 * tx], tile[v][ty][4 * tx + 1], tile[v][ty][4 * tx + 2],
                       tile[v][ty][4 * tx + 3]);
+      *reinterpret_cast<float4 *>(UT + NV * ncell + at) =
+          make_float4(tlo[v][ty][4 * tx], tlo[v][ty][4 * tx + 1], tlo[v][ty][4 * tx + 2],
+                      tlo[v][ty][4 * tx + 3]);
+    }
   }
   // block reduction: warps of 4 rows, then one set of atomics per block
   const int lin = tx + 8 * ty, wid = lin >> 5;
@@ -422,10 +434,12 @@ template <int NV, int RY>
 __device__ __forceinline__ void combine_tile(int i0, int j0, const float *Ukh, const float *Ukl,
                                              const float *U0h, const float *U0l, const float *Dx,
                                              const float *DyT, float *Uoh, float *Uol, float *UT,
-                                             int nx, int ny, long long ncell, int stage, float ihx,
-                                             float ihy, float gg1, Ctl *ctl) {
-  // D_y tile in, then (same element, same thread) the new hi part out
+                                             long long utlo, int nx, int ny, long long ncell,
+                                             int stage, float ihx, float ihy, float gg1, Ctl *ctl) {
+  // D_y tile in, then (same element, same thread) the new hi part out; the
+  // lo part through its own tile, utlo values behind the hi part in UT
   __shared__ float tile[NV][TT][TT + 1];
+  __shared__ float tlo[NV][TT][TT + 1];
   __shared__ float red_min[RY], red_max[RY];
   __shared__ unsigned int red_bad[RY];
   __shared__ unsigned long long red_first[RY];
@@ -473,6 +487,7 @@ __device__ __forceinline__ void combine_tile(int i0, int j0, const float *Ukh, c
       Th[v] = un.hi;
       Tl[v] = un.lo;
       tile[v][r][threadIdx.x] = un.hi;
+      tlo[v][r][threadIdx.x] = un.lo;
     }
     const float rho = Th[0], mx = Th[1], my = Th[2], E = Th[NV - 1];
     const dfl rE = df_mul({Th[0], Tl[0]}, {Th[NV - 1], Tl[NV - 1]});
@@ -498,7 +513,10 @@ __device__ __forceinline__ void combine_tile(int i0, int j0, const float *Ukh, c
     for (int rr = 0; rr < TT / RY; ++rr) {
       const int r = threadIdx.y + rr * RY;
       const int i = i0 + r, j = j0 + threadIdx.x;
-      if (i < nx && j < ny) UT[v * ncell + (long long)i * ny + j] = tile[v][threadIdx.x][r];
+      if (i < nx && j < ny) {
+        UT[v * ncell + (long long)i * ny + j] = tile[v][threadIdx.x][r];
+        UT[utlo + v * ncell + (long long)i * ny + j] = tlo[v][threadIdx.x][r];
+      }
     }
   // block reduction (one warp per threadIdx.y), then one set of atomics
 #pragma unroll
@@ -540,7 +558,7 @@ __global__ void __launch_bounds__(TT *RY, 6)
                      int ny, long long ncell, int stage, float ihx, float ihy, float gg1,
                      Ctl *ctl) {
   combine_tile<NV, RY>(blockIdx.x * TT, blockIdx.y * TT, Ukh, Ukl, U0h, U0l, Dx, DyT, Uoh, Uol,
-                       UT, nx, ny, ncell, stage, ihx, ihy, gg1, ctl);
+                       UT, NV * ncell, nx, ny, ncell, stage, ihx, ihy, gg1, ctl);
 }
 
 // batched problems: one block per tile of a problem, each problem at its
@@ -549,13 +567,13 @@ template <int NV, int RY>
 __global__ void __launch_bounds__(TT *RY, 6)
     combine_tb_kernel(const float *Ukh, const float *Ukl, const float *U0h, const float *U0l,
                       const float *Dx, const float *DyT, float *Uoh, float *Uol, float *UT,
-                      const TileRef *tiles, const ProbDesc *probs, int stage, float gg1,
-                      Ctl *ctls) {
+                      long long nvals_all, const TileRef *tiles, const ProbDesc *probs, int stage,
+                      float gg1, Ctl *ctls) {
   const TileRef t = tiles[blockIdx.x];
   const ProbDesc pd = probs[t.prob];
   const long long o = pd.off;
   combine_tile<NV, RY>(t.i0, t.j0, Ukh + o, Ukl + o, U0h + o, U0l + o, Dx + o, DyT + o, Uoh + o,
-                       Uol + o, UT + o, pd.nx, pd.ny, pd.ncell, stage, (float)pd.idx,
+                       Uol + o, UT + o, nvals_all, pd.nx, pd.ny, pd.ncell, stage, (float)pd.idx,
                        (float)pd.idy, gg1, ctls + t.prob);
 }
 
@@ -788,6 +806,13 @@ cudaError_t dispatch(const pp_cweno_s *h, int mode, bool periodic, const SweepAr
   SweepArgs b = a;
   b.ih = a.h > 0.0 ? 1.0 / a.h : 0.0;   // batched launches take it per problem
   b.ih_other = a.h_other > 0.0 ? 1.0 / a.h_other : 0.0;
+  b.ih_f = (float)b.ih;
+  b.ih_other_f = (float)b.ih_other;
+  b.gamma_f = (float)a.gamma;
+  b.wgl_f = (float)a.wgl;
+  b.eps_weno_f = (float)a.eps_weno;
+  b.gg1_f = (float)(a.gamma * (a.gamma - 1.0));
+  b.eps_fixed_f = (float)a.eps_fixed;
   return launch_sweep(c, b, nlines, st_override ? st_override : h->stream);
 }
 
@@ -908,6 +933,7 @@ cudaError_t launch_ysweep_t(const pp_cweno_s *h, int stage) {
   SweepArgs a;
   memset(&a, 0, sizeof(a));
   a.Uh = h->UT;
+  a.Ul = h->UT + nvals(h);
   fill_common(h, a, stage, 0.0, h->ctl);
   a.Dout = h->DT;
   a.ncell = h->ncell;
@@ -951,8 +977,8 @@ cudaError_t launch_combine_b(const pp_cweno_s *h, const void *Uin, void *Uout, i
   const float *U0h = hi_of(h->U0), *U0l = lo_of(h, h->U0);
   float *Uoh = hi_of(Uout), *Uol = lo_of(h, Uout);
   combine_tb_kernel<4, 8><<<(unsigned)h->ntiles, dim3(TT, 8), 0, h->stream>>>(
-      Ukh, Ukl, U0h, U0l, reinterpret_cast<const float *>(h->D), h->DT, Uoh, Uol, h->UT, h->tiles,
-      h->probs, stage, (float)(h->cfg.gamma * (h->cfg.gamma - 1.0)), h->ctl);
+      Ukh, Ukl, U0h, U0l, reinterpret_cast<const float *>(h->D), h->DT, Uoh, Uol, h->UT, nvals(h),
+      h->tiles, h->probs, stage, (float)(h->cfg.gamma * (h->cfg.gamma - 1.0)), h->ctl);
   return cudaGetLastError();
 }
 
@@ -961,11 +987,14 @@ cudaError_t launch_combine_b(const pp_cweno_s *h, const void *Uin, void *Uout, i
 cudaError_t transpose_state_hi(const pp_cweno_s *h, bool gated = false) {
   const Ctl *gate = gated ? h->ctl : nullptr;
   if (h->btrans) {
-    transpose_planes_b_kernel<<<dim3((unsigned)h->ntiles, (unsigned)h->nv), dim3(TT, 8), 0,
-                                h->stream>>>(hi_of(h->U0), h->UT, h->tiles, h->probs, gate);
+    transpose_planes_b_kernel<<<dim3((unsigned)h->ntiles, (unsigned)(2 * h->nv)), dim3(TT, 8), 0,
+                                h->stream>>>(hi_of(h->U0), h->UT, h->tiles, h->probs, nvals(h),
+                                             h->nv, gate);
     return cudaGetLastError();
   }
-  dim3 grid((unsigned)((h->nx + TT - 1) / TT), (unsigned)((h->ny + TT - 1) / TT), (unsigned)h->nv);
+  // the hi planes and the lo planes behind them, 2 nv planes in one launch
+  dim3 grid((unsigned)((h->nx + TT - 1) / TT), (unsigned)((h->ny + TT - 1) / TT),
+            (unsigned)(2 * h->nv));
   transpose_planes_kernel<<<grid, dim3(TT, 8), 0, h->stream>>>(hi_of(h->U0), h->UT, (int)h->nx,
                                                                (int)h->ny, h->ncell, gate);
   return cudaGetLastError();
@@ -1197,7 +1226,9 @@ int finish_create(pp_cweno_s *h) {
   h->ytrans = is_mixed(h) && h->nv == 4 && !h->batch;
   h->fcheck = h->cfg.cfl_positivity_cap != 0;
   const bool tr = h->ytrans || h->btrans;
-  if (e == cudaSuccess && tr) e = cudaMalloc(&h->UT, sizeof(float) * (size_t)nvals(h));
+  // transposed hi planes, then the transposed lo planes (the y sweep's
+  // difference form reads both)
+  if (e == cudaSuccess && tr) e = cudaMalloc(&h->UT, 2 * sizeof(float) * (size_t)nvals(h));
   if (e == cudaSuccess && tr) e = cudaMalloc(&h->DT, sizeof(float) * (size_t)nvals(h));
   if (e == cudaSuccess && h->cfg.recon == PP_RECON_CHARACTERISTIC) {
     const size_t es = is_mixed(h) ? sizeof(float) : sizeof(double);
