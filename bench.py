@@ -339,13 +339,18 @@ def run_native(args, ws, rank, local):
         # the whole seeded 1-D set (the 168 problems whose exact solution
         # opens a vacuum included) and the 2-D four-quadrant set, at the
         # positivity CFL with eq. (CFL-CD) checked on the face values
-        for name, probs, steps in (("riemann_1d", W.riemann_batch(), 20),
-                                   ("quadrant_2d", W.quadrant_batch(), 6)):
+        # (the 1-D set also in the characteristic-wise form: its data are
+        # all discontinuous)
+        rb = W.riemann_batch()
+        for name, probs, steps, recon in (("riemann_1d", rb, (20, 20), 0),
+                                          ("quadrant_2d", W.quadrant_batch(), (6, 6), 0),
+                                          ("riemann_1d_characteristic", rb, (10, 3), 1)):
             U0b = np.concatenate([np.ascontiguousarray(q.U0).ravel() for q in probs])
             cells = np.array([q.nx * q.ny for q in probs], dtype=np.float64)
             row = {"problems": len(probs), "cells": int(cells.sum())}
-            for prec, pname in ((1, "mixed"), (0, "fp64")):
-                sb = B.Solver(None, batch=[B.config_from_problem(q, prec, cfl_positivity_cap=True)
+            for prec, pname, steps in ((1, "mixed", steps[0]), (0, "fp64", steps[1])):
+                sb = B.Solver(None, batch=[B.config_from_problem(q, prec, cfl_positivity_cap=True,
+                                                                 recon=recon)
                                            for q in probs], stream=stream)
                 sb.set_state(U0b)
                 sb.enqueue_steps(3)
@@ -561,7 +566,9 @@ def main():
                                        "(omega_1/2 = 1/24, eq. (CFL-CD) checked on the face values, "
                                        "value over accepted steps): all 4096 1-D Riemann problems "
                                        "of 256-8192 cells (168 open an exact vacuum), 256 2-D "
-                                       "four-quadrant problems of 128^2-1024^2", **out["batches"]}
+                                       "four-quadrant problems of 128^2-1024^2; the 1-D set also "
+                                       "with the characteristic-wise reconstruction of Sec. 2.3",
+                               **out["batches"]}
         if out["characteristic"]:
             line["characteristic"] = {"note": "the same 4096^2 blast with the characteristic-wise "
                                               "reconstruction of Sec. 2.3 (block tridiagonal "

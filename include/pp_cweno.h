@@ -72,12 +72,15 @@ typedef enum {
                                   face: one block tridiagonal system per side, blocks
                                   diag(a, b, c) L (Sec. 2.3, eq. (1DEuler-FVC)),
                                   in the line arithmetic of either precision.
-                                  Single problems only (PP_ERR_UNSUPPORTED for
-                                  batches and pp_cweno_operator_noalloc); needs
+                                  Single problems and batches
+                                  (PP_ERR_UNSUPPORTED for
+                                  pp_cweno_operator_noalloc); needs
                                   2 (n (nv^2 + nv) + nv^2) values per line of
                                   scratch per sweep direction (periodic: nv^2 +
                                   nv (nv+1) per row; FP64, or FP32 for the mixed
-                                  form) */
+                                  form), plus 2 (4 nv + 4) n values of row
+                                  data; a batch sizes both per group of lines
+                                  by the group's longest line */
 } pp_recon_t;
 
 enum {
@@ -143,9 +146,8 @@ int pp_cweno_create(const pp_cweno_config *cfg, void *cuda_stream, pp_cweno_t *o
 
 /* Create one handle for nprob independent problems advanced together (each
  * with its own time step).  All configs must share ndim, gamma, precision,
- * the limiter settings and the flux, and use the component-wise
- * reconstruction (PP_ERR_UNSUPPORTED otherwise); sizes, domains, boundaries
- * and cfl may differ. */
+ * the limiter settings, the flux and the reconstruction (PP_ERR_ARG
+ * otherwise); sizes, domains, boundaries and cfl may differ. */
 int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda_stream,
                           pp_cweno_t *out);
 

@@ -25,6 +25,8 @@
 
 #include <cuda_runtime.h>
 
+#include "batch_lines.cuh"
+
 namespace ppk {
 
 struct CharArgs {
@@ -36,10 +38,16 @@ struct CharArgs {
   long long ncell;          // cells per variable plane
   long long nlines;
   long long cell_stride, line_stride;
-  int n;                    // cells per line
+  int n;                    // cells per line; batched: the longest line (position stride of rows, scr)
   int vn, vt;               // grid index of the normal / tangential momentum (vt < 0 in 1-D)
   int bclo, bchi;
   double gamma, eps_weno;
+  // batched launch (nullptr: one problem): the group's line table and the
+  // problem descriptors; each line takes its length, boundaries and slice
+  // of U, Um, Up from its problem
+  const LineRef *lines;
+  const ProbDesc *probs;
+  int xdir;                 // batched: 1 x lines, 0 y lines (columns), 2 rows of the transposed planes
 };
 
 // values of one row of the scratch: the multiplier block Y (nv x nv) and
@@ -48,8 +56,8 @@ inline long long char_row_values(int nv, bool periodic) {
   return (long long)nv * nv + (long long)nv * (periodic ? nv + 1 : 1);
 }
 
-// scratch for lines of n cells: both sides, n rows each plus one block per
-// line-side for the Woodbury coupling matrix
+// scratch for lines of (at most) n cells: both sides, n rows each plus one
+// block per line-side for the Woodbury coupling matrix
 inline long long char_scratch_values(int nv, bool periodic, long long n, long long nlines) {
   return 2 * (n * char_row_values(nv, periodic) + (long long)nv * nv) * nlines;
 }

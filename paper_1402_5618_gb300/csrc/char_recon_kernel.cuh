@@ -156,17 +156,51 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// geometry of one line: its first cell's offset in the planes, cell stride,
+// plane size, length and boundary kinds (a batched line from its problem)
+struct LineGeo {
+  long long base, cs, ncell;
+  int n, bclo, bchi;
+};
+
+__device__ __forceinline__ LineGeo line_geo(const CharArgs &a, long long line) {
+  LineGeo g;
+  if (!a.lines) {
+    g.base = line * a.line_stride;
+    g.cs = a.cell_stride;
+    g.ncell = a.ncell;
+    g.n = a.n;
+    g.bclo = a.bclo;
+    g.bchi = a.bchi;
+    return g;
+  }
+  const LineRef lr = a.lines[line];
+  const ProbDesc pd = a.probs[lr.prob];
+  g.ncell = pd.ncell;
+  if (a.xdir == 1) {
+    g.n = pd.nx; g.cs = 1; g.base = pd.off + (long long)lr.line * pd.nx;
+    g.bclo = pd.bc[0]; g.bchi = pd.bc[1];
+  } else if (a.xdir == 2) {   // a row of the problem's transposed planes: a y line
+    g.n = pd.ny; g.cs = 1; g.base = pd.off + (long long)lr.line * pd.ny;
+    g.bclo = pd.bc[2]; g.bchi = pd.bc[3];
+  } else {
+    g.n = pd.ny; g.cs = pd.nx; g.base = pd.off + lr.line;
+    g.bclo = pd.bc[2]; g.bchi = pd.bc[3];
+  }
+  return g;
+}
+
 // ghost-aware read of the line variables of line cell i (both kernels)
 template <typename real, int NV, bool PER>
-__device__ __forceinline__ void line_cell(const CharArgs &a, const real *U, long long lbase,
-                                          const int (&gv)[NV], int i, real (&out)[NV]) {
-  const int n = a.n;
+__device__ __forceinline__ void line_cell(const LineGeo &g, const real *U, const int (&gv)[NV],
+                                          int i, real (&out)[NV]) {
+  const int n = g.n;
   bool neg = false;
   if (i < 0 || i >= n) {
     if (PER) {
       i = (i % n + n) % n;
     } else {
-      const int bc = i < 0 ? a.bclo : a.bchi;
+      const int bc = i < 0 ? g.bclo : g.bchi;
       if (bc == 1) {
         i = i < 0 ? 0 : n - 1;
       } else {
@@ -175,9 +209,9 @@ __device__ __forceinline__ void line_cell(const CharArgs &a, const real *U, long
       }
     }
   }
-  const real *src = U + lbase + (long long)i * a.cell_stride;
+  const real *src = U + g.base + (long long)i * g.cs;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = src[gv[k] * a.ncell];
+  for (int k = 0; k < NV; ++k) out[k] = src[gv[k] * g.ncell];
   if (neg) out[1] = -out[1];
 }
 
@@ -206,7 +240,8 @@ __global__ void __launch_bounds__(256) char_rows_kernel(const CharArgs a) {
   constexpr int RC = 4 * NV + 4;
   constexpr int TW = CT_C + 4;        // cells of a tile row with the halo
   __shared__ real tile[NV][CT_L][TW + 1];
-  const int n = a.n;
+  __shared__ LineGeo sg[CT_L];
+  const int NMAX = a.n;               // position stride of the rows buffer
   const long long NL = a.nlines;
   const long long line0 = (long long)blockIdx.x * CT_L;
   const int c0 = blockIdx.y * CT_C;
@@ -214,14 +249,18 @@ __global__ void __launch_bounds__(256) char_rows_kernel(const CharArgs a) {
   int gv[NV];
   grid_vars<NV>(a, gv);
   const int tid = threadIdx.x;
-  const bool along_cells = a.cell_stride == 1;
+  if (tid < CT_L && line0 + tid < NL) sg[tid] = line_geo(a, line0 + tid);
+  __syncthreads();
+  const bool along_cells = a.lines ? a.xdir != 0 : a.cell_stride == 1;
   for (int idx = tid; idx < CT_L * TW; idx += blockDim.x) {
     const int ll = along_cells ? idx / TW : idx % CT_L;
     const int j = along_cells ? idx % TW : idx / CT_L;
     const int i = c0 - 2 + j;
-    if (line0 + ll >= NL || i < -2 || i > n + 1) continue;   // never read
+    if (line0 + ll >= NL) continue;
+    const LineGeo g = sg[ll];
+    if (i < -2 || i > g.n + 1) continue;   // never read
     real v[NV];
-    line_cell<real, NV, PER>(a, U, (line0 + ll) * a.line_stride, gv, i, v);
+    line_cell<real, NV, PER>(g, U, gv, i, v);
 #pragma unroll
     for (int k = 0; k < NV; ++k) tile[k][ll][j] = v[k];
   }
@@ -229,6 +268,7 @@ __global__ void __launch_bounds__(256) char_rows_kernel(const CharArgs a) {
   const int ll = tid % CT_L;
   const long long line = line0 + ll;
   if (line >= NL) return;
+  const int n = sg[ll].n;
   real *rows = reinterpret_cast<real *>(a.rows);
   const real gam = real(a.gamma), eps = real(a.eps_weno);
   for (int q = tid / CT_L; q < 2 * CT_C; q += blockDim.x / CT_L) {
@@ -247,7 +287,7 @@ __global__ void __launch_bounds__(256) char_rows_kernel(const CharArgs a) {
     roe_scalars<real, NV>(win[2], win[3], gam, rs);
     left_from<real, NV>(rs, L);
     const bool closure = !PER && (p == 0 || p == n - 1);
-    real *dst = rows + ((long long)side * n + p) * RC * NL + line;
+    real *dst = rows + ((long long)side * NMAX + p) * RC * NL + line;
 #pragma unroll
     for (int e = 0; e < 4; ++e) dst[e * NL] = rs[e];
 #pragma unroll
@@ -316,13 +356,15 @@ __global__ void __launch_bounds__(32) char_solve_kernel(const CharArgs a) {
   const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= a.nlines) return;
   const int side = blockIdx.y;
-  const int n = a.n;
+  const LineGeo geo = line_geo(a, line);
+  const int n = geo.n;
+  const int NMAX = a.n;   // position stride of rows and scratch
   const long long NL = a.nlines;
-  const long long lbase = line * a.line_stride;
-  const real *rows = reinterpret_cast<const real *>(a.rows) + (long long)side * n * RC * NL + line;
-  real *scr = reinterpret_cast<real *>(a.scr) + (long long)side * ((long long)n * ROW + NV * NV) * NL + line;
+  const long long lbase = geo.base;
+  const real *rows = reinterpret_cast<const real *>(a.rows) + (long long)side * NMAX * RC * NL + line;
+  real *scr = reinterpret_cast<real *>(a.scr) + (long long)side * ((long long)NMAX * ROW + NV * NV) * NL + line;
   auto slot = [&](int p, int e) -> real & { return scr[((long long)p * ROW + e) * NL]; };
-  auto wslot = [&](int e) -> real & { return scr[((long long)n * ROW + e) * NL]; };
+  auto wslot = [&](int e) -> real & { return scr[((long long)NMAX * ROW + e) * NL]; };
   int gv[NV];
   grid_vars<NV>(a, gv);
   auto cidx = [&](int p) { return side == 0 ? p : n - 1 - p; };
@@ -513,9 +555,9 @@ __global__ void __launch_bounds__(32) char_solve_kernel(const CharArgs a) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) slot(p, NV * NV + k * NC + c) = x[k][c];
     } else {
-      real *dst = out + lbase + (long long)cidx(p) * a.cell_stride;
+      real *dst = out + lbase + (long long)cidx(p) * geo.cs;
 #pragma unroll
-      for (int k = 0; k < NV; ++k) dst[gv[k] * a.ncell] = x[k][0];
+      for (int k = 0; k < NV; ++k) dst[gv[k] * geo.ncell] = x[k][0];
     }
   }
   cp_async_wait<0>();
@@ -544,13 +586,13 @@ __global__ void __launch_bounds__(32) char_solve_kernel(const CharArgs a) {
     gauss_solve<real, NV, 1>(S, t);
 #pragma unroll 1
     for (int p = 0; p < n; ++p) {
-      real *dst = out + lbase + (long long)cidx(p) * a.cell_stride;
+      real *dst = out + lbase + (long long)cidx(p) * geo.cs;
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         real s = slot(p, NV * NV + k * NC);
 #pragma unroll
         for (int j = 0; j < NV; ++j) s -= slot(p, NV * NV + k * NC + 1 + j) * t[j][0];
-        dst[gv[k] * a.ncell] = s;
+        dst[gv[k] * geo.ncell] = s;
       }
     }
   }

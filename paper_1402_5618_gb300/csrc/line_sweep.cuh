@@ -38,6 +38,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "batch_lines.cuh"
 #include "dfloat.cuh"
 #include "physics.cuh"
 
@@ -74,21 +75,6 @@ struct Ctl {
 };
 
 enum { MODE_XSWEEP = 0, MODE_FINAL = 1, MODE_OPERATOR = 2 };
-
-// one problem of a batch: its block of the concatenated state (values
-// [off, off + nv*ncell), variable planes of ncell cells) and grid
-struct ProbDesc {
-  long long off, ncell;
-  int nx, ny;
-  double dx, dy;
-  double idx, idy;    // 1/dx, 1/dy
-  int bc[4];
-};
-
-// one line of a batched launch: problem index and line index inside it
-struct LineRef {
-  int prob, line;
-};
 
 struct SweepArgs {
   // plain form: FP64 planes [nv][ncell]
@@ -134,7 +120,7 @@ struct SweepArgs {
 
 // resolve the line a cluster works on: for a batched launch, take the
 // problem's grid, boundaries, control block and its slice of every buffer
-template <int NV>
+template <typename real, int NV>
 __device__ __forceinline__ void bind_line(SweepArgs &a, long long &line) {
   if (!a.lines) return;
   LineRef lr = a.lines[line];
@@ -166,6 +152,10 @@ __device__ __forceinline__ void bind_line(SweepArgs &a, long long &line) {
   if (a.U0h) { a.U0h += o; a.U0l = a.U0h + a.nvals; }
   if (a.Uoh) { a.Uoh += o; a.Uol = a.Uoh + a.nvals; }
   if (a.Lout) a.Lout += o;
+  if (a.Fm_pre) {   // face values of the characteristic-wise reconstruction, same layout
+    a.Fm_pre = reinterpret_cast<const real *>(a.Fm_pre) + o;
+    a.Fp_pre = reinterpret_cast<const real *>(a.Fp_pre) + o;
+  }
 }
 
 // ---------------------------------------------------------------- maps
@@ -569,7 +559,7 @@ __global__ void __launch_bounds__(NV * (SEGC / M),
   const int R = args.R;
   const int rank = (int)cluster.block_rank();
   long long line = blockIdx.x / R;
-  bind_line<NV>(args, line);
+  bind_line<real, NV>(args, line);
   if (args.lines) {   // D buffers follow the state layout of the batch
     const long long o = args.probs[args_in.lines[blockIdx.x / R].prob].off;
     if (args.Din) args.Din = reinterpret_cast<const real *>(args.Din) + o;

@@ -651,6 +651,11 @@ struct LineGroup {
   bool trans = false;         // y lines as rows of the transposed planes (mixed 2-D batches)
   LineRef *lines = nullptr;   // device
   long long nlines = 0;
+  // characteristic-wise batches: the longest line of the group and the
+  // group's own row and block-solve scratch (groups of a direction run
+  // concurrently)
+  int nmax = 0;
+  void *cscr = nullptr, *crows = nullptr;
 };
 
 struct pp_cweno_s {
@@ -823,6 +828,7 @@ cudaError_t dispatch(const pp_cweno_s *h, int mode, bool periodic, const SweepAr
 cudaError_t launch_char(const pp_cweno_s *h, const SweepArgs &a, const void *U, long long nlines) {
   if (h->cfg.recon != PP_RECON_CHARACTERISTIC) return cudaSuccess;
   CharArgs c;
+  memset(&c, 0, sizeof(c));   // lines = nullptr: one problem
   c.U = U;
   c.Um = const_cast<void *>(a.Fm_pre);
   c.Up = const_cast<void *>(a.Fp_pre);
@@ -846,6 +852,33 @@ cudaError_t launch_char(const pp_cweno_s *h, const SweepArgs &a, const void *U, 
                     : launch_char_recon_f64(c, h->nv, per, part, h->stream);
     if (e == cudaSuccess && h->mark_hook) h->mark_hook();
   }
+  return e;
+}
+
+// The same for one line group of a batch, on the group's stream: every line
+// takes its problem's length, boundaries and slice of the planes
+cudaError_t launch_char_group(const pp_cweno_s *h, const LineGroup &g, const SweepArgs &a,
+                              const void *U, cudaStream_t st) {
+  CharArgs c;
+  memset(&c, 0, sizeof(c));
+  c.U = U;
+  c.Um = const_cast<void *>(a.Fm_pre);
+  c.Up = const_cast<void *>(a.Fp_pre);
+  c.scr = g.cscr;
+  c.rows = g.crows;
+  c.nlines = g.nlines;
+  c.n = g.nmax;
+  c.vn = a.vn;
+  c.vt = a.vt;
+  c.gamma = h->cfg.gamma;
+  c.eps_weno = h->cfg.eps_weno;
+  c.lines = g.lines;
+  c.probs = h->probs;
+  c.xdir = a.xdir;
+  cudaError_t e = cudaSuccess;
+  for (int part = 0; part < 2 && e == cudaSuccess; ++part)
+    e = is_mixed(h) ? launch_char_recon_f32(c, h->nv, g.periodic, part, st)
+                    : launch_char_recon_f64(c, h->nv, g.periodic, part, st);
   return e;
 }
 
@@ -924,6 +957,11 @@ cudaError_t launch_group(const pp_cweno_s *h, const LineGroup &g, int mode, cons
   a.vn = g.xdir ? 1 : 2;
   a.vt = h->nv == 4 ? (g.xdir ? 2 : 1) : -1;
   a.fdir = g.xdir ? 0 : 1;
+  if (!attrs_only && h->cfg.recon == PP_RECON_CHARACTERISTIC) {
+    cudaError_t e = launch_char_group(h, g, a, is_mixed(h) ? (const void *)a.Uh : (const void *)a.U,
+                                      st ? st : h->stream);
+    if (e != cudaSuccess) return e;
+  }
   return dispatch(h, mode, g.periodic, a, g.nlines, attrs_only, st);
 }
 
@@ -1230,7 +1268,15 @@ int finish_create(pp_cweno_s *h) {
   // difference form reads both)
   if (e == cudaSuccess && tr) e = cudaMalloc(&h->UT, 2 * sizeof(float) * (size_t)nvals(h));
   if (e == cudaSuccess && tr) e = cudaMalloc(&h->DT, sizeof(float) * (size_t)nvals(h));
-  if (e == cudaSuccess && h->cfg.recon == PP_RECON_CHARACTERISTIC) {
+  if (e == cudaSuccess && h->cfg.recon == PP_RECON_CHARACTERISTIC && h->batch) {
+    const size_t es = is_mixed(h) ? sizeof(float) : sizeof(double);
+    e = cudaMalloc(&h->UMP, 2 * es * (size_t)nvals(h));
+    for (LineGroup &g : h->groups) {
+      if (e != cudaSuccess) break;
+      e = cudaMalloc(&g.cscr, es * (size_t)char_scratch_values(h->nv, g.periodic, g.nmax, g.nlines));
+      if (e == cudaSuccess) e = cudaMalloc(&g.crows, es * (size_t)char_rows_values(h->nv, g.nmax, g.nlines));
+    }
+  } else if (e == cudaSuccess && h->cfg.recon == PP_RECON_CHARACTERISTIC) {
     const size_t es = is_mixed(h) ? sizeof(float) : sizeof(double);
     e = cudaMalloc(&h->UMP, 2 * es * (size_t)nvals(h));
     long long sx = char_scratch_values(h->nv, h->cfg.bc[0] == PP_BC_PERIODIC, h->nx, h->ny);
@@ -1262,8 +1308,9 @@ int finish_create(pp_cweno_s *h) {
   if (e != cudaSuccess) return PP_ERR_CUDA;
   if (h->batch) {
     h->launches_per_step = 1;
+    const long long per_group = h->cfg.recon == PP_RECON_CHARACTERISTIC ? 3 : 1;
     for (int s = 0; s < 3; ++s)
-      h->launches_per_step += (long long)h->groups.size() + (h->btrans ? 1 : 0);
+      h->launches_per_step += per_group * (long long)h->groups.size() + (h->btrans ? 1 : 0);
   } else {
     const int sweeps = h->nv == 4 ? 2 : 1;
     const int chars = h->cfg.recon == PP_RECON_CHARACTERISTIC ? 2 * sweeps : 0;
@@ -1296,6 +1343,10 @@ std::vector<std::pair<TuneKey, int>> g_tune_cache;
 // buffer as operator output).  Batches are not cached: their line mix is
 // their own.
 int autotune_batch(pp_cweno_s *h) {
+  if (h->cfg.recon == PP_RECON_CHARACTERISTIC) {   // its line kernels have no elimination to tune
+    h->m = 8;
+    return PP_OK;
+  }
   std::vector<Ctl> z((size_t)h->nprob);
   memset(z.data(), 0, sizeof(Ctl) * z.size());
   if (cudaMemcpyAsync(h->ctl_scratch, z.data(), sizeof(Ctl) * z.size(), cudaMemcpyHostToDevice,
@@ -1448,7 +1499,6 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
         c.limiter != c0.limiter || c.flux != c0.flux || c.recon != c0.recon ||
         c.cfl_positivity_cap != c0.cfl_positivity_cap)
       return PP_ERR_ARG;
-    if (c.recon != PP_RECON_COMPONENT) return PP_ERR_UNSUPPORTED;
   }
   pp_cweno_s *h = new (std::nothrow) pp_cweno_s();
   if (!h) return PP_ERR_CUDA;
@@ -1522,7 +1572,19 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
   if (e == cudaSuccess)
     e = cudaMemcpy(h->probs, h->probs_h.data(), sizeof(ProbDesc) * h->nprob, cudaMemcpyHostToDevice);
   for (size_t g = 0; g < h->groups.size() && e == cudaSuccess; ++g) {
+    // longest lines first: the last wave of a launch holds the short ones,
+    // and neighbouring lines (one warp of the characteristic solve) have
+    // nearly equal lengths; a problem's lines stay together
+    const bool gx = h->groups[g].xdir;
+    std::stable_sort(slines[g].begin(), slines[g].end(), [&](const LineRef &x, const LineRef &y) {
+      const ProbDesc &dx_ = h->probs_h[x.prob], &dy_ = h->probs_h[y.prob];
+      return (gx ? dx_.nx : dx_.ny) > (gx ? dy_.nx : dy_.ny);
+    });
     h->groups[g].nlines = (long long)slines[g].size();
+    for (const LineRef &lr : slines[g]) {
+      const ProbDesc &d = h->probs_h[lr.prob];
+      h->groups[g].nmax = std::max(h->groups[g].nmax, h->groups[g].xdir ? d.nx : d.ny);
+    }
     e = cudaMalloc(&h->groups[g].lines, sizeof(LineRef) * slines[g].size());
     if (e == cudaSuccess)
       e = cudaMemcpy(h->groups[g].lines, slines[g].data(), sizeof(LineRef) * slines[g].size(),
@@ -2034,7 +2096,11 @@ int pp_cweno_destroy(pp_cweno_t h) {
   cudaFree(h->UMP);
   cudaFree(h->cscr);
   cudaFree(h->crows);
-  for (auto &g : h->groups) cudaFree(g.lines);
+  for (auto &g : h->groups) {
+    cudaFree(g.lines);
+    cudaFree(g.cscr);
+    cudaFree(g.crows);
+  }
   for (cudaStream_t st : h->gstreams) cudaStreamDestroy(st);
   for (cudaEvent_t ev : h->gevents) cudaEventDestroy(ev);
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);

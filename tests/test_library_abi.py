@@ -73,15 +73,17 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
 
 
 def test_characteristic_form_limits():
-    """The characteristic-wise form serves single problems: an unknown
-    selector is PP_ERR_ARG and batches PP_ERR_UNSUPPORTED, both decided
-    before any device call (the allocation-free operator's refusal is
-    checked with real device buffers in the GPU tests)."""
+    """Reconstruction selectors are checked before any device call: an
+    unknown one is PP_ERR_ARG, and so is a batch whose problems mix the
+    component-wise and characteristic-wise forms (the allocation-free
+    operator's refusal of the characteristic form is checked with real
+    device buffers in the GPU tests)."""
     L = binding.lib()
     h = ctypes.c_void_p()
     c = binding.make_config(recon=2)
     assert L.pp_cweno_create(ctypes.byref(c), None, ctypes.byref(h)) == binding.PP_ERR_ARG
-    c = binding.make_config(recon=binding.RECON_CHARACTERISTIC)
-    arr = (binding.Config * 2)(c, c)
-    assert L.pp_cweno_create_batch(arr, 2, None, ctypes.byref(h)) == binding.PP_ERR_UNSUPPORTED
+    c0 = binding.make_config(recon=binding.RECON_COMPONENT)
+    c1 = binding.make_config(recon=binding.RECON_CHARACTERISTIC)
+    arr = (binding.Config * 2)(c1, c0)
+    assert L.pp_cweno_create_batch(arr, 2, None, ctypes.byref(h)) == binding.PP_ERR_ARG
     assert not h.value

@@ -126,3 +126,38 @@ def test_vacuum_subset_stays_in_G():
         U, t, steps, _, cnt, rc = oracle.advance(_grid(q, W1), q.U0, CFL, 1e9, max_steps=40)
         assert rc == -2 and steps == 40, q.name
         assert _in_G(U), q.name
+
+
+def test_face_check_stalls_at_a_floor_face_value():
+    """The cost of the face check near a vacuum: on problem 44 of the set (a
+    double rarefaction whose centre cell holds rho = 0.02) the limited face
+    values include one of density ~1e-9 that keeps its energy as kinetic
+    energy, so |u| = sqrt(2 E / rho) ~ 1e4 - 1e5; the checked dt then
+    collapses while every cell average stays tame.  Without the check the
+    same problem leaves G (a stage produces a cell outside it): the scheme
+    as read either stalls or loses positivity here."""
+    q = W.riemann_batch()[44]
+    g = oracle.make_grid(1, q.nx, 1, q.dx, 1.0, q.gamma, q.bc, face_cfl=W1)
+    U, t, steps, dt, cnt, rc = oracle.advance(g, q.U0, W1 / 2, 0.15, max_steps=300)
+    assert rc == -2 and steps == 300
+    assert t < 1e-3 and dt < 1e-8 and cnt.face_rate > 1e6
+    assert _in_G(U) and U[0].min() > 0.02
+    # the averages' rate alone: orders of magnitude below the face rate
+    assert oracle.max_rate(g, U) < 1e4
+    # the limited face values: one near the floor whose energy is kinetic
+    ext = np.concatenate([U[:, :1], U[:, :1], U, U[:, -1:], U[:, -1:]], axis=1)
+    um, up = np.zeros_like(U), np.zeros_like(U)
+    for v in range(3):
+        um[v], up[v] = oracle.recon_scalar(ext[v], False)
+    eps = min(1e-13, float(U[0].min()))
+    for j in range(q.nx):
+        um[:, j], up[:, j], _ = oracle.limit_cell(U[:, j], um[:, j], up[:, j], eps, q.gamma)
+    F = np.concatenate([um, up], axis=1)
+    rho = F[0]
+    pr = (q.gamma - 1.0) * (F[2] - 0.5 * F[1] ** 2 / rho)
+    k = int(np.argmin(rho))
+    assert rho[k] < 1e-8 and pr[k] > 0 and abs(F[1, k] / rho[k]) > 1e4
+    assert abs(F[1, k] / rho[k]) > 100 * np.sqrt(q.gamma * pr[k] / rho[k])
+    g0 = _grid(q)
+    U0, t0, s0, *_, rc0 = oracle.advance(g0, q.U0, W1 / 2, 0.01)
+    assert rc0 == -1 and t0 < 0.01
