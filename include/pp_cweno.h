@@ -80,7 +80,11 @@ typedef enum {
                                   nv (nv+1) per row; FP64, or FP32 for the mixed
                                   form), plus 2 (4 nv + 4) n values of row
                                   data; a batch sizes both per group of lines
-                                  by the group's longest line */
+                                  by the group's longest line; a mixed 2-D
+                                  problem keeps both directions' (and a
+                                  second set of face-value planes), its y
+                                  reconstruction running on a second stream
+                                  beside the x sweep */
 } pp_recon_t;
 
 enum {
