@@ -194,11 +194,11 @@ ALU_PEAK_TFLOPS = {1: 152 * 128 * 2 * 2.07e9 / 1e12, 0: 1.25}
 # what is still dirty in L2 when the kernel ends.  The FP64 form's dominant
 # kernel is its y sweep, for which no capture of these sources exists.
 TRAFFIC_PER_CELL = {            # {(precision, kernel): bytes per cell}
-    (1, "x_sweep"): 28.37,
-    (0, "x_sweep"): 59.63,
+    (1, "x_sweep"): 28.33,
+    (0, "x_sweep"): 59.64,
 }
-TRAFFIC_SRC_SHA256 = "26c3e81181a2accd54879cc986f5e4348e23b3c30f4397fa9b33ed0e4e36194a"
-KERNEL_SOURCES = ("line_sweep.cuh", "physics.cuh", "dfloat.cuh")
+TRAFFIC_SRC_SHA256 = "125b6e168b43838d09caa6c191c5d38175b8c94383bd35a6e8e9d3d6b2b84e5a"
+KERNEL_SOURCES = ("line_sweep.cuh", "physics.cuh", "dfloat.cuh", "batch_lines.cuh")
 
 
 def _kernel_src_sha256() -> str:
@@ -455,9 +455,37 @@ def _cpu_baseline(seconds_target: float = 20.0):
         el = time.perf_counter() - t0
         if el > seconds_target or n >= 4:
             break
-    return {"value": p.nx * p.ny * 3 * n / el, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle", "sample": f"{n} SSP-RK3 step(s) of the 4096^2 blast in FP64 "
-                                         f"({el:.1f} s, OpenMP over grid lines)"}
+    out = {"value": p.nx * p.ny * 3 * n / el, "unit": UNIT, "cores": oracle.num_threads(),
+           "kind": "oracle", "sample": f"{n} SSP-RK3 step(s) of the 4096^2 blast in FP64 "
+                                        f"({el:.1f} s, OpenMP over grid lines)"}
+    # one core: a step of the blast on 1024^2, and a step of each of the
+    # first 256 problems of the 1-D Riemann batch (a 1-D line is one
+    # thread's work in the oracle)
+    cores = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        q = W.blast_2d(1024)
+        gq = oracle.make_grid(q.ndim, q.nx, q.ny, q.dx, q.dy, q.gamma, q.bc)
+        Uq = np.ascontiguousarray(q.U0)
+        t0 = time.perf_counter()
+        oracle.rk3_step(gq, Uq, min(q.cfl, 1.0 / 12.0) / oracle.max_rate(gq, Uq))
+        el1 = time.perf_counter() - t0
+        rb = W.riemann_batch()[:256]
+        cells = 0
+        t0 = time.perf_counter()
+        for r in rb:
+            gr = oracle.make_grid(1, r.nx, 1, r.dx, 1.0, r.gamma, r.bc)
+            Ur = np.ascontiguousarray(r.U0)
+            oracle.rk3_step(gr, Ur, (1.0 / 24.0) / oracle.max_rate(gr, Ur))
+            cells += r.nx
+        el2 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    out["single_core"] = {"blast_1024": q.nx * q.ny * 3 / el1, "riemann_batch_256": cells * 3 / el2,
+                          "unit": UNIT, "sample": f"one SSP-RK3 step of the 1024^2 blast ({el1:.1f} s); "
+                                                  f"one step of each of the first 256 problems of the "
+                                                  f"1-D Riemann batch, {cells} cells ({el2:.1f} s)"}
+    return out
 
 
 def main():

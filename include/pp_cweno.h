@@ -157,19 +157,26 @@ int pp_cweno_create_batch(const pp_cweno_config *cfgs, int64_t nprob, void *cuda
 
 /* Copy initial cell averages in (layout above; on_device != 0: U is a
  * device pointer), set t = t0 and the step count to 0, check every cell is
- * in G and finite (PP_ERR_STATE otherwise).  Synchronises the stream. */
+ * finite and in G, the admissible set rho > 0, p > 0 of Sec. 2.4
+ * (PP_ERR_STATE otherwise), and take the first step's limiter epsilon
+ * eps = min(eps_pos, min rho) (Sec. 2.4 limiter, step 1) and the first dt
+ * (eq. (CFL-CD)) from it.  Synchronises the stream. */
 int pp_cweno_set_state(pp_cweno_t h, const double *U, int on_device, double t0);
 
 /* Copy the current state out; t and steps may be NULL.  Synchronises. */
 int pp_cweno_get_state(pp_cweno_t h, double *U, int on_device, double *t, int64_t *steps);
 
-/* One SSP-RK3 step with dt = min(cfl-limited dt, dt_max); *dt_taken may be
- * NULL.  Synchronises.  Batch handles: every problem takes one step.  With
+/* One SSP-RK3 step (eq. (RK3), Sec. 2.5: three stages, each one evaluation
+ * of the FVCW operator L with the positivity limiter of Sec. 2.4) with
+ * dt = min(cfl-limited dt, dt_max), the cfl-limited dt being
+ * cfl h / max(|u| + a) (eq. (CFL-CD)); *dt_taken may be NULL.
+ * Synchronises.  Batch handles: every problem takes one step.  With
  * cfl_positivity_cap a step that fails the face check is redone (up to 64
  * attempts) until it is accepted. */
 int pp_cweno_step(pp_cweno_t h, double dt_max, double *dt_taken);
 
-/* March every problem until its t reaches t_final (the last step is cut to
+/* March every problem with SSP-RK3 steps (eq. (RK3), Sec. 2.5; dt as in
+ * pp_cweno_step) until its t reaches t_final (the last step is cut to
  * land on it), or until max_steps steps were taken (PP_ERR_STEPS).  Steps
  * are replayed from a captured CUDA graph; the host reads the device-side
  * progress flags once per replay.  *steps_taken (may be NULL) receives the

@@ -598,12 +598,361 @@ __global__ void __launch_bounds__(32) char_solve_kernel(const CharArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- FP32, few walks
+// The same walk with four lanes per (line, side) chain, for launches with
+// few chains (batch groups of long 1-D lines: a few hundred walks of up to
+// 8192 positions, fewer than one warp per SM in the one-thread layout,
+// where the chain's latency is the whole cost).  Lane j holds column j of
+// the block being eliminated and the right-hand-side columns of unknown j:
+// column j of Y (and of the Woodbury block on periodic lines); the g
+// column is the same in every lane (every lane forms it from the same data
+// with the same multipliers).  Per position the lanes solve
+// B' [Y | g] = [C | r - A g_prev] together by Gaussian elimination with
+// partial pivoting: lane c finds the pivot of column c in its own column
+// and hands the exchange, the pivot's reciprocal and the multipliers to the
+// other lanes; the back substitution takes the upper triangle's entries
+// from their lanes.  A Y_prev needs column j of Y_prev only, which lane j
+// already holds.  With three fields lane 3 carries right-hand sides only.
+// The eight chains of a warp stay converged (full-warp shuffles over 4-lane
+// segments): the warp walks as many positions as its longest chain, and a
+// chain past its own end (a shorter batched line) computes on stale data
+// and stores nothing.  A position costs about twice the one-thread walk's
+// instructions per chain, so with many chains the one-thread walk is
+// faster; the launch picks by the number of chains.
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int LW = 4;   // lanes per chain (shuffle segment width)
+
+// X <- M^{-1} X over the four lanes of a chain: M's column j and NR
+// columns X[s] in lane j (lane ids below are within the chain's segment)
+template <int NV, int NR>
+__device__ __forceinline__ void lanes_solve(float (&M)[NV], float (&X)[NR][NV]) {
+  float inv[NV];
+  float U[NV][NV];   // U[c][q], q > c: row c of the factor, from lane q
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    if (c < NV - 1) {
+      int piv = c;
+      float best = fabsf(M[c]);
+#pragma unroll
+      for (int r = c + 1; r < NV; ++r) {
+        const float m = fabsf(M[r]);
+        if (m > best) { best = m; piv = r; }
+      }
+      piv = __shfl_sync(FULL, piv, c, LW);
+#pragma unroll
+      for (int r = c + 1; r < NV; ++r) {
+        const bool sw = piv == r;
+        const float t = M[c];
+        M[c] = sw ? M[r] : t;
+        M[r] = sw ? t : M[r];
+#pragma unroll
+        for (int s = 0; s < NR; ++s) {
+          const float u = X[s][c];
+          X[s][c] = sw ? X[s][r] : u;
+          X[s][r] = sw ? u : X[s][r];
+        }
+      }
+    }
+    const float iv = __shfl_sync(FULL, 1.0f / M[c], c, LW);
+    inv[c] = iv;
+#pragma unroll
+    for (int r = c + 1; r < NV; ++r) {
+      const float f = __shfl_sync(FULL, M[r] * iv, c, LW);
+      M[r] -= f * M[c];
+#pragma unroll
+      for (int s = 0; s < NR; ++s) X[s][r] -= f * X[s][c];
+    }
+#pragma unroll
+    for (int q = c + 1; q < NV; ++q) U[c][q] = __shfl_sync(FULL, M[c], q, LW);
+  }
+#pragma unroll
+  for (int s = 0; s < NR; ++s)
+#pragma unroll
+    for (int c = NV - 1; c >= 0; --c) {
+      float x = X[s][c];
+#pragma unroll
+      for (int q = c + 1; q < NV; ++q) x -= U[c][q] * X[s][q];
+      X[s][c] = x * inv[c];
+    }
+}
+
+template <int NV, bool PER>
+__global__ void __launch_bounds__(64) char_solve_lanes_kernel(const CharArgs a) {
+  constexpr int NC = PER ? NV + 1 : 1;       // right-hand-side columns of g
+  constexpr int ROW = NV * NV + NV * NC;     // scratch values per row: Y, g
+  constexpr int RC = 4 * NV + 4;             // Roe scalars and row coefficients per position
+  constexpr int CH = 16;                     // chains per block
+  constexpr int PD = 8;                      // positions in flight
+  constexpr int NR = PER ? 3 : 2;            // right-hand sides per lane: Y col, (Z col,) g
+  constexpr int SG = NR - 1;
+  constexpr int RING = RC > ROW ? RC : ROW;
+  // chain stride 18 words: the back substitution's four lanes of a chain
+  // read entries 4 apart (rows k of the record), which a stride of 16 puts
+  // in one bank; 18 spreads them over the 32 banks
+  constexpr int CHP = CH + 2;
+  __shared__ float ring[PD][RING][CHP];
+  const int tid = threadIdx.x;
+  const int ch = tid >> 2, j = tid & 3;
+  const long long NL = a.nlines;
+  const long long line_ = (long long)blockIdx.x * CH + ch;
+  const bool live = line_ < NL;
+  const long long line = live ? line_ : NL - 1;   // idle chains repeat the last line, store nothing
+  const bool col = live && j < NV;                // lane owns a column of the block
+  const int side = blockIdx.y;
+  const LineGeo geo = line_geo(a, line);
+  const int n = geo.n;
+  const int nw = __reduce_max_sync(FULL, n);      // the warp's longest chain
+  const int NMAX = a.n;                           // position stride of rows and scratch
+  const long long lbase = geo.base;
+  const float *rows = reinterpret_cast<const float *>(a.rows) + (long long)side * NMAX * RC * NL + line;
+  float *scr = reinterpret_cast<float *>(a.scr) + (long long)side * ((long long)NMAX * ROW + NV * NV) * NL + line;
+  auto slot = [&](int p, int e) -> float & { return scr[((long long)p * ROW + e) * NL]; };
+  auto wslot = [&](int e) -> float & { return scr[((long long)NMAX * ROW + e) * NL]; };
+  int gv[NV];
+  grid_vars<NV>(a, gv);
+  auto cidx = [&](int p) { return side == 0 ? p : n - 1 - p; };
+  // lane j's entries of a row record, split four ways over the chain
+  auto issue_row = [&](int p) {
+#pragma unroll
+    for (int q = 0; q < RC / 4; ++q) {
+      const int e = j + 4 * q;
+      cp_async<4>(&ring[p % PD][e][ch], &rows[((long long)p * RC + e) * NL]);
+    }
+  };
+#pragma unroll 1
+  for (int i = 0; i < PD - 1; ++i) {
+    if (i < n) issue_row(i);
+    cp_async_commit();
+  }
+  // k-th entry of this lane's column of an NV x NV matrix (no dynamic register index)
+  auto colj = [&](const float (&Mk)[NV]) {
+    float v = Mk[0];
+#pragma unroll
+    for (int q = 1; q < NV; ++q) v = j == q ? Mk[q] : v;
+    return v;
+  };
+
+  float Yc[NV], Zc[NV], gc[NV], GiAc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) Yc[k] = Zc[k] = gc[k] = GiAc[k] = 0.0f;
+#pragma unroll 1
+  for (int p = 0; p < nw; ++p) {
+    const bool act = live && p < n;
+    __syncwarp();   // slot (p - 1) % PD is read by every lane before it is refilled
+    if (p + PD - 1 < n) issue_row(p + PD - 1);
+    cp_async_commit();
+    cp_async_wait<PD - 1>();
+    __syncwarp();   // the chain's four lanes' copies of position p have landed
+    float co[RC];
+#pragma unroll
+    for (int e = 0; e < RC; ++e) co[e] = ring[p % PD][e][ch];
+    float L[NV][NV];
+    {
+      const float rs[4] = {co[0], co[1], co[2], co[3]};
+      left_from<float, NV>(rs, L);
+    }
+    float ca[NV], cb[NV], cc[NV], Lj[NV];
+    float M[NV], X[NR][NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      ca[k] = co[4 + 4 * k];
+      cb[k] = co[4 + 4 * k + 1];
+      cc[k] = co[4 + 4 * k + 2];
+      Lj[k] = colj(L[k]);
+      M[k] = cb[k] * Lj[k];
+      X[0][k] = cc[k] * Lj[k];
+      X[SG][k] = co[4 + 4 * k + 3];
+      if (PER) X[1][k] = 0.0f;
+    }
+    if constexpr (PER) {
+      if (p == 0) {
+        // G = -B_0: B'_0 = 2 B_0, Woodbury column j of U_0 = G, and column
+        // j of G^{-1} A_0 for the last position and the final correction
+        float Gm[NV], Aj[1][NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          Gm[k] = -M[k];
+          Aj[0][k] = ca[k] * Lj[k];
+          X[1][k] = Gm[k];
+          M[k] += M[k];
+        }
+        lanes_solve<NV, 1>(Gm, Aj);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          GiAc[k] = Aj[0][k];
+          if (col) wslot(k * NV + j) = GiAc[k];
+        }
+      }
+    }
+    if (p > 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        float tY = 0.0f, tg = 0.0f, tz = 0.0f;
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+          tY += L[k][m] * Yc[m];
+          tg += L[k][m] * gc[m];
+          if (PER) tz += L[k][m] * Zc[m];
+        }
+        M[k] -= ca[k] * tY;
+        X[SG][k] -= ca[k] * tg;
+        if (PER) X[1][k] -= ca[k] * tz;
+      }
+    }
+    if constexpr (PER) {
+      if (p == n - 1) {
+        // B'_{n-1} = B_{n-1} - C_{n-1} G^{-1} A_0; the coupling to x_0 moves
+        // into the Woodbury columns (U_{n-1} = C_{n-1})
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          float t = 0.0f;
+#pragma unroll
+          for (int m = 0; m < NV; ++m) t += cc[k] * L[k][m] * GiAc[m];
+          M[k] -= t;
+          X[1][k] += X[0][k];
+          X[0][k] = 0.0f;
+        }
+      }
+    }
+    lanes_solve<NV, NR>(M, X);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      Yc[k] = X[0][k];
+      gc[k] = X[SG][k];
+      if (PER) Zc[k] = X[1][k];
+      if (col && act) {
+        slot(p, k * NV + j) = Yc[k];
+        if (PER) slot(p, NV * NV + k * NC + 1 + j) = Zc[k];
+      }
+    }
+    if (act && j == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) slot(p, NV * NV + k * NC) = gc[k];
+    }
+  }
+  cp_async_wait<0>();
+  __syncwarp();   // the chain's scratch rows, written by all four lanes, are read below
+
+  // back substitution x_p = g_p - Y_p x_{p+1}; lane k (< NV) forms row k of
+  // x_p from row k of (Y_p, g_p) and all of x_{p+1}; step b is position
+  // n - 2 - b of each chain
+  const int k = j < NV ? j : NV - 1;
+  int gvk = gv[0];   // grid variable of field k, without a dynamic register index
+#pragma unroll
+  for (int q = 1; q < NV; ++q) gvk = k == q ? gv[q] : gvk;
+  float *out = reinterpret_cast<float *>(side == 0 ? a.Um : a.Up);
+  float x[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) x[c] = slot(n - 1, NV * NV + k * NC + c);
+  auto issue_mult = [&](int b) {
+    if (j >= NV) return;   // lane 3 of a three-field chain: nothing of its own
+    const int p = n - 2 - b;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) cp_async<4>(&ring[b % PD][k * NV + q][ch], &slot(p, k * NV + q));
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      cp_async<4>(&ring[b % PD][NV * NV + k * NC + c][ch], &slot(p, NV * NV + k * NC + c));
+  };
+  __syncwarp();
+#pragma unroll 1
+  for (int i = 0; i < PD - 1; ++i) {
+    if (i < n - 1) issue_mult(i);
+    cp_async_commit();
+  }
+  auto store_x = [&](int p) {
+    if (!col) return;
+    if (PER) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) slot(p, NV * NV + k * NC + c) = x[c];
+    } else {
+      out[lbase + (long long)cidx(p) * geo.cs + (long long)gvk * geo.ncell] = x[0];
+    }
+  };
+  store_x(n - 1);
+#pragma unroll 1
+  for (int b = 0; b < nw - 1; ++b) {
+    const int p = n - 2 - b;
+    if (b + PD - 1 < n - 1) issue_mult(b + PD - 1);
+    cp_async_commit();
+    cp_async_wait<PD - 1>();   // this lane's own copies only: no exchange through the ring
+    float Yr[NV], gr[NC];   // (lane 3 of a three-field chain reads values it never uses)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Yr[q] = ring[b % PD][k * NV + q][ch];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) gr[c] = ring[b % PD][NV * NV + k * NC + c][ch];
+    float xn[NV][NC];
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) xn[q][c] = __shfl_sync(FULL, x[c], q, LW);
+    if (p >= 0) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float s = gr[c];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) s -= Yr[q] * xn[q][c];
+        x[c] = s;
+      }
+      store_x(p);
+    }
+  }
+  cp_async_wait<0>();
+  if constexpr (PER) {
+    __syncwarp();   // every lane's rows of y and Z are in the scratch
+    // S = I + Z_0 + G^{-1} A_0 Z_{n-1}, t = y_0 + G^{-1} A_0 y_{n-1};
+    // x_p = y_p - Z_p S^{-1} t, row k in lane k
+    float S[NV][NV], t[NV][1], GiA[NV][NV];
+#pragma unroll
+    for (int r = 0; r < NV; ++r)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) GiA[r][q] = wslot(r * NV + q);
+#pragma unroll
+    for (int r = 0; r < NV; ++r) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        float s = (r == q ? 1.0f : 0.0f) + slot(0, NV * NV + r * NC + 1 + q);
+#pragma unroll
+        for (int m = 0; m < NV; ++m) s += GiA[r][m] * slot(n - 1, NV * NV + m * NC + 1 + q);
+        S[r][q] = s;
+      }
+      float s = slot(0, NV * NV + r * NC);
+#pragma unroll
+      for (int m = 0; m < NV; ++m) s += GiA[r][m] * slot(n - 1, NV * NV + m * NC);
+      t[r][0] = s;
+    }
+    gauss_solve<float, NV, 1>(S, t);
+    if (col) {
+#pragma unroll 4
+      for (int p = 0; p < n; ++p) {
+        float s = slot(p, NV * NV + k * NC);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) s -= slot(p, NV * NV + k * NC + 1 + q) * t[q][0];
+        out[lbase + (long long)cidx(p) * geo.cs + (long long)gvk * geo.ncell] = s;
+      }
+    }
+  }
+}
+
+// FP32 launches with fewer lines than this take the four-lane walk (2048
+// lines: 4096 chains, fewer than one warp per SM in the one-thread layout;
+// measured: the 4096^2 grid's 8192 chains walk faster one thread each,
+// 3.41 against 4.17 ms, the Riemann batch's groups of at most ~1700 chains
+// faster four lanes each, 96 against 149 ms per step)
+constexpr long long LANES_BELOW = 2048;
+
 template <typename real, int NV, bool PER>
 cudaError_t launch_nv(const CharArgs &a, int part, cudaStream_t st) {
   if (part == 0) {
     const dim3 grid((unsigned)((a.nlines + CT_L - 1) / CT_L), (unsigned)((a.n + CT_C - 1) / CT_C), 1);
     char_rows_kernel<real, NV, PER><<<grid, 256, 0, st>>>(a);
   } else {
+    if constexpr (sizeof(real) == 4) {
+      if (a.nlines < LANES_BELOW) {
+        char_solve_lanes_kernel<NV, PER><<<dim3((unsigned)((a.nlines + 15) / 16), 2, 1), 64, 0, st>>>(a);
+        return cudaGetLastError();
+      }
+    }
     char_solve_kernel<real, NV, PER><<<dim3((unsigned)((a.nlines + 31) / 32), 2, 1), 32, 0, st>>>(a);
   }
   return cudaGetLastError();

@@ -1,7 +1,8 @@
 """pp_cweno_operator_noalloc: the operator evaluated with the library's fixed
 device scratch instead of allocated memory, for callers that cannot call
-cudaMalloc.  It must give what pp_cweno_operator gives (same tolerance as the
-other operator tests), on two calls in a row sharing the scratch array.
+cudaMalloc.  It must give what pp_cweno_operator gives and what the oracle's
+operator gives (same tolerance as the other operator tests), on two calls in
+a row sharing the scratch array.
 
 This file is collected last on purpose."""
 import numpy as np
@@ -62,6 +63,31 @@ def test_noalloc_operator_matches_handle_operator_twice(B, name, make, eps):
         got = L.cpu().numpy().reshape(p.U0.shape)
         for v in range(p.U0.shape[0]):
             assert np.abs(got[v] - ref[v]).max() <= 1e-12 * scale[v], (name, v)
+
+
+@pytest.mark.parametrize("name,make,eps", [
+    ("jumps_2d_300x200", lambda: W.random_jumps_2d(300, 200, stream=72), 1e-13),
+    ("riemann_1d_1300_device_eps", lambda: W.riemann_1d(1300, (1.0, 0.4, 1.0), (0.2, -0.2, 0.1),
+                                                        bc=(2, 1)), 0.0),
+])
+def test_noalloc_operator_matches_oracle(B, name, make, eps):
+    """The allocation-free operator against the oracle's operator directly,
+    element-wise within 1e-12 of each variable's flux scale."""
+    import oracle
+    p = make()
+    Ud = torch.from_numpy(np.ascontiguousarray(p.U0).ravel()).cuda()
+    cfg = B.config_from_problem(p)
+    L = torch.full_like(Ud, float("nan"))
+    B.operator_noalloc(cfg, Ud, L, eps)
+    torch.cuda.synchronize()
+    got = L.cpu().numpy().reshape(p.U0.shape)
+    g = oracle.make_grid(p.ndim, p.nx, p.ny, p.dx, p.dy, p.gamma, p.bc)
+    ref = oracle.operator(g, p.U0, eps if eps > 0 else min(cfg.eps_pos, p.U0[0].min()))
+    ref = ref[0] if isinstance(ref, tuple) else ref
+    scale = _scale(p, p.U0)
+    err = [np.abs(got[v] - ref[v]).max() / scale[v] for v in range(p.U0.shape[0])]
+    print(f"PARITY noalloc vs oracle {name}: max |dL| / flux scale {np.max(err):.2e}")
+    assert max(err) <= 1e-12, (name, err)
 
 
 def test_noalloc_rejects_oversized_and_mixed(B):
