@@ -687,11 +687,10 @@ __global__ void __launch_bounds__(64) char_solve_lanes_kernel(const CharArgs a) 
   constexpr int NR = PER ? 3 : 2;            // right-hand sides per lane: Y col, (Z col,) g
   constexpr int SG = NR - 1;
   constexpr int RING = RC > ROW ? RC : ROW;
-  // chain stride 18 words: the back substitution's four lanes of a chain
-  // read entries 4 apart (rows k of the record), which a stride of 16 puts
-  // in one bank; 18 spreads them over the 32 banks
-  constexpr int CHP = CH + 2;
-  __shared__ float ring[PD][RING][CHP];
+  // (a chain stride of 18 words instead of 16 takes the back substitution's
+  // 4-way bank conflicts away but measured slower: 120 against 95 ms per
+  // Riemann batch step)
+  __shared__ float ring[PD][RING][CH];
   const int tid = threadIdx.x;
   const int ch = tid >> 2, j = tid & 3;
   const long long NL = a.nlines;
