@@ -48,6 +48,8 @@ struct CharArgs {
   const LineRef *lines;
   const ProbDesc *probs;
   int xdir;                 // batched: 1 x lines, 0 y lines (columns), 2 rows of the transposed planes
+  int layout;               // FP32 block solve: 0 one thread per walk, 1 four lanes per walk,
+                            // < 0 by the number of walks (four lanes below 2048 lines)
 };
 
 // values of one row of the scratch: the multiplier block Y (nv x nv) and

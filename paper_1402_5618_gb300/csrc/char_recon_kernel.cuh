@@ -933,11 +933,12 @@ __global__ void __launch_bounds__(64) char_solve_lanes_kernel(const CharArgs a) 
   }
 }
 
-// FP32 launches with fewer lines than this take the four-lane walk (2048
-// lines: 4096 chains, fewer than one warp per SM in the one-thread layout;
-// measured: the 4096^2 grid's 8192 chains walk faster one thread each,
-// 3.41 against 4.17 ms, the Riemann batch's groups of at most ~1700 chains
-// faster four lanes each, 96 against 149 ms per step)
+// Without a timed choice (CharArgs::layout < 0), FP32 launches with fewer
+// lines than this take the four-lane walk (2048 lines: 4096 chains, fewer
+// than one warp per SM in the one-thread layout; measured: the 4096^2
+// grid's 8192 chains walk faster one thread each, 3.41 against 4.17 ms, the
+// Riemann batch's groups of at most ~1700 chains faster four lanes each, 96
+// against 149 ms per step)
 constexpr long long LANES_BELOW = 2048;
 
 template <typename real, int NV, bool PER>
@@ -947,7 +948,7 @@ cudaError_t launch_nv(const CharArgs &a, int part, cudaStream_t st) {
     char_rows_kernel<real, NV, PER><<<grid, 256, 0, st>>>(a);
   } else {
     if constexpr (sizeof(real) == 4) {
-      if (a.nlines < LANES_BELOW) {
+      if (a.layout == 1 || (a.layout < 0 && a.nlines < LANES_BELOW)) {
         char_solve_lanes_kernel<NV, PER><<<dim3((unsigned)((a.nlines + 15) / 16), 2, 1), 64, 0, st>>>(a);
         return cudaGetLastError();
       }

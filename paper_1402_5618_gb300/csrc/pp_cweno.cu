@@ -656,6 +656,7 @@ struct LineGroup {
   // concurrently)
   int nmax = 0;
   void *cscr = nullptr, *crows = nullptr;
+  mutable int char_layout = -1;   // FP32 block-solve layout, timed at the first step
 };
 
 struct pp_cweno_s {
@@ -697,6 +698,10 @@ struct pp_cweno_s {
   void *UMPy = nullptr, *cscry = nullptr, *crowsy = nullptr;
   cudaStream_t ystream = nullptr;
   cudaEvent_t yfork = nullptr, yjoin = nullptr;
+  // FP32 block-solve layout per direction (one thread or four lanes per
+  // walk), timed on the handle's own state at the first step; -1 until then
+  mutable int char_layout[2] = {-1, -1};
+  bool char_tuning = false;
   // per-kernel profiling: called after each reconstruction launch, so that
   // the reconstruction and the line kernel get separate events
   std::function<void()> mark_hook;
@@ -832,6 +837,38 @@ cudaError_t dispatch(const pp_cweno_s *h, int mode, bool periodic, const SweepAr
 // (line geometry, boundaries) from the planes U in the line arithmetic, into
 // the handle's U^- / U^+ planes (Sec. 2.3); the line kernel then limits them
 // and forms the fluxes and the update.  Nothing to do for other handles.
+// Autotuner of the FP32 block solve: with the rows of c computed, time the
+// solve in both layouts (one thread per walk, four lanes per walk; CUDA
+// events on the stream, the first launch of each a warm-up) and keep the
+// faster in *layout.  The solve writes only the face-value planes and its
+// scratch, which the step recomputes.
+cudaError_t pick_char_layout(CharArgs c, int nv, bool per, cudaStream_t st, int *layout) {
+  cudaError_t e = launch_char_recon_f32(c, nv, per, 0, st);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_l = 0;
+  for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
+    c.layout = l;
+    float t_min = 1e30f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = launch_char_recon_f32(c, nv, per, 1, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0 && t < t_min) t_min = t;
+    }
+    if (t_min < best) { best = t_min; best_l = l; }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e == cudaSuccess) *layout = best_l;
+  return e;
+}
+
 cudaError_t launch_char(const pp_cweno_s *h, const SweepArgs &a, const void *U, long long nlines,
                         cudaStream_t st = nullptr) {
   if (h->cfg.recon != PP_RECON_CHARACTERISTIC) return cudaSuccess;
@@ -856,6 +893,9 @@ cudaError_t launch_char(const pp_cweno_s *h, const SweepArgs &a, const void *U, 
   c.eps_weno = h->cfg.eps_weno;
   const bool per = a.bclo == PP_BC_PERIODIC;
   cudaError_t e = cudaSuccess;
+  if (h->char_tuning && is_mixed(h))
+    e = pick_char_layout(c, h->nv, per, st ? st : h->stream, &h->char_layout[ybuf ? 1 : 0]);
+  c.layout = h->char_layout[ybuf ? 1 : 0];
   for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
     e = is_mixed(h) ? launch_char_recon_f32(c, h->nv, per, part, st ? st : h->stream)
                     : launch_char_recon_f64(c, h->nv, per, part, st ? st : h->stream);
@@ -894,6 +934,8 @@ cudaError_t launch_char_group(const pp_cweno_s *h, const LineGroup &g, const Swe
   c.probs = h->probs;
   c.xdir = a.xdir;
   cudaError_t e = cudaSuccess;
+  if (h->char_tuning && is_mixed(h)) e = pick_char_layout(c, h->nv, g.periodic, st, &g.char_layout);
+  c.layout = g.char_layout;
   for (int part = 0; part < 2 && e == cudaSuccess; ++part)
     e = is_mixed(h) ? launch_char_recon_f32(c, h->nv, g.periodic, part, st)
                     : launch_char_recon_f64(c, h->nv, g.periodic, part, st);
@@ -1431,7 +1473,24 @@ std::vector<std::pair<TuneKey, int>> g_tune_cache;
 int autotune_batch(pp_cweno_s *h) {
   if (h->cfg.recon == PP_RECON_CHARACTERISTIC) {   // its line kernels have no elimination to tune
     h->m = 8;
-    return PP_OK;
+    if (!is_mixed(h)) return PP_OK;
+    // the block-solve layout of every line group, on the batch's own state
+    h->char_tuning = true;
+    cudaError_t e = cudaSuccess;
+    for (const LineGroup &g : h->groups) {
+      if (e != cudaSuccess) break;
+      SweepArgs a;
+      memset(&a, 0, sizeof(a));
+      fill_state(h, a, h->U0, h->U0, nullptr);
+      fill_common(h, a, 0, 1e-13, h->ctl_scratch);
+      a.xdir = g.xdir ? 1 : (g.trans ? 2 : 0);
+      a.vn = g.xdir ? 1 : 2;
+      a.vt = h->nv == 4 ? (g.xdir ? 2 : 1) : -1;
+      e = launch_char_group(h, g, a, g.trans ? (const void *)h->UT : (const void *)a.Uh, h->stream);
+    }
+    h->char_tuning = false;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? PP_OK : PP_ERR_CUDA;
   }
   std::vector<Ctl> z((size_t)h->nprob);
   memset(z.data(), 0, sizeof(Ctl) * z.size());
@@ -1475,6 +1534,22 @@ int autotune(pp_cweno_s *h) {
   if (h->tuned) return PP_OK;
   h->tuned = true;
   if (h->batch) return autotune_batch(h);
+  if (h->cfg.recon == PP_RECON_CHARACTERISTIC && is_mixed(h)) {
+    // the block-solve layout of each direction, on the handle's own state
+    // (the reconstruction writes only its planes and scratch)
+    pp_cweno_s *hm = h;
+    hm->char_tuning = true;
+    SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    fill_state(h, a, h->U0, h->U0, nullptr);
+    fill_common(h, a, 0, 1e-13, h->ctl_scratch);
+    const long long nl = fill_geometry(h, a, true);
+    cudaError_t e = launch_char(h, a, a.Uh, nl);
+    if (e == cudaSuccess && h->nv == 4) e = launch_char_y(h, h->U0, h->stream);
+    hm->char_tuning = false;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return PP_ERR_CUDA;
+  }
   TuneKey key{h->cfg.precision, h->nv == 4 ? 2 : 1, h->nx, h->ny, h->cfg.bc[0] == PP_BC_PERIODIC};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
