@@ -65,3 +65,22 @@ def test_checked_step_tail_is_kept_out_of_the_stage_kernels():
     assert tail["launches_per_step"] == 3
     assert tail["avg_ms_per_step"] == pytest.approx(0.204, abs=1e-4)
     assert tail["share"] == pytest.approx(0.204 / sum(row), abs=1e-3)
+
+
+def test_cpu_baseline_reports_all_cores_and_one_core(monkeypatch):
+    """The bench's oracle baseline (no GPU): all-core steps of the blast and
+    the one-core figures (a blast step, one step of each of the first
+    problems of the Riemann batch), on shrunk workloads so the test is fast;
+    the oracle's thread count is restored afterwards."""
+    import oracle
+    from paper_1402_5618_gb300 import workloads as W
+    real_blast, real_rb = W.blast_2d, W.riemann_batch
+    monkeypatch.setattr(bench, "N_GRID", 48)
+    monkeypatch.setattr(W, "blast_2d", lambda n, *a, **k: real_blast(min(n, 48), *a, **k))
+    monkeypatch.setattr(W, "riemann_batch", lambda *a, **k: real_rb(nprob=8, n_lo=64, n_hi=128))
+    cores = oracle.num_threads()
+    out = bench._cpu_baseline(0.05)
+    assert oracle.num_threads() == cores
+    assert out["kind"] == "oracle" and out["cores"] == cores and out["value"] > 0
+    sc = out["single_core"]
+    assert sc["blast_1024"] > 0 and sc["riemann_batch_256"] > 0 and sc["unit"] == bench.UNIT
